@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark of the MacLAB step on GB300 (prints ONE JSON line on rank 0).
+
+Workload (default): 3D lid-driven cavity, D3Q19, 128^3 nodes including the
+wall shell, FP32 storage (drho = rho - 1, u / e), Re = 100 (lid speed
+Re / (6 * 127) in lattice units), synthetic start from rest.  One benchmark
+"step" is ``--inner`` MacLAB time steps (default 100) through the C ABI
+(``maclab_step``).  The L2 cache is flushed (a 256 MiB write) before every
+timed step, outside the timed interval; each step is timed with CUDA events on
+the stream the kernels run on.
+
+``value`` is MLUPS = fluid lattice-node updates per second / 1e6, summed over
+ranks.  Extra keys: ``roofline`` of the dominant step kernel, ``cpu_baseline``
+(the FP64 CPU oracle on a bounded sample), ``e2e`` (the same rate with host
+buffers copied in and out every step), ``fp64`` (the same workload in FP64
+storage), ``gpu_launches`` and ``clocks``.
+
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline, FP32 D3Q19 128³ vs FP64; adjoint/forward time"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=128, help="cavity side (nodes, walls included)")
+    p.add_argument("--re", type=float, default=100.0)
+    p.add_argument("--inner", type=int, default=100, help="MacLAB steps per benchmark step")
+    p.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "f16"])
+    p.add_argument("--no-extras", action="store_true", help="skip fp64 / e2e / cpu legs")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if "Active" in r[5 + j]
+                          and "Not" not in r[5 + j]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def traffic_from_profiles(kernel_tag, source_hash):
+    """DRAM bytes per launch recorded by an ncu capture (profiles/*.md), if the
+    kernel source has not changed since (same hash)."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".md"):
+            continue
+        txt = open(os.path.join(pdir, name)).read()
+        m_tag = re.search(r"^kernel_tag:\s*(\S+)", txt, re.M)
+        m_hash = re.search(r"^source_sha256:\s*(\S+)", txt, re.M)
+        m_tr = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt, re.M)
+        if m_tag and m_hash and m_tr and m_tag.group(1) == kernel_tag:
+            return float(m_tr.group(1)) if m_hash.group(1) == source_hash else None
+    return None
+
+
+def step_source_hash():
+    h = hashlib.sha256()
+    for f in ("step.cu", "lattice.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1901_02716_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def cavity_case(n, re):
+    from paper_1901_02716_gb300 import inputs
+    return inputs.cavity3d(n, lid=inputs.lid_speed(re, n))
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+
+def oracle_rate(n, re, budget_s=10.0, max_steps=None):
+    """FP64 CPU oracle MLUPS on the same cavity; steps chosen to fill ~budget_s."""
+    from oracle import oracle as orc
+    case = cavity_case(n, re)
+    rho, u = case.rho.copy(), case.u.copy()
+    t0 = time.perf_counter()
+    rho, u = orc.step(case.lattice, rho, u, case.periodic, wall=case.wall_mask)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(t1, 1e-6)))
+    if max_steps:
+        steps = min(steps, max_steps)
+    t0 = time.perf_counter()
+    rho, u = orc.step(case.lattice, rho, u, case.periodic, wall=case.wall_mask, nsteps=steps)
+    dt = time.perf_counter() - t0
+    return case.n_fluid * steps / dt / 1e6, steps, dt
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    case = cavity_case(args.n, args.re)
+    rho, u = case.rho.copy(), case.u.copy()
+    for _ in range(args.warmup):
+        rho, u = orc.step(case.lattice, rho, u, case.periodic, wall=case.wall_mask)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rho, u = orc.step(case.lattice, rho, u, case.periodic, wall=case.wall_mask)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = case.n_fluid * args.steps / total / 1e6
+    sample = (f"{args.steps} MacLAB steps of the {args.n}^3 D3Q19 cavity (one per benchmark "
+              f"step), FP64 CPU oracle, single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"3D lid-driven cavity D3Q19 {args.n}^3, Re={args.re:g}",
+                   "inner_steps": 1, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1901_02716_gb300 import _build
+    from paper_1901_02716_gb300 import maclab as M
+
+    torch.cuda.set_device(local_rank)
+    if not os.path.exists(M.library_path()):
+        _build.build()
+    prec = M.PRECISION_NAMES[args.precision]
+    case = cavity_case(args.n, args.re)
+    stream = torch.cuda.current_stream()
+    solver = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
+    lups_per_step = case.n_fluid * args.inner
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one_step():
+        solver.step(args.inner)
+
+    # warm-up
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    dist_barrier(world)
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))                 # evict the state from L2 (not timed)
+        ev[i][0].record(stream)
+        one_step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    clocks = sampler.stop() if sampler else None
+    per = [a.elapsed_time(b) for a, b in ev]          # ms
+    total_ms = sum(per)
+    total_ms = dist_max(total_ms, world)
+    value = world * lups_per_step * args.steps / (total_ms * 1e-3) / 1e6
+    launches_per_step = solver.launches_per_step() * args.inner
+    avg_launch_ms = total_ms / (args.steps * launches_per_step)
+
+    if rank != 0:
+        solver.close()
+        return
+
+    d = 3
+    bytes_per_lup = (d + 1) * 2 * {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[args.precision]
+    steps_per_launch = solver.steps_per_launch()
+    algo_bytes = bytes_per_lup * case.n_fluid * steps_per_launch
+    peak, peak_kind = peaks()
+    achieved = algo_bytes / (avg_launch_ms * 1e-3) / 1e9
+    kernel_tag = solver.kernel_tag()
+    traffic = traffic_from_profiles(kernel_tag, step_source_hash())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"3D lid-driven cavity D3Q19 {args.n}^3 (walls included), "
+                               f"Re={args.re:g}, {args.precision} storage",
+                   "inner_steps": args.inner, "fluid_nodes": case.n_fluid,
+                   "l2": "flushed (256 MiB write) before each timed step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": kernel_tag, "bytes_per_lup": bytes_per_lup,
+                     "peak_kind": peak_kind, "avg_launch_us": avg_launch_ms * 1e3},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clocks,
+    }
+
+    if not args.no_extras:
+        line["e2e"] = e2e_leg(M, case, prec, args, stream)
+        if args.precision != "f64":
+            line["fp64"] = fp64_leg(M, case, args, stream, flush)
+        mlups, steps, secs = oracle_rate(args.n, args.re)
+        line["cpu_baseline"] = {
+            "value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} MacLAB steps of the same {args.n}^3 cavity from rest "
+                      f"({secs:.1f} s, FP64, single thread)"}
+    solver.close()
+    print(json.dumps(line), flush=True)
+
+
+def ctypes_stream(stream):
+    return stream.cuda_stream if stream.cuda_stream else None
+
+
+def e2e_leg(M, case, prec, args, stream):
+    """Same MLUPS through the public API with host buffers: pinned host (rho, u)
+    in, ``inner`` steps, (rho, u) back to pinned host, every step."""
+    import torch
+    grid = case.grid
+    rho_h = torch.empty(grid, dtype=torch.float32).pin_memory()
+    u_h = torch.empty((3,) + grid, dtype=torch.float32).pin_memory()
+    rho_h.copy_(torch.from_numpy(case.rho.astype(np.float32)))
+    u_h.copy_(torch.from_numpy(case.u.astype(np.float32)))
+    rho_n, u_n = rho_h.numpy(), u_h.numpy()
+    s = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
+    k = max(2, min(args.steps, 5))
+    for _ in range(2):
+        s.set_state(rho_n, u_n)
+        s.step(args.inner)
+        s.get_state_into(rho_n, u_n)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        s.set_state(rho_n, u_n)
+        s.step(args.inner)
+        s.get_state_into(rho_n, u_n)           # synchronises
+    dt = time.perf_counter() - t0
+    s.close()
+    nbytes = rho_h.numel() * 4 + u_h.numel() * 4
+    return {"value": case.n_fluid * args.inner * k / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+
+def fp64_leg(M, case, args, stream, flush):
+    import torch
+    s = M.Solver.from_case(case, M.F64, stream=ctypes_stream(stream))
+    for _ in range(2):
+        s.step(args.inner)
+    ts = []
+    for i in range(3):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.step(args.inner)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    s.close()
+    return {"value": case.n_fluid * args.inner * 3 / (sum(ts) * 1e-3) / 1e6, "unit": "MLUPS",
+            "bytes_per_lup": 64}
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("MACLAB_BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * maclab.h -- C ABI of the GB300 MacLAB library (libmaclab.so).
+ *
+ * The library advances the macroscopic lattice Boltzmann method of Zhou,
+ * "Macroscopic Lattice Boltzmann Method (MacLAB)": with relaxation time
+ * tau = 1 no distribution function is stored, and each node's new density and
+ * momentum are the zeroth and first moments of the equilibria, Eq. (2), of its
+ * upstream neighbours x - e_a dt (Eqs. (4) and (5)); the particle speed is
+ * e = 6 nu / dx (Eq. (6)) and the time step dt = dx / e.  Walls keep the
+ * physical values they are given (procedure step (iv); Tests 2, 3 and 5);
+ * periodic axes wrap (Tests 1 and 4).
+ *
+ * Conventions for every call:
+ *  - Return a maclab_status: 0 = OK, > 0 warning, < 0 error.  Nothing throws,
+ *    nothing aborts.  maclab_status_string() names a status.
+ *  - Arrays are structure-of-arrays with x fastest: node index
+ *    (z * ny + y) * nx + x; a velocity field is d consecutive arrays of N
+ *    values (all x-components, then y, then z).  N = nx * ny * nz counts wall
+ *    nodes too.  D2Q9 uses nz = 1.
+ *  - "where" = MACLAB_HOST (pageable or pinned host memory) or MACLAB_DEVICE
+ *    (memory of the handle's GPU).  Caller buffers stay owned by the caller
+ *    and are not retained after the call returns.
+ *  - Work is queued on the handle's CUDA stream (the one given in the config,
+ *    or the default stream).  Calls that return data to the host synchronise
+ *    that stream; the others are asynchronous, and a device-side failure
+ *    surfaces as MACLAB_ERR_CUDA at the next synchronising call.
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef MACLAB_H
+#define MACLAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t maclab_status;
+#define MACLAB_OK 0
+#define MACLAB_WARN_RLE 1          /* lattice Reynolds number U dx / nu > 1 (stated
+                                      stability bound, sentence after Eq. (6)) */
+#define MACLAB_ERR_INVALID (-1)    /* bad argument, size, pointer or mask */
+#define MACLAB_ERR_CUDA (-2)       /* CUDA runtime error (launch, copy, device fault) */
+#define MACLAB_ERR_NONFINITE (-3)  /* NaN or Inf found in the state */
+#define MACLAB_ERR_TIMEOUT (-4)    /* a bounded device-side wait ran out */
+#define MACLAB_ERR_OOM (-5)        /* device or host allocation failed */
+#define MACLAB_ERR_UNSUPPORTED (-6)/* valid request that this build does not serve */
+
+typedef enum { MACLAB_D2Q9 = 0, MACLAB_D3Q19 = 1 } maclab_lattice;
+
+/* How the state is stored on the device.  Arithmetic is FP64 for MACLAB_F64
+ * and FP32 for the others.  The density is stored as drho = rho / rho0 - 1 and
+ * the velocity in lattice units u / e. */
+typedef enum {
+  MACLAB_F64 = 0,
+  MACLAB_F32 = 1,
+  MACLAB_BF16_STORE = 2,
+  MACLAB_F16_STORE = 3
+} maclab_precision;
+
+typedef enum { MACLAB_HOST = 0, MACLAB_DEVICE = 1 } maclab_where;
+typedef enum { MACLAB_DTYPE_F64 = 0, MACLAB_DTYPE_F32 = 1 } maclab_dtype;
+
+typedef struct maclab_ctx *maclab_handle;
+
+/*
+ * Problem statement, following the paper's procedure step (i): choose dx,
+ * give nu; the library derives e = 6 nu / dx and dt = dx / e (Eq. (6)).
+ */
+typedef struct {
+  int32_t lattice;          /* maclab_lattice */
+  int32_t precision;        /* maclab_precision */
+  int64_t dims[3];          /* nx, ny, nz (nz = 1 for D2Q9); each >= 1 */
+  double dx;                /* lattice spacing, > 0 */
+  double nu;                /* kinematic viscosity, > 0 */
+  double rho0;              /* reference density (<= 0 means 1, as in the tests) */
+  uint32_t periodic;        /* bit0 x, bit1 y, bit2 z */
+  const uint8_t *node_type; /* HOST array of N bytes, or NULL (all fluid):
+                               0 = fluid, k >= 1 = wall node with wall id k.  On a
+                               non-periodic axis the first and last layers must
+                               be wall nodes. */
+  int32_t n_wall_ids;       /* number of wall ids (ids 1..n_wall_ids) */
+  const double *wall_rho;   /* HOST, n_wall_ids physical densities (NULL = rho0) */
+  const double *wall_u;     /* HOST, n_wall_ids * 3 physical velocities (x,y,z) */
+  double body_force[3];     /* physical body acceleration, e.g. -(1/rho0) dp/dx of
+                               Test 2; 0 = none.  Added after the division of
+                               Eq. (5) as force * dt / e in lattice units. */
+  void *stream;             /* cudaStream_t to run on, or NULL (default stream) */
+} maclab_config;
+
+/* Create a solver for one domain.  Copies the config and its tables, allocates
+ * the device state (two buffers of (d + 1) * N values) and sets the state to
+ * rest (rho = rho0, u = 0) with wall values in place.  Returns
+ * MACLAB_WARN_RLE (with a valid handle) if a wall speed exceeds the stated
+ * stability bound.  Errors: MACLAB_ERR_INVALID (dims, dx, nu, lattice,
+ * precision, wall ids, or an open boundary on a non-periodic axis),
+ * MACLAB_ERR_OOM, MACLAB_ERR_CUDA.  On error *out is NULL. */
+maclab_status maclab_create(const maclab_config *cfg, maclab_handle *out);
+
+/* Free the handle and its device memory (synchronises its stream). NULL is OK. */
+maclab_status maclab_destroy(maclab_handle h);
+
+/* out[0] = e (Eq. (6)), out[1] = dt = dx / e, out[2] = lattice Reynolds number
+ * of the fastest wall, max|U_w| dx / nu, out[3..5] = body force per step in
+ * lattice units, out[6] = fluid node count, out[7] = steps taken so far. */
+maclab_status maclab_params(maclab_handle h, double out[8]);
+
+/* Set the state from physical fields: rho (N values) and u (d * N values) of
+ * the given dtype, in host or device memory.  Wall nodes are overwritten with
+ * their wall id's values.  Resets the step counter. */
+maclab_status maclab_set_state(maclab_handle h, const void *rho, const void *u,
+                               int32_t where, int32_t dtype);
+
+/* Read the current physical state into rho (N) and u (d * N).  Synchronises. */
+maclab_status maclab_get_state(maclab_handle h, void *rho, void *u, int32_t where,
+                               int32_t dtype);
+
+/* Raw stored state, (d + 1) * N values in the storage type of the precision
+ * (double, float, bfloat16 or half): drho, then the d lattice velocity
+ * components.  This is the checkpoint format: setting a state read earlier
+ * resumes bit-identically. maclab_state_bytes gives the size in bytes. */
+maclab_status maclab_state_bytes(maclab_handle h, size_t *bytes);
+maclab_status maclab_get_lattice_state(maclab_handle h, void *state, int32_t where);
+maclab_status maclab_set_lattice_state(maclab_handle h, const void *state, int32_t where);
+
+/* Advance n >= 0 MacLAB steps (Eqs. (4)-(5), walls kept, periodic wrap),
+ * asynchronously on the handle's stream. */
+maclab_status maclab_step(maclab_handle h, int64_t n);
+
+/* Step kernels.  MACLAB_KERNEL_AUTO lets the library choose (the default);
+ * MACLAB_KERNEL_REFERENCE is the simple one-thread-per-node gather, kept as the
+ * GPU-side yardstick; MACLAB_KERNEL_TILED is the staged, vectorised kernel.
+ * Both compute Eqs. (4)-(5) with the same arithmetic per node. */
+#define MACLAB_KERNEL_AUTO 0
+#define MACLAB_KERNEL_REFERENCE 1
+#define MACLAB_KERNEL_TILED 2
+
+/* Choose the step kernel.  MACLAB_ERR_UNSUPPORTED if the tiled kernel cannot
+ * serve this domain (then the handle keeps its previous choice). */
+maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel);
+
+/* Describe the kernel in use: out[0] = kernel id (REFERENCE or TILED),
+ * out[1] = time steps advanced per launch, out[2] = kernel launches per
+ * launch group, out[3] = threads per block.  *name (may be NULL) receives a
+ * static string naming the kernel instance. */
+maclab_status maclab_kernel_info(maclab_handle h, int32_t out[4], const char **name);
+
+/* Run the handle's stream to completion and report any CUDA error. */
+maclab_status maclab_sync(maclab_handle h);
+
+/* Name of a status code (static string). */
+const char *maclab_status_string(maclab_status s);
+
+/* Library build tag, e.g. "maclab sm_103a". */
+const char *maclab_version(void);
+
+/* Message of the last failing call on this host thread (empty if none). */
+const char *maclab_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MACLAB_H */

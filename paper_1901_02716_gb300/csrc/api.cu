@@ -1,0 +1,412 @@
+// api.cu -- the C ABI of libmaclab (declared in include/maclab.h).
+//
+// Host-side only: validation, the unit conversion of procedure step (i)
+// (e = 6 nu / dx, Eq. (6); dt = dx / e), buffer ownership and launches.  All
+// arithmetic on fields happens in the kernels of step.cu / convert.cu.
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "lattice.cuh"
+
+using namespace maclab;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+maclab_status fail(maclab_status s, const char* msg) {
+  g_last_error = msg;
+  return s;
+}
+
+maclab_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return MACLAB_ERR_CUDA;
+}
+
+#define CUDA_TRY(call, where)                       \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool on_closed_boundary(const Geometry& g, int64_t x, int64_t y, int64_t z) {
+  if (!(g.periodic & 1u) && (x == 0 || x == g.nx - 1)) return true;
+  if (!(g.periodic & 2u) && (y == 0 || y == g.ny - 1)) return true;
+  if (g.d == 3 && !(g.periodic & 4u) && (z == 0 || z == g.nz - 1)) return true;
+  return false;
+}
+
+void free_ctx(maclab_ctx* h) {
+  if (!h) return;
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
+  cudaFree(h->d_node_type);
+  cudaFree(h->d_wall_lat);
+  cudaFree(h->d_staging);
+  delete h;
+}
+
+maclab_status ensure_staging(maclab_ctx* h, size_t bytes) {
+  if (h->staging_cap >= bytes) return MACLAB_OK;
+  cudaFree(h->d_staging);
+  h->d_staging = nullptr;
+  h->staging_cap = 0;
+  if (cudaMalloc(&h->d_staging, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MACLAB_ERR_OOM, "staging allocation failed");
+  }
+  h->staging_cap = bytes;
+  return MACLAB_OK;
+}
+
+size_t state_bytes(const maclab_ctx* h) { return (size_t)(h->g.d + 1) * (size_t)h->g.n * h->elem; }
+
+// Copy the current buffer onto the other one so that both hold the same wall
+// values (wall nodes are never written by the step kernels).
+maclab_status mirror_buffers(maclab_ctx* h) {
+  CUDA_TRY(cudaMemcpyAsync(h->buf[h->cur ^ 1], h->buf[h->cur], state_bytes(h),
+                           cudaMemcpyDeviceToDevice, h->stream),
+           "mirror state");
+  return MACLAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* maclab_status_string(maclab_status s) {
+  switch (s) {
+    case MACLAB_OK: return "MACLAB_OK";
+    case MACLAB_WARN_RLE: return "MACLAB_WARN_RLE: lattice Reynolds number above 1";
+    case MACLAB_ERR_INVALID: return "MACLAB_ERR_INVALID: invalid argument";
+    case MACLAB_ERR_CUDA: return "MACLAB_ERR_CUDA: CUDA error";
+    case MACLAB_ERR_NONFINITE: return "MACLAB_ERR_NONFINITE: non-finite value in the state";
+    case MACLAB_ERR_TIMEOUT: return "MACLAB_ERR_TIMEOUT: bounded device wait expired";
+    case MACLAB_ERR_OOM: return "MACLAB_ERR_OOM: allocation failed";
+    case MACLAB_ERR_UNSUPPORTED: return "MACLAB_ERR_UNSUPPORTED: not supported by this build";
+  }
+  return "unknown maclab_status";
+}
+
+const char* maclab_version(void) { return "maclab sm_103a"; }
+
+const char* maclab_last_error(void) { return g_last_error.c_str(); }
+
+maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {
+  if (!out) return fail(MACLAB_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(MACLAB_ERR_INVALID, "cfg is NULL");
+  if (cfg->lattice != MACLAB_D2Q9 && cfg->lattice != MACLAB_D3Q19)
+    return fail(MACLAB_ERR_INVALID, "unknown lattice");
+  if (cfg->precision < MACLAB_F64 || cfg->precision > MACLAB_F16_STORE)
+    return fail(MACLAB_ERR_INVALID, "unknown precision");
+  const int d = cfg->lattice == MACLAB_D2Q9 ? 2 : 3;
+  const int64_t nx = cfg->dims[0], ny = cfg->dims[1], nz = cfg->dims[2];
+  if (nx < 1 || ny < 1 || nz < 1) return fail(MACLAB_ERR_INVALID, "dims must be >= 1");
+  if (d == 2 && nz != 1) return fail(MACLAB_ERR_INVALID, "D2Q9 needs dims[2] == 1");
+  if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30))
+    return fail(MACLAB_ERR_INVALID, "dimension too large");
+  const int64_t N = nx * ny * nz;
+  if (N > ((int64_t)1 << 40)) return fail(MACLAB_ERR_INVALID, "too many nodes");
+  if (!(cfg->dx > 0) || !(cfg->nu > 0) || !isfinite(cfg->dx) || !isfinite(cfg->nu))
+    return fail(MACLAB_ERR_INVALID, "dx and nu must be finite and > 0");
+  if (cfg->n_wall_ids < 0 || cfg->n_wall_ids > 255)
+    return fail(MACLAB_ERR_INVALID, "n_wall_ids must be in 0..255");
+  if (cfg->n_wall_ids > 0 && !cfg->wall_u)
+    return fail(MACLAB_ERR_INVALID, "wall_u is NULL");
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(cfg->body_force[i])) return fail(MACLAB_ERR_INVALID, "body_force not finite");
+
+  maclab_ctx* h = new (std::nothrow) maclab_ctx();
+  if (!h) return fail(MACLAB_ERR_OOM, "host allocation failed");
+  Geometry& g = h->g;
+  g.lattice = cfg->lattice == MACLAB_D2Q9 ? kD2Q9 : kD3Q19;
+  g.d = d;
+  g.nx = (int)nx;
+  g.ny = (int)ny;
+  g.nz = (int)nz;
+  g.n = N;
+  g.periodic = cfg->periodic & (d == 2 ? 3u : 7u);
+  h->precision = cfg->precision;
+  h->elem = storage_bytes(cfg->precision);
+  h->dx = cfg->dx;
+  h->nu = cfg->nu;
+  h->rho0 = cfg->rho0 > 0 ? cfg->rho0 : 1.0;
+  h->e = 6.0 * cfg->nu / cfg->dx;  // Eq. (6)
+  h->dt = cfg->dx / h->e;
+  h->stream = (cudaStream_t)cfg->stream;
+  cudaGetDevice(&h->device);
+  for (int i = 0; i < 3; ++i) {
+    h->force_phys[i] = i < d ? cfg->body_force[i] : 0.0;
+    h->force_lat[i] = h->force_phys[i] * h->dt / h->e;
+  }
+
+  // wall tables
+  h->n_wall_ids = cfg->n_wall_ids;
+  double umax = 0;
+  for (int k = 0; k < h->n_wall_ids; ++k) {
+    const double r = cfg->wall_rho ? cfg->wall_rho[k] : h->rho0;
+    if (!(r > 0) || !isfinite(r)) { free_ctx(h); return fail(MACLAB_ERR_INVALID, "wall_rho must be > 0"); }
+    h->wall_rho.push_back(r);
+    h->wall_lat.push_back(r / h->rho0 - 1.0);
+    double s = 0;
+    for (int i = 0; i < 3; ++i) {
+      const double v = cfg->wall_u[3 * k + i];
+      if (!isfinite(v)) { free_ctx(h); return fail(MACLAB_ERR_INVALID, "wall_u not finite"); }
+      h->wall_u.push_back(v);
+      h->wall_lat.push_back(i < d ? v / h->e : 0.0);
+      if (i < d) s += v * v;
+    }
+    umax = fmax(umax, sqrt(s));
+  }
+  h->rle = umax * cfg->dx / cfg->nu;
+
+  // node types: validate, classify (none / box / mask)
+  int64_t n_wall = 0;
+  bool box = true;
+  if (cfg->node_type) {
+    for (int64_t z = 0, i = 0; z < nz; ++z)
+      for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x, ++i) {
+          const int k = cfg->node_type[i];
+          if (k > h->n_wall_ids) { free_ctx(h); return fail(MACLAB_ERR_INVALID, "node_type id out of range"); }
+          const bool closed = on_closed_boundary(g, x, y, z);
+          if (closed && k == 0) {
+            free_ctx(h);
+            return fail(MACLAB_ERR_INVALID,
+                        "fluid node on the outer layer of a non-periodic axis (needs a wall)");
+          }
+          if ((k != 0) != closed) box = false;
+          n_wall += k != 0;
+        }
+  } else {
+    for (int i = 0; i < d; ++i)
+      if (!((g.periodic >> i) & 1u)) {
+        free_ctx(h);
+        return fail(MACLAB_ERR_INVALID, "non-periodic axis without a node_type mask");
+      }
+  }
+  h->n_fluid = N - n_wall;
+  g.wall_mode = n_wall == 0 ? kWallNone : (box ? kWallBox : kWallMask);
+
+  DeviceGuard dg(h->device);
+  const size_t sb = state_bytes(h);
+  if (cudaMalloc(&h->buf[0], sb) != cudaSuccess || cudaMalloc(&h->buf[1], sb) != cudaSuccess) {
+    cudaGetLastError();
+    free_ctx(h);
+    return fail(MACLAB_ERR_OOM, "state allocation failed");
+  }
+  if (n_wall > 0) {
+    if (cudaMalloc(&h->d_node_type, (size_t)N) != cudaSuccess ||
+        cudaMalloc(&h->d_wall_lat, sizeof(double) * h->wall_lat.size()) != cudaSuccess) {
+      cudaGetLastError();
+      free_ctx(h);
+      return fail(MACLAB_ERR_OOM, "mask allocation failed");
+    }
+    cudaError_t e1 = cudaMemcpy(h->d_node_type, cfg->node_type, (size_t)N, cudaMemcpyHostToDevice);
+    cudaError_t e2 = cudaMemcpy(h->d_wall_lat, h->wall_lat.data(),
+                                sizeof(double) * h->wall_lat.size(), cudaMemcpyHostToDevice);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      free_ctx(h);
+      return cuda_fail(e1 != cudaSuccess ? e1 : e2, "mask upload");
+    }
+  }
+  g.mask = g.wall_mode == kWallMask ? h->d_node_type : nullptr;
+
+  // rest state with the wall values in place, in both buffers
+  cudaError_t e = cudaMemsetAsync(h->buf[0], 0, sb, h->stream);
+  if (e == cudaSuccess)
+    e = launch_fill_walls(g, h->precision, h->d_node_type, h->d_wall_lat, h->n_wall_ids, h->buf[0],
+                          h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->buf[1], h->buf[0], sb, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    free_ctx(h);
+    return cuda_fail(e, "initial state");
+  }
+  h->kernel = pick_step_kernel(g, h->precision);
+  *out = h;
+  return h->rle > 1.0 ? MACLAB_WARN_RLE : MACLAB_OK;
+}
+
+maclab_status maclab_destroy(maclab_handle h) {
+  if (!h) return MACLAB_OK;
+  DeviceGuard dg(h->device);
+  cudaStreamSynchronize(h->stream);
+  free_ctx(h);
+  return MACLAB_OK;
+}
+
+maclab_status maclab_params(maclab_handle h, double out[8]) {
+  if (!h || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  out[0] = h->e;
+  out[1] = h->dt;
+  out[2] = h->rle;
+  out[3] = h->force_lat[0];
+  out[4] = h->force_lat[1];
+  out[5] = h->force_lat[2];
+  out[6] = (double)h->n_fluid;
+  out[7] = (double)h->steps;
+  return MACLAB_OK;
+}
+
+maclab_status maclab_state_bytes(maclab_handle h, size_t* bytes) {
+  if (!h || !bytes) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  *bytes = state_bytes(h);
+  return MACLAB_OK;
+}
+
+maclab_status maclab_set_state(maclab_handle h, const void* rho, const void* u, int32_t where,
+                               int32_t dtype) {
+  if (!h || !rho || !u) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (dtype != MACLAB_DTYPE_F64 && dtype != MACLAB_DTYPE_F32)
+    return fail(MACLAB_ERR_INVALID, "dtype must be F64 or F32");
+  if (where != MACLAB_HOST && where != MACLAB_DEVICE) return fail(MACLAB_ERR_INVALID, "bad where");
+  DeviceGuard dg(h->device);
+  const size_t es = dtype == MACLAB_DTYPE_F64 ? 8 : 4;
+  const size_t nb = (size_t)h->g.n * es;
+  const void* r = rho;
+  const void* v = u;
+  if (where == MACLAB_HOST) {
+    maclab_status s = ensure_staging(h, nb * (h->g.d + 1));
+    if (s != MACLAB_OK) return s;
+    char* st = (char*)h->d_staging;
+    CUDA_TRY(cudaMemcpyAsync(st, rho, nb, cudaMemcpyHostToDevice, h->stream), "set_state H2D");
+    CUDA_TRY(cudaMemcpyAsync(st + nb, u, nb * h->g.d, cudaMemcpyHostToDevice, h->stream),
+             "set_state H2D");
+    r = st;
+    v = st + nb;
+  }
+  CUDA_TRY(launch_set_physical(h->g, h->precision, r, v, dtype, h->rho0, h->e, h->d_node_type,
+                               h->d_wall_lat, h->n_wall_ids, h->buf[h->cur], h->stream),
+           "set_state kernel");
+  maclab_status s = mirror_buffers(h);
+  if (s != MACLAB_OK) return s;
+  h->steps = 0;
+  if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "set_state sync");
+  return MACLAB_OK;
+}
+
+maclab_status maclab_get_state(maclab_handle h, void* rho, void* u, int32_t where, int32_t dtype) {
+  if (!h || !rho || !u) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (dtype != MACLAB_DTYPE_F64 && dtype != MACLAB_DTYPE_F32)
+    return fail(MACLAB_ERR_INVALID, "dtype must be F64 or F32");
+  if (where != MACLAB_HOST && where != MACLAB_DEVICE) return fail(MACLAB_ERR_INVALID, "bad where");
+  DeviceGuard dg(h->device);
+  const size_t es = dtype == MACLAB_DTYPE_F64 ? 8 : 4;
+  const size_t nb = (size_t)h->g.n * es;
+  if (where == MACLAB_DEVICE) {
+    CUDA_TRY(launch_get_physical(h->g, h->precision, h->buf[h->cur], rho, u, dtype, h->rho0, h->e,
+                                 h->stream),
+             "get_state kernel");
+  } else {
+    maclab_status s = ensure_staging(h, nb * (h->g.d + 1));
+    if (s != MACLAB_OK) return s;
+    char* st = (char*)h->d_staging;
+    CUDA_TRY(launch_get_physical(h->g, h->precision, h->buf[h->cur], st, st + nb, dtype, h->rho0,
+                                 h->e, h->stream),
+             "get_state kernel");
+    CUDA_TRY(cudaMemcpyAsync(rho, st, nb, cudaMemcpyDeviceToHost, h->stream), "get_state D2H");
+    CUDA_TRY(cudaMemcpyAsync(u, st + nb, nb * h->g.d, cudaMemcpyDeviceToHost, h->stream),
+             "get_state D2H");
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "get_state sync");
+  return MACLAB_OK;
+}
+
+maclab_status maclab_get_lattice_state(maclab_handle h, void* state, int32_t where) {
+  if (!h || !state) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (where != MACLAB_HOST && where != MACLAB_DEVICE) return fail(MACLAB_ERR_INVALID, "bad where");
+  DeviceGuard dg(h->device);
+  CUDA_TRY(cudaMemcpyAsync(state, h->buf[h->cur], state_bytes(h),
+                           where == MACLAB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           h->stream),
+           "get_lattice_state");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "get_lattice_state sync");
+  return MACLAB_OK;
+}
+
+maclab_status maclab_set_lattice_state(maclab_handle h, const void* state, int32_t where) {
+  if (!h || !state) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (where != MACLAB_HOST && where != MACLAB_DEVICE) return fail(MACLAB_ERR_INVALID, "bad where");
+  DeviceGuard dg(h->device);
+  CUDA_TRY(cudaMemcpyAsync(h->buf[h->cur], state, state_bytes(h),
+                           where == MACLAB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           h->stream),
+           "set_lattice_state");
+  maclab_status s = mirror_buffers(h);
+  if (s != MACLAB_OK) return s;
+  if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "set_lattice_state sync");
+  return MACLAB_OK;
+}
+
+maclab_status maclab_step(maclab_handle h, int64_t n) {
+  if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  if (n < 0) return fail(MACLAB_ERR_INVALID, "n must be >= 0");
+  DeviceGuard dg(h->device);
+  StepLaunch s;
+  s.g = h->g;
+  s.precision = h->precision;
+  for (int i = 0; i < 3; ++i) s.force[i] = h->force_lat[i];
+  for (int64_t k = 0; k < n; ++k) {
+    s.in = h->buf[h->cur];
+    s.out = h->buf[h->cur ^ 1];
+    CUDA_TRY(launch_step(s, h->stream, h->kernel), "step launch");
+    h->cur ^= 1;
+    h->steps += 1;
+  }
+  return MACLAB_OK;
+}
+
+maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
+  if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  if (kernel == MACLAB_KERNEL_AUTO) {
+    h->kernel = pick_step_kernel(h->g, h->precision);
+    return MACLAB_OK;
+  }
+  if (kernel != MACLAB_KERNEL_REFERENCE && kernel != MACLAB_KERNEL_TILED)
+    return fail(MACLAB_ERR_INVALID, "unknown kernel id");
+  if (!step_kernel_supported(h->g, h->precision, kernel))
+    return fail(MACLAB_ERR_UNSUPPORTED, "kernel does not support this domain");
+  h->kernel = kernel;
+  return MACLAB_OK;
+}
+
+maclab_status maclab_kernel_info(maclab_handle h, int32_t out[4], const char** name) {
+  if (!h || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  const KernelInfo k = describe_step_kernel(h->g, h->precision, h->kernel);
+  out[0] = k.id;
+  out[1] = k.steps_per_launch;
+  out[2] = k.launches;
+  out[3] = k.threads;
+  if (name) *name = k.name;
+  return MACLAB_OK;
+}
+
+maclab_status maclab_sync(maclab_handle h) {
+  if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  DeviceGuard dg(h->device);
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "sync");
+  return MACLAB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// common.cuh -- storage types, loads/stores and the solver context shared by the
+// CUDA translation units of libmaclab.  Internal: not part of the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "maclab.h"
+
+namespace maclab {
+
+// ------------------------------------------------------------------ storage
+
+template <typename S>
+struct Store;  // S = storage type; C = arithmetic type
+
+template <>
+struct Store<double> {
+  using C = double;
+  __device__ __forceinline__ static double ld(const double* p) { return __ldg(p); }
+  __device__ __forceinline__ static void st(double* p, double v) { *p = v; }
+  __device__ __forceinline__ static double from(double v) { return v; }
+  __device__ __forceinline__ static double to(double v) { return v; }
+};
+template <>
+struct Store<float> {
+  using C = float;
+  __device__ __forceinline__ static float ld(const float* p) { return __ldg(p); }
+  __device__ __forceinline__ static void st(float* p, float v) { *p = v; }
+  __device__ __forceinline__ static float from(float v) { return v; }
+  __device__ __forceinline__ static float to(float v) { return v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  using C = float;
+  __device__ __forceinline__ static float ld(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+  }
+  __device__ __forceinline__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  __device__ __forceinline__ static float from(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ __forceinline__ static __nv_bfloat16 to(float v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct Store<__half> {
+  using C = float;
+  __device__ __forceinline__ static float ld(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ __forceinline__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+  __device__ __forceinline__ static float from(__half v) { return __half2float(v); }
+  __device__ __forceinline__ static __half to(float v) { return __float2half_rn(v); }
+};
+
+inline size_t storage_bytes(int precision) {
+  switch (precision) {
+    case MACLAB_F64: return 8;
+    case MACLAB_F32: return 4;
+    case MACLAB_BF16_STORE:
+    case MACLAB_F16_STORE: return 2;
+    default: return 0;
+  }
+}
+
+// ------------------------------------------------------------------ geometry
+
+// How wall nodes are identified inside the step kernels.
+enum WallMode : int {
+  kWallNone = 0,  // all nodes are fluid (fully periodic)
+  kWallBox = 1,   // exactly the first/last layers of every non-periodic axis
+  kWallMask = 2,  // explicit per-node byte mask (nonzero = wall)
+};
+
+struct Geometry {
+  int lattice;        // kD2Q9 / kD3Q19
+  int d;              // 2 or 3
+  int nx, ny, nz;     // nz = 1 for D2Q9
+  int64_t n;          // nx * ny * nz
+  uint32_t periodic;  // bit0 x, bit1 y, bit2 z
+  int wall_mode;      // WallMode
+  const uint8_t* mask;  // device node types (kWallMask), else unused
+};
+
+// Arguments of one step launch (device pointers to whole stored states).
+struct StepLaunch {
+  Geometry g;
+  int precision;
+  const void* in;
+  void* out;
+  double force[3];  // lattice-unit increment added after the division of Eq. (5)
+};
+
+// Defined in step.cu.  Kernel ids follow MACLAB_KERNEL_* of maclab.h.
+struct KernelInfo {
+  int id;                // MACLAB_KERNEL_REFERENCE / MACLAB_KERNEL_TILED
+  int steps_per_launch;  // time steps one launch group advances
+  int launches;          // kernel launches in one group
+  int threads;           // threads per block
+  const char* name;      // static name of the instance
+};
+bool step_kernel_supported(const Geometry& g, int precision, int kernel);
+int pick_step_kernel(const Geometry& g, int precision);
+KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel);
+// Queue one launch group of `kernel` (advances steps_per_launch steps).
+cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel);
+
+// Defined in convert.cu.
+cudaError_t launch_set_physical(const Geometry& g, int precision, const void* rho,
+                                const void* u, int dtype, double rho0, double e,
+                                const uint8_t* node_type, const double* wall_lat,
+                                int n_wall_ids, void* state, cudaStream_t stream);
+cudaError_t launch_get_physical(const Geometry& g, int precision, const void* state,
+                                void* rho, void* u, int dtype, double rho0, double e,
+                                cudaStream_t stream);
+cudaError_t launch_fill_walls(const Geometry& g, int precision, const uint8_t* node_type,
+                              const double* wall_lat, int n_wall_ids, void* state,
+                              cudaStream_t stream);
+
+}  // namespace maclab
+
+// ------------------------------------------------------------------ the handle
+
+struct maclab_ctx {
+  maclab::Geometry g{};
+  int precision = MACLAB_F32;
+  double dx = 0, nu = 0, rho0 = 1, e = 0, dt = 0, rle = 0;
+  double force_phys[3] = {0, 0, 0};
+  double force_lat[3] = {0, 0, 0};
+  int n_wall_ids = 0;
+  std::vector<double> wall_rho, wall_u;  // physical, n_wall_ids and n_wall_ids * 3
+  std::vector<double> wall_lat;          // lattice units, n_wall_ids * 4 (drho, u0, u1, u2)
+  int64_t n_fluid = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  uint8_t* d_node_type = nullptr;  // device copy of the node types (if any walls)
+  double* d_wall_lat = nullptr;    // device copy of wall_lat
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;                     // buf[cur] holds the current state
+  size_t elem = 4;                 // bytes per stored value
+  int64_t steps = 0;
+  int kernel = MACLAB_KERNEL_REFERENCE;
+  void* d_staging = nullptr;       // device staging for host set/get
+  size_t staging_cap = 0;
+};

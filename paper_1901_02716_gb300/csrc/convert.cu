@@ -1,0 +1,139 @@
+// convert.cu -- unit maps at the boundary of the library.
+//
+// Physical (rho, u) <-> stored lattice state (drho = rho / rho0 - 1, ut = u / e)
+// with e = 6 nu / dx (Eq. (6)).  Wall nodes take their wall id's values
+// (procedure step (iv): physical variables are retained on walls).  The maps
+// are computed in FP64 and rounded once to the storage type.
+
+#include "common.cuh"
+
+namespace maclab {
+
+template <typename T>
+__device__ __forceinline__ double ld_user(const T* p, int64_t i) {
+  return (double)p[i];
+}
+
+template <typename S, typename T>
+__global__ void set_physical_k(int d, int64_t N, const T* __restrict__ rho, const T* __restrict__ u,
+                               double inv_rho0, double inv_e, const uint8_t* __restrict__ node_type,
+                               const double* __restrict__ wall_lat, int n_wall_ids,
+                               S* __restrict__ state) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = node_type ? (int)node_type[i] : 0;
+    if (k > 0 && k <= n_wall_ids) {
+      const double* w = wall_lat + 4 * (k - 1);
+      state[i] = Store<S>::to(typename Store<S>::C(w[0]));
+      for (int c = 0; c < d; ++c) state[(1 + c) * N + i] = Store<S>::to(typename Store<S>::C(w[1 + c]));
+    } else {
+      state[i] = Store<S>::to(typename Store<S>::C(ld_user(rho, i) * inv_rho0 - 1.0));
+      for (int c = 0; c < d; ++c)
+        state[(1 + c) * N + i] = Store<S>::to(typename Store<S>::C(ld_user(u, c * N + i) * inv_e));
+    }
+  }
+}
+
+template <typename S>
+__global__ void fill_walls_k(int d, int64_t N, const uint8_t* __restrict__ node_type,
+                             const double* __restrict__ wall_lat, int n_wall_ids,
+                             S* __restrict__ state) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)node_type[i];
+    if (k > 0 && k <= n_wall_ids) {
+      const double* w = wall_lat + 4 * (k - 1);
+      state[i] = Store<S>::to(typename Store<S>::C(w[0]));
+      for (int c = 0; c < d; ++c) state[(1 + c) * N + i] = Store<S>::to(typename Store<S>::C(w[1 + c]));
+    }
+  }
+}
+
+template <typename S, typename T>
+__global__ void get_physical_k(int d, int64_t N, const S* __restrict__ state, double rho0, double e,
+                               T* __restrict__ rho, T* __restrict__ u) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    rho[i] = (T)(rho0 * (1.0 + (double)Store<S>::from(state[i])));
+    for (int c = 0; c < d; ++c) u[c * N + i] = (T)(e * (double)Store<S>::from(state[(1 + c) * N + i]));
+  }
+}
+
+static unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 4096) b = 4096;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename S>
+static cudaError_t set_t(const Geometry& g, const void* rho, const void* u, int dtype, double rho0,
+                         double e, const uint8_t* nt, const double* wl, int nw, void* state,
+                         cudaStream_t st) {
+  if (dtype == MACLAB_DTYPE_F64)
+    set_physical_k<S, double><<<grid_for(g.n), 256, 0, st>>>(
+        g.d, g.n, (const double*)rho, (const double*)u, 1.0 / rho0, 1.0 / e, nt, wl, nw, (S*)state);
+  else
+    set_physical_k<S, float><<<grid_for(g.n), 256, 0, st>>>(
+        g.d, g.n, (const float*)rho, (const float*)u, 1.0 / rho0, 1.0 / e, nt, wl, nw, (S*)state);
+  return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t get_t(const Geometry& g, const void* state, void* rho, void* u, int dtype,
+                         double rho0, double e, cudaStream_t st) {
+  if (dtype == MACLAB_DTYPE_F64)
+    get_physical_k<S, double><<<grid_for(g.n), 256, 0, st>>>(g.d, g.n, (const S*)state, rho0, e,
+                                                            (double*)rho, (double*)u);
+  else
+    get_physical_k<S, float><<<grid_for(g.n), 256, 0, st>>>(g.d, g.n, (const S*)state, rho0, e,
+                                                           (float*)rho, (float*)u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_physical(const Geometry& g, int precision, const void* rho, const void* u,
+                                int dtype, double rho0, double e, const uint8_t* nt,
+                                const double* wl, int nw, void* state, cudaStream_t st) {
+  switch (precision) {
+    case MACLAB_F64: return set_t<double>(g, rho, u, dtype, rho0, e, nt, wl, nw, state, st);
+    case MACLAB_F32: return set_t<float>(g, rho, u, dtype, rho0, e, nt, wl, nw, state, st);
+    case MACLAB_BF16_STORE:
+      return set_t<__nv_bfloat16>(g, rho, u, dtype, rho0, e, nt, wl, nw, state, st);
+    case MACLAB_F16_STORE: return set_t<__half>(g, rho, u, dtype, rho0, e, nt, wl, nw, state, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_get_physical(const Geometry& g, int precision, const void* state, void* rho,
+                                void* u, int dtype, double rho0, double e, cudaStream_t st) {
+  switch (precision) {
+    case MACLAB_F64: return get_t<double>(g, state, rho, u, dtype, rho0, e, st);
+    case MACLAB_F32: return get_t<float>(g, state, rho, u, dtype, rho0, e, st);
+    case MACLAB_BF16_STORE: return get_t<__nv_bfloat16>(g, state, rho, u, dtype, rho0, e, st);
+    case MACLAB_F16_STORE: return get_t<__half>(g, state, rho, u, dtype, rho0, e, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fill_walls(const Geometry& g, int precision, const uint8_t* nt, const double* wl,
+                              int nw, void* state, cudaStream_t st) {
+  if (!nt) return cudaSuccess;
+  switch (precision) {
+    case MACLAB_F64:
+      fill_walls_k<double><<<grid_for(g.n), 256, 0, st>>>(g.d, g.n, nt, wl, nw, (double*)state);
+      break;
+    case MACLAB_F32:
+      fill_walls_k<float><<<grid_for(g.n), 256, 0, st>>>(g.d, g.n, nt, wl, nw, (float*)state);
+      break;
+    case MACLAB_BF16_STORE:
+      fill_walls_k<__nv_bfloat16><<<grid_for(g.n), 256, 0, st>>>(g.d, g.n, nt, wl, nw,
+                                                                 (__nv_bfloat16*)state);
+      break;
+    case MACLAB_F16_STORE:
+      fill_walls_k<__half><<<grid_for(g.n), 256, 0, st>>>(g.d, g.n, nt, wl, nw, (__half*)state);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace maclab

@@ -1,0 +1,371 @@
+"""Thin ctypes binding of libmaclab (the C ABI in include/maclab.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  The functions keep the C names (``maclab_create``, ``maclab_step``,
+...) and raise ``MacLABError`` on a negative status; ``Solver`` wraps a handle.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or device);
+the binding passes their data pointers and the matching ``where`` flag.  There
+is no CPU fallback: if the library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+D2Q9, D3Q19 = 0, 1
+F64, F32, BF16_STORE, F16_STORE = 0, 1, 2, 3
+HOST, DEVICE = 0, 1
+DTYPE_F64, DTYPE_F32 = 0, 1
+OK, WARN_RLE = 0, 1
+KERNEL_AUTO, KERNEL_REFERENCE, KERNEL_TILED = 0, 1, 2
+ERR_INVALID, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_OOM, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+
+PRECISION_NAMES = {"f64": F64, "f32": F32, "bf16": BF16_STORE, "f16": F16_STORE}
+STORAGE_NP = {F64: np.float64, F32: np.float32, BF16_STORE: np.uint16, F16_STORE: np.float16}
+
+
+class MacLABError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+class maclab_config(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("dims", ctypes.c_int64 * 3),
+        ("dx", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("periodic", ctypes.c_uint32),
+        ("node_type", ctypes.c_void_p),
+        ("n_wall_ids", ctypes.c_int32),
+        ("wall_rho", ctypes.c_void_p),
+        ("wall_u", ctypes.c_void_p),
+        ("body_force", ctypes.c_double * 3),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+# name -> (restype, argtypes); every symbol include/maclab.h declares
+_H = ctypes.c_void_p
+_VP = ctypes.c_void_p
+_S = ctypes.c_int32
+SIGNATURES = {
+    "maclab_create": (_S, [ctypes.POINTER(maclab_config), ctypes.POINTER(_H)]),
+    "maclab_destroy": (_S, [_H]),
+    "maclab_params": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
+    "maclab_set_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
+    "maclab_get_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
+    "maclab_state_bytes": (_S, [_H, ctypes.POINTER(ctypes.c_size_t)]),
+    "maclab_get_lattice_state": (_S, [_H, _VP, ctypes.c_int32]),
+    "maclab_set_lattice_state": (_S, [_H, _VP, ctypes.c_int32]),
+    "maclab_step": (_S, [_H, ctypes.c_int64]),
+    "maclab_sync": (_S, [_H]),
+    "maclab_set_kernel": (_S, [_H, ctypes.c_int32]),
+    "maclab_kernel_info": (_S, [_H, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_char_p)]),
+    "maclab_status_string": (ctypes.c_char_p, [_S]),
+    "maclab_version": (ctypes.c_char_p, []),
+    "maclab_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load libmaclab.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            if build_if_missing:
+                _build.build()
+            else:
+                raise MacLABError(ERR_UNSUPPORTED,
+                                  f"{path} is missing: build it with "
+                                  "paper_1901_02716_gb300._build.build() (no CPU fallback)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, what):
+    if status < 0:
+        L = lib()
+        msg = L.maclab_last_error().decode() or L.maclab_status_string(status).decode()
+        raise MacLABError(status, f"{what}: {L.maclab_status_string(status).decode()} ({msg})")
+    return status
+
+
+def _ptr(a):
+    """(pointer, where) of a numpy array or torch tensor."""
+    if a is None:
+        return None, HOST
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _dtype_code(a):
+    if isinstance(a, np.ndarray):
+        dt = a.dtype
+        if dt == np.float64:
+            return DTYPE_F64
+        if dt == np.float32:
+            return DTYPE_F32
+    else:
+        import torch
+        if a.dtype == torch.float64:
+            return DTYPE_F64
+        if a.dtype == torch.float32:
+            return DTYPE_F32
+    raise TypeError("fields must be float64 or float32")
+
+
+# ---------------------------------------------------------------- C names
+
+def maclab_create(cfg: maclab_config):
+    h = _H()
+    s = lib().maclab_create(ctypes.byref(cfg), ctypes.byref(h))
+    _check(s, "maclab_create")
+    return h, s
+
+
+def maclab_destroy(h):
+    return _check(lib().maclab_destroy(h), "maclab_destroy")
+
+
+def maclab_params(h):
+    out = (ctypes.c_double * 8)()
+    _check(lib().maclab_params(h, out), "maclab_params")
+    return list(out)
+
+
+def maclab_set_state(h, rho, u):
+    pr, wr = _ptr(rho)
+    pu, wu = _ptr(u)
+    if wr != wu:
+        raise ValueError("rho and u must live in the same memory")
+    dt = _dtype_code(rho)
+    if _dtype_code(u) != dt:
+        raise ValueError("rho and u must have the same dtype")
+    return _check(lib().maclab_set_state(h, pr, pu, wr, dt), "maclab_set_state")
+
+
+def maclab_get_state(h, rho, u):
+    pr, wr = _ptr(rho)
+    pu, wu = _ptr(u)
+    if wr != wu:
+        raise ValueError("rho and u must live in the same memory")
+    dt = _dtype_code(rho)
+    if _dtype_code(u) != dt:
+        raise ValueError("rho and u must have the same dtype")
+    return _check(lib().maclab_get_state(h, pr, pu, wr, dt), "maclab_get_state")
+
+
+def maclab_state_bytes(h):
+    n = ctypes.c_size_t()
+    _check(lib().maclab_state_bytes(h, ctypes.byref(n)), "maclab_state_bytes")
+    return n.value
+
+
+def maclab_get_lattice_state(h, state):
+    p, w = _ptr(state)
+    return _check(lib().maclab_get_lattice_state(h, p, w), "maclab_get_lattice_state")
+
+
+def maclab_set_lattice_state(h, state):
+    p, w = _ptr(state)
+    return _check(lib().maclab_set_lattice_state(h, p, w), "maclab_set_lattice_state")
+
+
+def maclab_step(h, n):
+    return _check(lib().maclab_step(h, int(n)), "maclab_step")
+
+
+def maclab_sync(h):
+    return _check(lib().maclab_sync(h), "maclab_sync")
+
+
+def maclab_set_kernel(h, kernel):
+    return _check(lib().maclab_set_kernel(h, int(kernel)), "maclab_set_kernel")
+
+
+def maclab_kernel_info(h):
+    out = (ctypes.c_int32 * 4)()
+    name = ctypes.c_char_p()
+    _check(lib().maclab_kernel_info(h, out, ctypes.byref(name)), "maclab_kernel_info")
+    return {"kernel": out[0], "steps_per_launch": out[1], "launches_per_group": out[2],
+            "threads": out[3], "name": name.value.decode() if name.value else ""}
+
+
+def maclab_status_string(s):
+    return lib().maclab_status_string(int(s)).decode()
+
+
+def maclab_version():
+    return lib().maclab_version().decode()
+
+
+# ---------------------------------------------------------------- solver object
+
+def make_config(lattice, dims, dx, nu, precision=F32, periodic=0, node_type=None, wall_rho=None,
+                wall_u=None, body_force=None, rho0=1.0, stream=None):
+    """Build a maclab_config; returns (cfg, keepalive) -- keep the second alive."""
+    d = 2 if lattice == D2Q9 else 3
+    dims3 = list(dims) + [1] * (3 - len(dims))
+    cfg = maclab_config()
+    cfg.lattice = lattice
+    cfg.precision = PRECISION_NAMES.get(precision, precision) if isinstance(precision, str) else precision
+    cfg.dims = (ctypes.c_int64 * 3)(*dims3)
+    cfg.dx, cfg.nu, cfg.rho0 = float(dx), float(nu), float(rho0)
+    cfg.periodic = int(periodic)
+    keep = []
+    if node_type is not None:
+        nt = np.ascontiguousarray(node_type, dtype=np.uint8)
+        if nt.size != int(np.prod(dims3)):
+            raise ValueError("node_type has the wrong size")
+        keep.append(nt)
+        cfg.node_type = nt.ctypes.data
+    if wall_u is not None:
+        wu = np.zeros((len(wall_u), 3))
+        wu[:, :d] = np.asarray(wall_u, dtype=np.float64).reshape(len(wall_u), -1)[:, :d]
+        keep.append(wu)
+        cfg.wall_u = wu.ctypes.data
+        cfg.n_wall_ids = len(wall_u)
+        if wall_rho is not None:
+            wr = np.ascontiguousarray(wall_rho, dtype=np.float64)
+            keep.append(wr)
+            cfg.wall_rho = wr.ctypes.data
+    bf = [0.0, 0.0, 0.0]
+    if body_force is not None:
+        for i, v in enumerate(body_force):
+            bf[i] = float(v)
+    cfg.body_force = (ctypes.c_double * 3)(*bf)
+    cfg.stream = stream
+    return cfg, keep
+
+
+class Solver:
+    """One MacLAB domain on the GPU (owns a maclab handle)."""
+
+    def __init__(self, lattice, dims, dx, nu, precision=F32, periodic=0, node_type=None,
+                 wall_rho=None, wall_u=None, body_force=None, rho0=1.0, stream=None):
+        cfg, keep = make_config(lattice, dims, dx, nu, precision, periodic, node_type, wall_rho,
+                                wall_u, body_force, rho0, stream)
+        self.handle, self.create_status = maclab_create(cfg)
+        self.lattice = lattice
+        self.d = 2 if lattice == D2Q9 else 3
+        self.dims = tuple(dims)
+        self.grid = tuple(reversed(self.dims if self.d == 3 else self.dims[:2]))
+        self.precision = cfg.precision
+        self.dx, self.nu, self.rho0 = dx, nu, rho0
+
+    @classmethod
+    def from_case(cls, case, precision=F32, dx=1.0, nu=1.0 / 6.0, stream=None):
+        """Solver for an ``inputs.Case`` given in lattice units.
+
+        With the defaults dx = 1 and nu = 1/6, Eq. (6) gives e = 1 and dt = 1, so
+        physical and lattice units coincide; the case's force is then passed as
+        the physical body acceleration.
+        """
+        e = 6.0 * nu / dx
+        dt = dx / e
+        bf = None if case.force is None else [f * e / dt for f in case.force]
+        wu = None if case.wall_u is None else np.asarray(case.wall_u) * e
+        s = cls(case.lattice, case.dims, dx, nu, precision, case.periodic, case.node_type,
+                case.wall_rho, wu, bf, stream=stream)
+        s.set_state(np.ascontiguousarray(case.rho, dtype=np.float64),
+                    np.ascontiguousarray(case.u * e, dtype=np.float64))
+        return s
+
+    def close(self):
+        if getattr(self, "handle", None):
+            maclab_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def params(self):
+        p = maclab_params(self.handle)
+        return {"e": p[0], "dt": p[1], "R_le": p[2], "force_lattice": p[3:6], "n_fluid": int(p[6]),
+                "steps": int(p[7])}
+
+    def set_state(self, rho, u):
+        maclab_set_state(self.handle, rho, u)
+
+    def get_state(self, dtype=np.float64):
+        rho = np.empty(self.grid, dtype=dtype)
+        u = np.empty((self.d,) + self.grid, dtype=dtype)
+        maclab_get_state(self.handle, rho, u)
+        return rho, u
+
+    def get_state_into(self, rho, u):
+        maclab_get_state(self.handle, rho, u)
+
+    def state_bytes(self):
+        return maclab_state_bytes(self.handle)
+
+    def get_lattice_state(self, out=None):
+        if out is None:
+            out = np.empty(self.state_bytes(), dtype=np.uint8)
+        maclab_get_lattice_state(self.handle, out)
+        return out
+
+    def set_lattice_state(self, state):
+        maclab_set_lattice_state(self.handle, state)
+
+    def step(self, n=1):
+        maclab_step(self.handle, n)
+
+    def set_kernel(self, kernel):
+        maclab_set_kernel(self.handle, kernel)
+
+    def kernel_info(self):
+        return maclab_kernel_info(self.handle)
+
+    def kernel_tag(self):
+        return self.kernel_info()["name"]
+
+    def steps_per_launch(self):
+        return self.kernel_info()["steps_per_launch"]
+
+    def launches_per_step(self):
+        """Kernel launches per MacLAB time step (a fraction under time blocking)."""
+        info = self.kernel_info()
+        return info["launches_per_group"] / info["steps_per_launch"]
+
+    def sync(self):
+        maclab_sync(self.handle)

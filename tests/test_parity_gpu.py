@@ -1,0 +1,167 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 CPU oracle.
+
+Same seeded inputs on both sides; element-wise comparison.  Bars:
+  * FP64 storage: <= 1e-12 relative (max norm) on rho and u;
+  * FP32 storage: <= 1e-5 relative L2 on u, <= 1e-6 absolute on rho;
+  * BF16 / FP16 storage (FP32 arithmetic): the error is stated, not held to
+    1e-5: <= 2e-2 (bf16) and <= 3e-3 (f16) relative L2 on u after 7 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1901_02716_gb300 import inputs
+from paper_1901_02716_gb300 import maclab as M
+
+pytestmark = pytest.mark.gpu
+
+D2, D3 = inputs.D2Q9, inputs.D3Q19
+TOL_U = {M.F64: 1e-12, M.F32: 1e-5, M.BF16_STORE: 2e-2, M.F16_STORE: 3e-3}
+TOL_R = {M.F64: 1e-12, M.F32: 1e-6, M.BF16_STORE: 1e-3, M.F16_STORE: 2e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1901_02716_gb300 import _build
+    _build.build()
+
+
+def rel_l2(a, b):
+    nb = np.sqrt(np.sum(b * b))
+    return np.sqrt(np.sum((a - b) ** 2)) / (nb if nb > 0 else 1.0)
+
+
+def run_both(case, precision, steps, kernel=None):
+    s = M.Solver.from_case(case, precision)
+    if kernel is not None:
+        s.set_kernel(kernel)
+    s.step(steps)
+    r_g, u_g = s.get_state()
+    s.close()
+    r_o, u_o = orc.step(case.lattice, case.rho, case.u, case.periodic, wall=case.wall_mask,
+                        force=case.force, nsteps=steps)
+    return r_g, u_g, r_o, u_o
+
+
+def assert_parity(r_g, u_g, r_o, u_o, precision):
+    if precision == M.F64:
+        assert np.abs(r_g - r_o).max() <= TOL_R[precision] * np.abs(r_o).max()
+        assert np.abs(u_g - u_o).max() <= TOL_U[precision] * max(np.abs(u_o).max(), 1e-300)
+    else:
+        assert np.abs(r_g - r_o).max() <= TOL_R[precision]
+        assert rel_l2(u_g, u_o) <= TOL_U[precision]
+
+
+CASES = [
+    # lattice, dims, periodic, walls
+    (D2, (17, 13), 0b11, "none"),
+    (D2, (33, 20), 0b00, "box"),
+    (D2, (40, 23), 0b01, "mixed"),
+    (D3, (9, 7, 5), 0b111, "none"),
+    (D3, (12, 10, 9), 0b000, "box"),
+    (D3, (16, 9, 11), 0b101, "mixed"),
+]
+
+
+@pytest.mark.parametrize("lat,dims,periodic,walls", CASES)
+@pytest.mark.parametrize("precision", [M.F64, M.F32])
+@pytest.mark.parametrize("steps", [1, 7])
+def test_random_fields(lat, dims, periodic, walls, precision, steps):
+    case = inputs.random_case(lat, dims, periodic, seed=31, u_amp=0.08, rho_amp=0.02,
+                              walls=walls, force=tuple([1e-4] * len(dims)))
+    assert_parity(*run_both(case, precision, steps), precision)
+
+
+@pytest.mark.parametrize("lat,dims,periodic,walls", [CASES[1], CASES[4]])
+@pytest.mark.parametrize("precision", [M.BF16_STORE, M.F16_STORE])
+def test_16bit_storage(lat, dims, periodic, walls, precision):
+    case = inputs.random_case(lat, dims, periodic, seed=32, u_amp=0.08, rho_amp=0.02,
+                              walls=walls)
+    assert_parity(*run_both(case, precision, 7), precision)
+
+
+@pytest.mark.parametrize("precision", [M.F64, M.F32])
+def test_tgv2d_1000_steps(precision):
+    """Taylor-Green vortex, D2Q9 64x64 periodic, u0 = 0.02, 1000 steps."""
+    case = inputs.tgv2d(64, 0.02)
+    r_g, u_g, r_o, u_o = run_both(case, precision, 1000)
+    assert_parity(r_g, u_g, r_o, u_o, precision)
+    k = 2 * math.pi / 64
+    amp = np.sum(u_g * case.u) / np.sum(case.u * case.u)
+    assert amp == pytest.approx(((1 + 2 * math.cos(k)) / 3) ** 1000, rel=1e-5)
+
+
+def test_physical_units_roundtrip():
+    """Couette set-up of Test 1 in SI units (dx = 0.02, nu = 0.001): the library's
+    unit map (e = 6 nu / dx) must agree with the oracle's."""
+    dx, nu = 0.02, 0.001
+    e, dt = orc.params(dx, nu)
+    case = inputs.channel2d(20, 51, u_top=0.1 / e)
+    s = M.Solver(M.D2Q9, case.dims, dx, nu, M.F64, case.periodic, case.node_type, case.wall_rho,
+                 np.asarray(case.wall_u) * e)
+    p = s.params
+    assert p["e"] == pytest.approx(e, rel=1e-15) and p["dt"] == pytest.approx(dt, rel=1e-15)
+    g = inputs.rng(40)
+    rho = 1 + 0.01 * g.uniform(-1, 1, size=case.grid)
+    u = 0.02 * g.uniform(-1, 1, size=(2,) + case.grid)
+    s.set_state(rho, u)
+    s.step(5)
+    r_g, u_g = s.get_state()
+    rl, ul = orc.to_lattice(*inputs.place_walls(rho, u / e, case.node_type, case.wall_rho,
+                                                 case.wall_u), dx, nu)
+    rl, ul = orc.step(D2, rl, ul, case.periodic, wall=case.wall_mask, nsteps=5)
+    r_o, u_o = orc.to_physical(rl, ul, dx, nu)
+    assert np.abs(r_g - r_o).max() < 1e-13
+    assert np.abs(u_g - u_o).max() < 1e-13 * e
+
+
+@pytest.mark.parametrize("lat,dims,periodic,walls", [
+    (D2, (1, 1), 0b11, "none"), (D3, (1, 1, 1), 0b111, "none"), (D2, (2, 2), 0b11, "none"),
+    (D2, (3, 3), 0b00, "box"), (D3, (3, 3, 3), 0b000, "box"), (D2, (2, 5), 0b00, "box"),
+    (D3, (1, 4, 3), 0b001, "box")])
+def test_degenerate_sizes(lat, dims, periodic, walls):
+    case = inputs.random_case(lat, dims, periodic, seed=33, u_amp=0.05, walls=walls)
+    assert_parity(*run_both(case, M.F64, 3), M.F64)
+
+
+def test_zero_steps_and_resume_bit_identical():
+    case = inputs.random_case(D3, (12, 11, 10), 0b011, seed=34, walls="box")
+    s = M.Solver.from_case(case, M.F32)
+    s.step(0)
+    r0, u0 = s.get_state()
+    assert np.abs(u0 - case.u).max() < 1e-7
+    s.step(4)
+    snap = s.get_lattice_state()
+    s.step(5)
+    ref = s.get_lattice_state().copy()
+    s.set_lattice_state(snap)
+    s.step(5)
+    assert np.array_equal(s.get_lattice_state(), ref)
+    s.close()
+
+
+def test_device_pointers_through_torch():
+    torch = pytest.importorskip("torch")
+    case = inputs.random_case(D2, (64, 48), 0b11, seed=35)
+    s = M.Solver(D2, case.dims, 1.0, 1 / 6, M.F32, case.periodic)
+    rho = torch.tensor(case.rho, dtype=torch.float32, device="cuda")
+    u = torch.tensor(case.u, dtype=torch.float32, device="cuda")
+    s.set_state(rho, u)
+    s.step(3)
+    r2 = torch.empty_like(rho)
+    u2 = torch.empty_like(u)
+    s.get_state_into(r2, u2)
+    r_o, u_o = orc.step(D2, case.rho, case.u, case.periodic, nsteps=3)
+    assert rel_l2(u2.double().cpu().numpy(), u_o) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("lat,n", [(D3, 128), (D2, 1024)])
+def test_full_size_box_walls(lat, n):
+    """At the benchmark sizes (128^3 D3Q19, 1024^2 D2Q9), FP32, in the launch
+    configuration the benchmark uses: whole fields against the oracle."""
+    dims = (n,) * (3 if lat == D3 else 2)
+    case = inputs.random_case(lat, dims, 0, seed=36, u_amp=0.08, rho_amp=0.02, walls="box")
+    assert_parity(*run_both(case, M.F32, 3), M.F32)
