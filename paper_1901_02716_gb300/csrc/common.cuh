@@ -89,6 +89,7 @@ struct StepLaunch {
   const void* in;
   void* out;
   double force[3];  // lattice-unit increment added after the division of Eq. (5)
+  int ty = 0, tz = 0;  // tile shape of the tiled kernel (0 = default)
 };
 
 // Defined in step.cu.  Kernel ids follow MACLAB_KERNEL_* of maclab.h.
@@ -104,6 +105,11 @@ int pick_step_kernel(const Geometry& g, int precision);
 KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel);
 // Queue one launch group of `kernel` (advances steps_per_launch steps).
 cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel);
+
+// Defined in step_tiled.cu.
+bool tiled_supported(const Geometry& g, int precision, int ty, int tz);
+cudaError_t launch_tiled(const StepLaunch& s, cudaStream_t stream, int ty, int tz);
+int tiled_threads(const Geometry& g, int precision, int ty, int tz);
 
 // Defined in convert.cu.
 cudaError_t launch_set_physical(const Geometry& g, int precision, const void* rho,
@@ -140,6 +146,7 @@ struct maclab_ctx {
   size_t elem = 4;                 // bytes per stored value
   int64_t steps = 0;
   int kernel = MACLAB_KERNEL_REFERENCE;
+  int ty = 0, tz = 0;              // tiled-kernel shape (0 = default)
   void* d_staging = nullptr;       // device staging for host set/get
   size_t staging_cap = 0;
 };

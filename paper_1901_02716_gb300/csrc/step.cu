@@ -15,7 +15,8 @@
 // Kernels here:
 //  * step_naive: one thread per node, the Q upstream states read straight from
 //    global memory.  Any size; the reference the faster kernel is tested on.
-//  * step_tiled: see the comment above it.
+//  * step_tiled (step_tiled.cu): strips of 4 nodes per thread, a march along
+//    the slowest axis, equilibria exchanged through shared memory.
 
 #include "common.cuh"
 #include "lattice.cuh"
@@ -117,9 +118,9 @@ static cudaError_t launch_naive_lat(const StepLaunch& s, cudaStream_t stream) {
 }
 
 bool step_kernel_supported(const Geometry& g, int precision, int kernel) {
-  (void)g;
-  (void)precision;
-  return kernel == MACLAB_KERNEL_REFERENCE;
+  if (kernel == MACLAB_KERNEL_REFERENCE) return true;
+  if (kernel == MACLAB_KERNEL_TILED) return tiled_supported(g, precision, 0, 0);
+  return false;
 }
 
 int pick_step_kernel(const Geometry& g, int precision) {
@@ -127,18 +128,24 @@ int pick_step_kernel(const Geometry& g, int precision) {
                                                                  : MACLAB_KERNEL_REFERENCE;
 }
 
-static const char* naive_name(const Geometry& g, int precision) {
-  static const char* names[2][4] = {
-      {"step_naive<D2Q9,f64>", "step_naive<D2Q9,f32>", "step_naive<D2Q9,bf16>",
-       "step_naive<D2Q9,f16>"},
-      {"step_naive<D3Q19,f64>", "step_naive<D3Q19,f32>", "step_naive<D3Q19,bf16>",
-       "step_naive<D3Q19,f16>"}};
-  return names[g.lattice == kD2Q9 ? 0 : 1][precision & 3];
+static const char* kernel_name(const Geometry& g, int precision, int kernel) {
+  static const char* names[2][2][4] = {
+      {{"step_naive<D2Q9,f64>", "step_naive<D2Q9,f32>", "step_naive<D2Q9,bf16>",
+        "step_naive<D2Q9,f16>"},
+       {"step_naive<D3Q19,f64>", "step_naive<D3Q19,f32>", "step_naive<D3Q19,bf16>",
+        "step_naive<D3Q19,f16>"}},
+      {{"step_tiled<D2Q9,f64>", "step_tiled<D2Q9,f32>", "step_tiled<D2Q9,bf16>",
+        "step_tiled<D2Q9,f16>"},
+       {"step_tiled<D3Q19,f64>", "step_tiled<D3Q19,f32>", "step_tiled<D3Q19,bf16>",
+        "step_tiled<D3Q19,f16>"}}};
+  return names[kernel == MACLAB_KERNEL_TILED ? 1 : 0][g.lattice == kD2Q9 ? 0 : 1][precision & 3];
 }
 
 KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel) {
-  (void)kernel;
-  return KernelInfo{MACLAB_KERNEL_REFERENCE, 1, 1, 256, naive_name(g, precision)};
+  if (kernel == MACLAB_KERNEL_TILED)
+    return KernelInfo{MACLAB_KERNEL_TILED, 1, 1, tiled_threads(g, precision, 0, 0),
+                      kernel_name(g, precision, kernel)};
+  return KernelInfo{MACLAB_KERNEL_REFERENCE, 1, 1, 256, kernel_name(g, precision, kernel)};
 }
 
 cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel) {
@@ -146,6 +153,8 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel) {
     case MACLAB_KERNEL_REFERENCE:
       return s.g.lattice == kD2Q9 ? launch_naive_lat<kD2Q9>(s, stream)
                                   : launch_naive_lat<kD3Q19>(s, stream);
+    case MACLAB_KERNEL_TILED:
+      return launch_tiled(s, stream, s.ty, s.tz);
     default:
       return cudaErrorInvalidValue;
   }
