@@ -140,9 +140,16 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * serve this domain (then the handle keeps its previous choice). */
 maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel);
 
+/* Tile shape of the tiled kernel: ty rows of y per block (3D only) and tz
+ * planes of the slowest axis per block; 0 keeps the library's default.
+ * MACLAB_ERR_UNSUPPORTED if no built instance has that shape for this domain
+ * (the previous shape is kept). */
+maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz);
+
 /* Describe the kernel in use: out[0] = kernel id (REFERENCE or TILED),
  * out[1] = time steps advanced per launch, out[2] = kernel launches per
- * launch group, out[3] = threads per block.  *name (may be NULL) receives a
+ * launch group, out[3] = threads per block (out[3] = 0 and out[1..2] = 1 for
+ * the reference kernel's grid-stride launch of 256-thread blocks).  *name (may be NULL) receives a
  * static string naming the kernel instance. */
 maclab_status maclab_kernel_info(maclab_handle h, int32_t out[4], const char **name);
 

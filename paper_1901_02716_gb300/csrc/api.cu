@@ -145,6 +145,8 @@ maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {
   g.nz = (int)nz;
   g.n = N;
   g.periodic = cfg->periodic & (d == 2 ? 3u : 7u);
+  g.ilv = (nx % 4 == 0) ? 1 : 0;
+  g.hx = (int)(nx / 2);
   h->precision = cfg->precision;
   h->elem = storage_bytes(cfg->precision);
   h->dx = cfg->dx;
@@ -221,7 +223,12 @@ maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {
       free_ctx(h);
       return fail(MACLAB_ERR_OOM, "mask allocation failed");
     }
-    cudaError_t e1 = cudaMemcpy(h->d_node_type, cfg->node_type, (size_t)N, cudaMemcpyHostToDevice);
+    // device copy in storage order
+    std::vector<uint8_t> nt_mem((size_t)N);
+    for (int64_t row = 0; row < N / nx; ++row)
+      for (int64_t x = 0; x < nx; ++x)
+        nt_mem[(size_t)(row * nx + mem_x(g, (int)x))] = cfg->node_type[row * nx + x];
+    cudaError_t e1 = cudaMemcpy(h->d_node_type, nt_mem.data(), (size_t)N, cudaMemcpyHostToDevice);
     cudaError_t e2 = cudaMemcpy(h->d_wall_lat, h->wall_lat.data(),
                                 sizeof(double) * h->wall_lat.size(), cudaMemcpyHostToDevice);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -367,6 +374,8 @@ maclab_status maclab_step(maclab_handle h, int64_t n) {
   s.g = h->g;
   s.precision = h->precision;
   for (int i = 0; i < 3; ++i) s.force[i] = h->force_lat[i];
+  s.ty = h->ty;
+  s.tz = h->tz;
   for (int64_t k = 0; k < n; ++k) {
     s.in = h->buf[h->cur];
     s.out = h->buf[h->cur ^ 1];
@@ -391,9 +400,19 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
   return MACLAB_OK;
 }
 
+maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz) {
+  if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  if (ty < 0 || tz < 0 || tz > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad tile shape");
+  if (!tiled_supported(h->g, h->precision, ty, tz))
+    return fail(MACLAB_ERR_UNSUPPORTED, "no built tiled instance has this shape");
+  h->ty = ty;
+  h->tz = tz;
+  return MACLAB_OK;
+}
+
 maclab_status maclab_kernel_info(maclab_handle h, int32_t out[4], const char** name) {
   if (!h || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
-  const KernelInfo k = describe_step_kernel(h->g, h->precision, h->kernel);
+  const KernelInfo k = describe_step_kernel(h->g, h->precision, h->kernel, h->ty, h->tz);
   out[0] = k.id;
   out[1] = k.steps_per_launch;
   out[2] = k.launches;

@@ -79,8 +79,21 @@ struct Geometry {
   int64_t n;          // nx * ny * nz
   uint32_t periodic;  // bit0 x, bit1 y, bit2 z
   int wall_mode;      // WallMode
-  const uint8_t* mask;  // device node types (kWallMask), else unused
+  const uint8_t* mask;  // device node types in storage order (kWallMask), else unused
+  int ilv;            // 1: the two halves of every x row are interleaved in storage
+  int hx;             // nx / 2 (used when ilv)
 };
+
+// Storage position within an x row of logical x, and its inverse.  With ilv
+// (nx % 4 == 0) node x is stored at 2 (x mod H) + [x >= H], H = nx / 2, so that
+// four consecutive stored values are the node pairs (x, x + H), (x + 1, x + 1 + H)
+// the tiled kernel computes on; otherwise storage order is x itself.
+__host__ __device__ inline int mem_x(const Geometry& g, int x) {
+  return g.ilv ? (x < g.hx ? 2 * x : 2 * (x - g.hx) + 1) : x;
+}
+__host__ __device__ inline int log_x(const Geometry& g, int m) {
+  return g.ilv ? (m >> 1) + (m & 1) * g.hx : m;
+}
 
 // Arguments of one step launch (device pointers to whole stored states).
 struct StepLaunch {
@@ -102,7 +115,7 @@ struct KernelInfo {
 };
 bool step_kernel_supported(const Geometry& g, int precision, int kernel);
 int pick_step_kernel(const Geometry& g, int precision);
-KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel);
+KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, int ty, int tz);
 // Queue one launch group of `kernel` (advances steps_per_launch steps).
 cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel);
 

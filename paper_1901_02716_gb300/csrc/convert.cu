@@ -3,7 +3,8 @@
 // Physical (rho, u) <-> stored lattice state (drho = rho / rho0 - 1, ut = u / e)
 // with e = 6 nu / dx (Eq. (6)).  Wall nodes take their wall id's values
 // (procedure step (iv): physical variables are retained on walls).  The maps
-// are computed in FP64 and rounded once to the storage type.
+// are computed in FP64 and rounded once to the storage type.  User arrays are
+// in logical order; the state and the device node-type copy in storage order.
 
 #include "common.cuh"
 
@@ -14,8 +15,14 @@ __device__ __forceinline__ double ld_user(const T* p, int64_t i) {
   return (double)p[i];
 }
 
+// User arrays are in logical order (x fastest); the state in storage order.
+__device__ __forceinline__ int64_t user_index(const Geometry& g, int64_t m) {
+  const int64_t row = m / g.nx;
+  return row * g.nx + log_x(g, (int)(m - row * g.nx));
+}
+
 template <typename S, typename T>
-__global__ void set_physical_k(int d, int64_t N, const T* __restrict__ rho, const T* __restrict__ u,
+__global__ void set_physical_k(Geometry g, int d, int64_t N, const T* __restrict__ rho, const T* __restrict__ u,
                                double inv_rho0, double inv_e, const uint8_t* __restrict__ node_type,
                                const double* __restrict__ wall_lat, int n_wall_ids,
                                S* __restrict__ state) {
@@ -27,9 +34,10 @@ __global__ void set_physical_k(int d, int64_t N, const T* __restrict__ rho, cons
       state[i] = Store<S>::to(typename Store<S>::C(w[0]));
       for (int c = 0; c < d; ++c) state[(1 + c) * N + i] = Store<S>::to(typename Store<S>::C(w[1 + c]));
     } else {
-      state[i] = Store<S>::to(typename Store<S>::C(ld_user(rho, i) * inv_rho0 - 1.0));
+      const int64_t j = user_index(g, i);
+      state[i] = Store<S>::to(typename Store<S>::C(ld_user(rho, j) * inv_rho0 - 1.0));
       for (int c = 0; c < d; ++c)
-        state[(1 + c) * N + i] = Store<S>::to(typename Store<S>::C(ld_user(u, c * N + i) * inv_e));
+        state[(1 + c) * N + i] = Store<S>::to(typename Store<S>::C(ld_user(u, c * N + j) * inv_e));
     }
   }
 }
@@ -50,12 +58,13 @@ __global__ void fill_walls_k(int d, int64_t N, const uint8_t* __restrict__ node_
 }
 
 template <typename S, typename T>
-__global__ void get_physical_k(int d, int64_t N, const S* __restrict__ state, double rho0, double e,
-                               T* __restrict__ rho, T* __restrict__ u) {
+__global__ void get_physical_k(Geometry g, int d, int64_t N, const S* __restrict__ state, double rho0,
+                               double e, T* __restrict__ rho, T* __restrict__ u) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    rho[i] = (T)(rho0 * (1.0 + (double)Store<S>::from(state[i])));
-    for (int c = 0; c < d; ++c) u[c * N + i] = (T)(e * (double)Store<S>::from(state[(1 + c) * N + i]));
+    const int64_t j = user_index(g, i);
+    rho[j] = (T)(rho0 * (1.0 + (double)Store<S>::from(state[i])));
+    for (int c = 0; c < d; ++c) u[c * N + j] = (T)(e * (double)Store<S>::from(state[(1 + c) * N + i]));
   }
 }
 
@@ -71,10 +80,10 @@ static cudaError_t set_t(const Geometry& g, const void* rho, const void* u, int 
                          cudaStream_t st) {
   if (dtype == MACLAB_DTYPE_F64)
     set_physical_k<S, double><<<grid_for(g.n), 256, 0, st>>>(
-        g.d, g.n, (const double*)rho, (const double*)u, 1.0 / rho0, 1.0 / e, nt, wl, nw, (S*)state);
+        g, g.d, g.n, (const double*)rho, (const double*)u, 1.0 / rho0, 1.0 / e, nt, wl, nw, (S*)state);
   else
     set_physical_k<S, float><<<grid_for(g.n), 256, 0, st>>>(
-        g.d, g.n, (const float*)rho, (const float*)u, 1.0 / rho0, 1.0 / e, nt, wl, nw, (S*)state);
+        g, g.d, g.n, (const float*)rho, (const float*)u, 1.0 / rho0, 1.0 / e, nt, wl, nw, (S*)state);
   return cudaGetLastError();
 }
 
@@ -82,10 +91,10 @@ template <typename S>
 static cudaError_t get_t(const Geometry& g, const void* state, void* rho, void* u, int dtype,
                          double rho0, double e, cudaStream_t st) {
   if (dtype == MACLAB_DTYPE_F64)
-    get_physical_k<S, double><<<grid_for(g.n), 256, 0, st>>>(g.d, g.n, (const S*)state, rho0, e,
+    get_physical_k<S, double><<<grid_for(g.n), 256, 0, st>>>(g, g.d, g.n, (const S*)state, rho0, e,
                                                             (double*)rho, (double*)u);
   else
-    get_physical_k<S, float><<<grid_for(g.n), 256, 0, st>>>(g.d, g.n, (const S*)state, rho0, e,
+    get_physical_k<S, float><<<grid_for(g.n), 256, 0, st>>>(g, g.d, g.n, (const S*)state, rho0, e,
                                                            (float*)rho, (float*)u);
   return cudaGetLastError();
 }

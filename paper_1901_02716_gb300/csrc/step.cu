@@ -1,6 +1,7 @@
 // step.cu -- the MacLAB time step (Eqs. (2), (4), (5)) on the GPU.
 //
-// Stored state: drho = rho / rho0 - 1 and ut = u / e, structure of arrays.
+// Stored state: drho = rho / rho0 - 1 and ut = u / e, structure of arrays in
+// storage order (see mem_x in common.cuh).
 // With rho = 1 + drho and P_a = 3 c_a.ut + 9/2 (c_a.ut)^2 - 3/2 ut.ut, the
 // equilibrium of Eq. (2) is f_a^eq = w_a (1 + drho + (1 + drho) P_a).  The
 // constant w_a sums to 1 over a and w_a c_a sums to 0, so Eqs. (4)-(5) become
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(256) step_naive(Geometry g, const S* __restric
   const int64_t N = g.n;
   for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < N;
        node += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(node % g.nx);
+    const int x = log_x(g, (int)(node % g.nx));
     const int y = (int)((node / g.nx) % g.ny);
     const int z = (int)(node / ((int64_t)g.nx * g.ny));
     if (is_wall_node<LAT>(g, x, y, z, node)) continue;
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) step_naive(Geometry g, const S* __restric
       const int xs = wrap(x - L::c(a, 0), g.nx);
       const int ys = wrap(y - L::c(a, 1), g.ny);
       const int zs = D == 3 ? wrap(z - L::c(a, 2), g.nz) : 0;
-      const int64_t s = ((int64_t)zs * g.ny + ys) * g.nx + xs;
+      const int64_t s = ((int64_t)zs * g.ny + ys) * g.nx + mem_x(g, xs);
       const C r = Store<S>::ld(in + s);
       C u[3] = {Store<S>::ld(in + N + s), Store<S>::ld(in + 2 * N + s),
                 D == 3 ? Store<S>::ld(in + 3 * N + s) : C(0)};
@@ -141,9 +142,9 @@ static const char* kernel_name(const Geometry& g, int precision, int kernel) {
   return names[kernel == MACLAB_KERNEL_TILED ? 1 : 0][g.lattice == kD2Q9 ? 0 : 1][precision & 3];
 }
 
-KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel) {
+KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, int ty, int tz) {
   if (kernel == MACLAB_KERNEL_TILED)
-    return KernelInfo{MACLAB_KERNEL_TILED, 1, 1, tiled_threads(g, precision, 0, 0),
+    return KernelInfo{MACLAB_KERNEL_TILED, 1, 1, tiled_threads(g, precision, ty, tz),
                       kernel_name(g, precision, kernel)};
   return KernelInfo{MACLAB_KERNEL_REFERENCE, 1, 1, 256, kernel_name(g, precision, kernel)};
 }

@@ -69,6 +69,7 @@ SIGNATURES = {
     "maclab_step": (_S, [_H, ctypes.c_int64]),
     "maclab_sync": (_S, [_H]),
     "maclab_set_kernel": (_S, [_H, ctypes.c_int32]),
+    "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "maclab_kernel_info": (_S, [_H, ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_char_p)]),
     "maclab_status_string": (ctypes.c_char_p, [_S]),
@@ -212,6 +213,10 @@ def maclab_set_kernel(h, kernel):
     return _check(lib().maclab_set_kernel(h, int(kernel)), "maclab_set_kernel")
 
 
+def maclab_set_tile(h, ty, tz):
+    return _check(lib().maclab_set_tile(h, int(ty), int(tz)), "maclab_set_tile")
+
+
 def maclab_kernel_info(h):
     out = (ctypes.c_int32 * 4)()
     name = ctypes.c_char_p()
@@ -352,6 +357,9 @@ class Solver:
 
     def set_kernel(self, kernel):
         maclab_set_kernel(self.handle, kernel)
+
+    def set_tile(self, ty=0, tz=0):
+        maclab_set_tile(self.handle, ty, tz)
 
     def kernel_info(self):
         return maclab_kernel_info(self.handle)

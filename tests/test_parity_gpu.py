@@ -85,8 +85,8 @@ TILED_CASES = [
     (D3, (8, 8, 5), 0b111, "none"),
     (D3, (12, 10, 9), 0b000, "box"),
     (D3, (16, 9, 19), 0b101, "mixed"),
-    (D3, (32, 12, 7), 0b011, "box"),
-    (D3, (4, 6, 3), 0b111, "none"),
+    (D3, (32, 16, 7), 0b011, "box"),
+    (D3, (4, 8, 3), 0b111, "none"),
     (D3, (20, 13, 17), 0b100, "mixed"),
 ]
 
@@ -98,7 +98,13 @@ def test_tiled_kernel(lat, dims, periodic, walls, precision, steps):
     case = inputs.random_case(lat, dims, periodic, seed=37, u_amp=0.08, rho_amp=0.02,
                               walls=walls, force=tuple([-2e-4] * len(dims)))
     s = M.Solver.from_case(case, precision)
-    s.set_kernel(M.KERNEL_TILED)
+    try:
+        s.set_kernel(M.KERNEL_TILED)
+    except M.MacLABError as e:
+        s.close()
+        # FP32 is built for every width; FP64 / 16-bit storage only for some
+        assert precision != M.F32 and e.status == M.ERR_UNSUPPORTED
+        pytest.skip("no tiled instance of this width for this storage type")
     assert s.kernel_info()["kernel"] == M.KERNEL_TILED
     s.close()
     assert_parity(*run_both(case, precision, steps, kernel=M.KERNEL_TILED), precision)
@@ -175,8 +181,8 @@ def test_physical_units_roundtrip():
     s.set_state(rho, u)
     s.step(5)
     r_g, u_g = s.get_state()
-    rl, ul = orc.to_lattice(*inputs.place_walls(rho, u / e, case.node_type, case.wall_rho,
-                                                 case.wall_u), dx, nu)
+    # the same start in lattice units (rho0 = 1): walls take their lattice values
+    rl, ul = inputs.place_walls(rho, u / e, case.node_type, case.wall_rho, case.wall_u)
     rl, ul = orc.step(D2, rl, ul, case.periodic, wall=case.wall_mask, nsteps=5)
     r_o, u_o = orc.to_physical(rl, ul, dx, nu)
     assert np.abs(r_g - r_o).max() < 1e-13
