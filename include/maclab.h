@@ -153,6 +153,23 @@ maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz);
  * static string naming the kernel instance. */
 maclab_status maclab_kernel_info(maclab_handle h, int32_t out[4], const char **name);
 
+/* FP64 diagnostics over the fluid nodes (walls excluded), physical units:
+ * out[0] mass, sum of rho; out[1] kinetic energy, sum of rho |u|^2 / 2;
+ * out[2..4] momentum, sum of rho u_i (out[4] = 0 in 2D); out[5] steady
+ * residual ||u^n - u^(n-1)||_2 / ||u^n||_2 (lattice units; -1 when the
+ * previous step's state is not held, e.g. right after a set_state);
+ * out[6] largest |u| / e (lattice Mach number); out[7] number of non-finite
+ * stored values.  Mass and momentum are invariants of the periodic update
+ * (Eq. (15)).  Synchronises the stream.  Returns MACLAB_ERR_NONFINITE (with
+ * out filled) if out[7] > 0. */
+maclab_status maclab_diagnostics(maclab_handle h, double out[8]);
+
+/* Capture maclab_step's launches in CUDA graphs of `steps` time steps each
+ * (rounded up to an even count; 0 turns graphs off, the default is 32).
+ * Graphs are built on first use and rebuilt after any change of kernel or
+ * tile shape. */
+maclab_status maclab_set_graph(maclab_handle h, int32_t steps);
+
 /* Run the handle's stream to completion and report any CUDA error. */
 maclab_status maclab_sync(maclab_handle h);
 

@@ -54,8 +54,20 @@ bool on_closed_boundary(const Geometry& g, int64_t x, int64_t y, int64_t z) {
   return false;
 }
 
+void drop_graphs(maclab_ctx* h) {
+  for (int c = 0; c < 2; ++c)
+    if (h->graph_exec[c]) {
+      cudaGraphExecDestroy(h->graph_exec[c]);
+      h->graph_exec[c] = nullptr;
+    }
+}
+
 void free_ctx(maclab_ctx* h) {
   if (!h) return;
+  drop_graphs(h);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  cudaFree(h->d_partial);
+  cudaFree(h->d_diag);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->d_node_type);
@@ -211,7 +223,10 @@ maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {
 
   DeviceGuard dg(h->device);
   const size_t sb = state_bytes(h);
-  if (cudaMalloc(&h->buf[0], sb) != cudaSuccess || cudaMalloc(&h->buf[1], sb) != cudaSuccess) {
+  h->diag_nblocks = diag_blocks(N);
+  if (cudaMalloc(&h->buf[0], sb) != cudaSuccess || cudaMalloc(&h->buf[1], sb) != cudaSuccess ||
+      cudaMalloc(&h->d_partial, sizeof(double) * kDiagOut * h->diag_nblocks) != cudaSuccess ||
+      cudaMalloc(&h->d_diag, sizeof(double) * kDiagOut) != cudaSuccess) {
     cudaGetLastError();
     free_ctx(h);
     return fail(MACLAB_ERR_OOM, "state allocation failed");
@@ -309,6 +324,7 @@ maclab_status maclab_set_state(maclab_handle h, const void* rho, const void* u, 
   maclab_status s = mirror_buffers(h);
   if (s != MACLAB_OK) return s;
   h->steps = 0;
+  h->prev_valid = false;
   if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "set_state sync");
   return MACLAB_OK;
 }
@@ -362,7 +378,46 @@ maclab_status maclab_set_lattice_state(maclab_handle h, const void* state, int32
            "set_lattice_state");
   maclab_status s = mirror_buffers(h);
   if (s != MACLAB_OK) return s;
+  h->prev_valid = false;
   if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "set_lattice_state sync");
+  return MACLAB_OK;
+}
+
+static StepLaunch step_launch(const maclab_ctx* h, int from) {
+  StepLaunch s;
+  s.g = h->g;
+  s.precision = h->precision;
+  for (int i = 0; i < 3; ++i) s.force[i] = h->force_lat[i];
+  s.ty = h->ty;
+  s.tz = h->tz;
+  s.in = h->buf[from];
+  s.out = h->buf[from ^ 1];
+  return s;
+}
+
+// Capture graph_steps launches starting from buffer c (graph_steps is even, so
+// the graph ends on buffer c again).
+static maclab_status build_graph(maclab_ctx* h, int c) {
+  if (!h->capture_stream) {
+    if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "capture stream");
+  }
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < h->graph_steps && err == cudaSuccess; ++k)
+    err = launch_step(step_launch(h, c ^ (k & 1)), h->capture_stream, h->kernel);
+  cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &graph);
+  if (err != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(err != cudaSuccess ? err : e2, "graph capture");
+  }
+  err = cudaGraphInstantiate(&h->graph_exec[c], graph, 0);
+  cudaGraphDestroy(graph);
+  if (err != cudaSuccess) {
+    h->graph_exec[c] = nullptr;
+    return cuda_fail(err, "graph instantiate");
+  }
   return MACLAB_OK;
 }
 
@@ -370,24 +425,60 @@ maclab_status maclab_step(maclab_handle h, int64_t n) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (n < 0) return fail(MACLAB_ERR_INVALID, "n must be >= 0");
   DeviceGuard dg(h->device);
-  StepLaunch s;
-  s.g = h->g;
-  s.precision = h->precision;
-  for (int i = 0; i < 3; ++i) s.force[i] = h->force_lat[i];
-  s.ty = h->ty;
-  s.tz = h->tz;
+  while (h->graph_steps > 0 && n >= h->graph_steps) {
+    if (!h->graph_exec[h->cur]) {
+      maclab_status s = build_graph(h, h->cur);
+      if (s != MACLAB_OK) return s;
+    }
+    CUDA_TRY(cudaGraphLaunch(h->graph_exec[h->cur], h->stream), "graph launch");
+    h->steps += h->graph_steps;
+    n -= h->graph_steps;
+    h->prev_valid = true;
+  }
   for (int64_t k = 0; k < n; ++k) {
-    s.in = h->buf[h->cur];
-    s.out = h->buf[h->cur ^ 1];
-    CUDA_TRY(launch_step(s, h->stream, h->kernel), "step launch");
+    CUDA_TRY(launch_step(step_launch(h, h->cur), h->stream, h->kernel), "step launch");
     h->cur ^= 1;
     h->steps += 1;
+    h->prev_valid = true;
   }
+  return MACLAB_OK;
+}
+
+maclab_status maclab_set_graph(maclab_handle h, int32_t steps) {
+  if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  if (steps < 0 || steps > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad graph length");
+  DeviceGuard dg(h->device);
+  drop_graphs(h);
+  h->graph_steps = steps + (steps & 1);
+  return MACLAB_OK;
+}
+
+maclab_status maclab_diagnostics(maclab_handle h, double out[8]) {
+  if (!h || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  DeviceGuard dg(h->device);
+  CUDA_TRY(launch_diagnostics(h->g, h->precision, h->buf[h->cur],
+                              h->prev_valid ? h->buf[h->cur ^ 1] : nullptr, h->d_partial,
+                              h->diag_nblocks, h->d_diag, h->stream),
+           "diagnostics kernel");
+  double r[kDiagOut];
+  CUDA_TRY(cudaMemcpyAsync(r, h->d_diag, sizeof(r), cudaMemcpyDeviceToHost, h->stream), "diagnostics D2H");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "diagnostics sync");
+  const double nf = (double)h->n_fluid;
+  out[0] = h->rho0 * (nf + r[0]);
+  out[1] = 0.5 * h->rho0 * h->e * h->e * r[1];
+  out[2] = h->rho0 * h->e * r[2];
+  out[3] = h->rho0 * h->e * r[3];
+  out[4] = h->rho0 * h->e * r[4];
+  out[5] = h->prev_valid ? (r[6] > 0 ? sqrt(r[5] / r[6]) : 0.0) : -1.0;
+  out[6] = r[7];
+  out[7] = r[8];
+  if (r[8] > 0) return fail(MACLAB_ERR_NONFINITE, "non-finite values in the state");
   return MACLAB_OK;
 }
 
 maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  drop_graphs(h);
   if (kernel == MACLAB_KERNEL_AUTO) {
     h->kernel = pick_step_kernel(h->g, h->precision);
     return MACLAB_OK;
@@ -405,6 +496,7 @@ maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz) {
   if (ty < 0 || tz < 0 || tz > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad tile shape");
   if (!tiled_supported(h->g, h->precision, ty, tz))
     return fail(MACLAB_ERR_UNSUPPORTED, "no built tiled instance has this shape");
+  drop_graphs(h);
   h->ty = ty;
   h->tz = tz;
   return MACLAB_OK;

@@ -124,6 +124,12 @@ bool tiled_supported(const Geometry& g, int precision, int ty, int tz);
 cudaError_t launch_tiled(const StepLaunch& s, cudaStream_t stream, int ty, int tz);
 int tiled_threads(const Geometry& g, int precision, int ty, int tz);
 
+// Defined in reduce.cu.
+constexpr int kDiagOut = 9;
+int diag_blocks(int64_t n);
+cudaError_t launch_diagnostics(const Geometry& g, int precision, const void* cur, const void* prev,
+                               double* partial, int nblocks, double* out, cudaStream_t st);
+
 // Defined in convert.cu.
 cudaError_t launch_set_physical(const Geometry& g, int precision, const void* rho,
                                 const void* u, int dtype, double rho0, double e,
@@ -162,4 +168,12 @@ struct maclab_ctx {
   int ty = 0, tz = 0;              // tiled-kernel shape (0 = default)
   void* d_staging = nullptr;       // device staging for host set/get
   size_t staging_cap = 0;
+  bool prev_valid = false;         // buf[cur ^ 1] holds the state one step back
+  double* d_partial = nullptr;     // diagnostics scratch (per-block partial sums)
+  double* d_diag = nullptr;        // diagnostics result (kDiagOut doubles)
+  int diag_nblocks = 0;
+  // CUDA graphs of graph_steps steps, one per starting buffer
+  int graph_steps = 32;
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  cudaStream_t capture_stream = nullptr;
 };

@@ -70,6 +70,8 @@ SIGNATURES = {
     "maclab_sync": (_S, [_H]),
     "maclab_set_kernel": (_S, [_H, ctypes.c_int32]),
     "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
+    "maclab_set_graph": (_S, [_H, ctypes.c_int32]),
+    "maclab_diagnostics": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
     "maclab_kernel_info": (_S, [_H, ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_char_p)]),
     "maclab_status_string": (ctypes.c_char_p, [_S]),
@@ -217,6 +219,19 @@ def maclab_set_tile(h, ty, tz):
     return _check(lib().maclab_set_tile(h, int(ty), int(tz)), "maclab_set_tile")
 
 
+def maclab_set_graph(h, steps):
+    return _check(lib().maclab_set_graph(h, int(steps)), "maclab_set_graph")
+
+
+def maclab_diagnostics(h, raise_nonfinite=True):
+    out = (ctypes.c_double * 8)()
+    s = lib().maclab_diagnostics(h, out)
+    if s != ERR_NONFINITE or raise_nonfinite:
+        _check(s, "maclab_diagnostics")
+    return {"mass": out[0], "kinetic": out[1], "momentum": list(out[2:5]), "residual": out[5],
+            "max_u_lattice": out[6], "nonfinite": int(out[7]), "status": s}
+
+
 def maclab_kernel_info(h):
     out = (ctypes.c_int32 * 4)()
     name = ctypes.c_char_p()
@@ -357,6 +372,12 @@ class Solver:
 
     def set_kernel(self, kernel):
         maclab_set_kernel(self.handle, kernel)
+
+    def set_graph(self, steps):
+        maclab_set_graph(self.handle, steps)
+
+    def diagnostics(self, raise_nonfinite=True):
+        return maclab_diagnostics(self.handle, raise_nonfinite)
 
     def set_tile(self, ty=0, tz=0):
         maclab_set_tile(self.handle, ty, tz)
