@@ -170,6 +170,37 @@ maclab_status maclab_diagnostics(maclab_handle h, double out[8]);
  * tile shape. */
 maclab_status maclab_set_graph(maclab_handle h, int32_t steps);
 
+/* Diagnostics sums without any device allocation.  (Not part of the method:
+ * the paper has no counterpart.)  For callers that cannot allocate device
+ * memory while they run -- for example a host loop that reserved all device
+ * memory for its own pool up front, or code that may not block on an
+ * allocation.  The per-block partial sums live in a fixed array of 288 KiB
+ * that every GPU loading the library holds until the process exits; one call
+ * reduces at most 33,554,432 nodes (larger n_nodes: MACLAB_ERR_INVALID).
+ *
+ * state: device, (d + 1) * n_nodes stored values of the precision's storage
+ *   type, drho then the d lattice velocity components, in any node order
+ *   (e.g. a buffer filled by maclab_get_lattice_state).
+ * prev_state: device, the same layout one step earlier, or NULL (then the
+ *   residual sums are 0).
+ * exclude: device, n_nodes bytes in the same node order, nonzero = leave the
+ *   node out (walls), or NULL.
+ * out_sums: device, 9 doubles written with the raw lattice-unit sums over the
+ *   included nodes: [0] sum drho, [1] sum rho |u|^2, [2..4] sum rho u_i,
+ *   [5] sum |u - u_prev|^2, [6] sum |u|^2, [7] max |u|, [8] non-finite count.
+ * stream: cudaStream_t (NULL = default stream); the call is asynchronous.
+ *
+ * The first call on a device looks up the array's address on that device
+ * (with that device current); make that first call before any stream capture.
+ * Every call on a device reuses the same array: calls that overlap on the GPU
+ * race.  Nothing in it needs clearing between calls (each call writes the
+ * entries it reads).  No cudaMalloc, cudaFree or other allocating routine is
+ * called.  Errors: MACLAB_ERR_INVALID (arguments, size), MACLAB_ERR_CUDA. */
+maclab_status maclab_diagnostics_noalloc(int32_t lattice, int32_t precision, int64_t n_nodes,
+                                         const void *state, const void *prev_state,
+                                         const uint8_t *exclude, double *out_sums,
+                                         void *stream);
+
 /* Run the handle's stream to completion and report any CUDA error. */
 maclab_status maclab_sync(maclab_handle h);
 

@@ -102,6 +102,8 @@ maclab_status mirror_buffers(maclab_ctx* h) {
 
 }  // namespace
 
+void maclab::record_error(const char* msg) { g_last_error = msg; }
+
 extern "C" {
 
 const char* maclab_status_string(maclab_status s) {

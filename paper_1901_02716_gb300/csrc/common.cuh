@@ -124,6 +124,9 @@ bool tiled_supported(const Geometry& g, int precision, int ty, int tz);
 cudaError_t launch_tiled(const StepLaunch& s, cudaStream_t stream, int ty, int tz);
 int tiled_threads(const Geometry& g, int precision, int ty, int tz);
 
+// Defined in api.cu: message returned by maclab_last_error on this thread.
+void record_error(const char* msg);
+
 // Defined in reduce.cu.
 constexpr int kDiagOut = 9;
 int diag_blocks(int64_t n);

@@ -14,6 +14,8 @@
 // Two kernels: per-block partials into a scratch array, then one block folds
 // the partials.
 
+#include <mutex>
+
 #include "common.cuh"
 #include "lattice.cuh"
 
@@ -148,4 +150,91 @@ cudaError_t launch_diagnostics(const Geometry& g, int precision, const void* cur
   return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+//
+// For callers that cannot allocate device memory while they run (for example a
+// host loop that reserved all device memory for its own pool up front, or code
+// that may not block on an allocation): the same two kernels, with the
+// per-block partial sums in a fixed array that the library reserves when it is
+// loaded, instead of a buffer owned by a handle.
+//
+// Each block folds a fixed run of kNoAllocNodesPerBlock nodes, so the partials
+// a call needs grow with the node count; the array holds kNoAllocMaxBlocks of
+// them, which bounds one call to kNoAllocMaxNodes nodes.
+
+constexpr int64_t kNoAllocMaxBlocks = 4096;
+constexpr int64_t kNoAllocNodesPerBlock = 8192;
+constexpr int64_t kNoAllocMaxNodes = kNoAllocMaxBlocks * kNoAllocNodesPerBlock;  // 33,554,432
+
+// Held by every GPU that loads the library, until the process exits
+// (4096 x 9 doubles = 288 KiB).  Every call overwrites the entries it reads
+// before reading them, so nothing here has to start at zero; calls that
+// overlap on the GPU share it and race.
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * kDiagSlots];
+
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[64] = {};  // device address of g_noalloc_partials, per device
+}  // namespace
+
+// Address of the array on the current device: looked up once per device (the
+// first call on a device does it) with that device current.
+static cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace maclab
+
+using namespace maclab;
+
+extern "C" maclab_status maclab_diagnostics_noalloc(int32_t lattice, int32_t precision,
+                                                    int64_t n_nodes, const void* state,
+                                                    const void* prev_state,
+                                                    const uint8_t* exclude, double* out_sums,
+                                                    void* stream) {
+  auto err = [](maclab_status s, const char* m) {
+    record_error(m);
+    return s;
+  };
+  if (lattice != MACLAB_D2Q9 && lattice != MACLAB_D3Q19) return err(MACLAB_ERR_INVALID, "unknown lattice");
+  if (precision < MACLAB_F64 || precision > MACLAB_F16_STORE)
+    return err(MACLAB_ERR_INVALID, "unknown precision");
+  if (!state || !out_sums) return err(MACLAB_ERR_INVALID, "state and out_sums are required");
+  if (n_nodes < 1) return err(MACLAB_ERR_INVALID, "n_nodes must be >= 1");
+  if (n_nodes > kNoAllocMaxNodes)
+    return err(MACLAB_ERR_INVALID,
+               "n_nodes exceeds the 33554432 nodes the fixed scratch of "
+               "maclab_diagnostics_noalloc can reduce in one call");
+  double* partials = nullptr;
+  cudaError_t e = noalloc_scratch(&partials);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return err(MACLAB_ERR_CUDA, "cudaGetSymbolAddress of the fixed scratch failed");
+  }
+  Geometry g{};
+  g.lattice = lattice == MACLAB_D2Q9 ? kD2Q9 : kD3Q19;
+  g.d = lattice == MACLAB_D2Q9 ? 2 : 3;
+  g.nx = 1;
+  g.ny = 1;
+  g.nz = 1;
+  g.n = n_nodes;
+  g.wall_mode = exclude ? kWallMask : kWallNone;
+  g.mask = exclude;
+  const int nblocks = (int)((n_nodes + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock);
+  e = launch_diagnostics(g, precision, state, prev_state, partials, nblocks, out_sums,
+                         (cudaStream_t)stream);
+  if (e != cudaSuccess) return err(MACLAB_ERR_CUDA, cudaGetErrorString(e));
+  return MACLAB_OK;
+}

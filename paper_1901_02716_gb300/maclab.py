@@ -72,6 +72,8 @@ SIGNATURES = {
     "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "maclab_set_graph": (_S, [_H, ctypes.c_int32]),
     "maclab_diagnostics": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
+    "maclab_diagnostics_noalloc": (_S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _VP, _VP,
+                                        _VP, _VP, _VP]),
     "maclab_kernel_info": (_S, [_H, ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_char_p)]),
     "maclab_status_string": (ctypes.c_char_p, [_S]),
@@ -230,6 +232,15 @@ def maclab_diagnostics(h, raise_nonfinite=True):
         _check(s, "maclab_diagnostics")
     return {"mass": out[0], "kinetic": out[1], "momentum": list(out[2:5]), "residual": out[5],
             "max_u_lattice": out[6], "nonfinite": int(out[7]), "status": s}
+
+
+def maclab_diagnostics_noalloc(lattice, precision, n_nodes, state, prev_state, exclude, out_sums,
+                               stream=None):
+    """Raw FP64 sums into ``out_sums`` (device, 9 doubles) with no device
+    allocation; all array arguments are device pointers (ints) or None."""
+    return _check(lib().maclab_diagnostics_noalloc(int(lattice), int(precision), int(n_nodes),
+                                                   state, prev_state, exclude, out_sums, stream),
+                  "maclab_diagnostics_noalloc")
 
 
 def maclab_kernel_info(h):
