@@ -134,7 +134,7 @@ def traffic_from_profiles(kernel_tag, source_hash):
 
 def step_source_hash():
     h = hashlib.sha256()
-    for f in ("step.cu", "lattice.cuh", "common.cuh"):
+    for f in ("step.cu", "step_tiled.cuh", "step_tiled.cu", "lattice.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1901_02716_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
