@@ -170,6 +170,55 @@ maclab_status maclab_diagnostics(maclab_handle h, double out[8]);
  * tile shape. */
 maclab_status maclab_set_graph(maclab_handle h, int32_t steps);
 
+/* ---------------------------------------------------------------- adjoint
+ * Reverse mode of maclab_step, for gradients of a loss on the final state
+ * with respect to the initial fields, the wall values, the body force and nu.
+ * Not in the paper; it is the chain rule applied to Eqs. (2), (4), (5) (see
+ * adjoint.cu).  Adjoint arrays hold (d + 1) * N values of the arithmetic type
+ * (double for MACLAB_F64, float otherwise) -- the adjoint of drho, then of
+ * the d lattice velocity components -- in the same node order as the raw
+ * state of maclab_get_lattice_state.  All array arguments of these calls are
+ * DEVICE pointers; the calls run on the handle's stream. */
+
+/* Size in bytes of one adjoint array. */
+maclab_status maclab_adjoint_bytes(maclab_handle h, size_t *bytes);
+
+/* One reverse step.  state_n: raw state at step n; state_np1: the raw state
+ * one maclab_step later; lam_np1: adjoint of state_np1; lam_n (output, must
+ * not alias lam_np1): adjoint of state_n.  grad_force (d doubles, or NULL)
+ * accumulates the gradient with respect to the lattice-unit body-force
+ * increment.  The first call allocates a scratch array of the adjoint size
+ * owned by the handle. */
+maclab_status maclab_adjoint_step(maclab_handle h, const void *state_n, const void *state_np1,
+                                  const void *lam_np1, void *lam_n, double *grad_force);
+
+/* Seed the reverse pass: the gradients of the loss with respect to the
+ * physical output fields rho (N values) and u (d * N values, logical order;
+ * either may be NULL = zero) of dtype, for the raw final state state_T, give
+ * the adjoint array lam_T.  *dot_T receives sum over nodes of lam_u . u
+ * (lattice units), which maclab_adjoint_finish needs for dL/dnu.
+ * Synchronises the stream. */
+maclab_status maclab_adjoint_seed(maclab_handle h, const void *grad_rho, const void *grad_u,
+                                  int32_t dtype, const void *state_T, void *lam_T, double *dot_T);
+
+/* Finish the reverse pass from lam_0, the adjoint of the raw initial state
+ * state_0 (the state maclab_set_state produced).  Outputs (any may be NULL):
+ * grad_rho0 / grad_u0 (device, dtype, logical order): gradients with respect
+ * to the physical rho and u given to maclab_set_state (zero on wall nodes,
+ * whose values come from the wall tables); grad_wall (HOST, n_wall_ids * 4
+ * doubles): gradient with respect to each wall id's physical (rho, u_x, u_y,
+ * u_z); grad_scalars (HOST, 5 doubles): [0] dL/dnu, [1] dL/de, [2..4]
+ * gradient with respect to the physical body acceleration.  dot_T comes from
+ * maclab_adjoint_seed; grad_force_lat (HOST, d doubles) is the sum of all
+ * maclab_adjoint_step grad_force outputs.  The loss is taken at a fixed
+ * number of steps: changing nu changes e = 6 nu / dx and so the lattice
+ * velocities of the initial field, the walls and the output, and the force
+ * increment force * dx / e^2.  Synchronises the stream. */
+maclab_status maclab_adjoint_finish(maclab_handle h, const void *lam_0, const void *state_0,
+                                    void *grad_rho0, void *grad_u0, int32_t dtype, double dot_T,
+                                    const double *grad_force_lat, double *grad_wall,
+                                    double *grad_scalars);
+
 /* Diagnostics sums without any device allocation.  (Not part of the method:
  * the paper has no counterpart.)  For callers that cannot allocate device
  * memory while they run -- for example a host loop that reserved all device

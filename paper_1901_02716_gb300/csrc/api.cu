@@ -68,6 +68,8 @@ void free_ctx(maclab_ctx* h) {
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   cudaFree(h->d_partial);
   cudaFree(h->d_diag);
+  cudaFree(h->d_adj_scratch);
+  cudaFree(h->d_adj_red);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->d_node_type);
@@ -452,6 +454,104 @@ maclab_status maclab_set_graph(maclab_handle h, int32_t steps) {
   DeviceGuard dg(h->device);
   drop_graphs(h);
   h->graph_steps = steps + (steps & 1);
+  return MACLAB_OK;
+}
+
+static size_t adjoint_bytes(const maclab_ctx* h) {
+  return (size_t)(h->g.d + 1) * (size_t)h->g.n * (h->precision == MACLAB_F64 ? 8 : 4);
+}
+
+static maclab_status ensure_adjoint(maclab_ctx* h) {
+  if (!h->d_adj_scratch) {
+    if (cudaMalloc(&h->d_adj_scratch, adjoint_bytes(h)) != cudaSuccess) {
+      cudaGetLastError();
+      h->d_adj_scratch = nullptr;
+      return fail(MACLAB_ERR_OOM, "adjoint scratch allocation failed");
+    }
+  }
+  if (!h->d_adj_red) {
+    if (cudaMalloc(&h->d_adj_red, sizeof(double) * (1 + 4 * (size_t)h->n_wall_ids)) != cudaSuccess) {
+      cudaGetLastError();
+      h->d_adj_red = nullptr;
+      return fail(MACLAB_ERR_OOM, "adjoint scratch allocation failed");
+    }
+  }
+  return MACLAB_OK;
+}
+
+maclab_status maclab_adjoint_bytes(maclab_handle h, size_t* bytes) {
+  if (!h || !bytes) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  *bytes = adjoint_bytes(h);
+  return MACLAB_OK;
+}
+
+maclab_status maclab_adjoint_step(maclab_handle h, const void* state_n, const void* state_np1,
+                                  const void* lam_np1, void* lam_n, double* grad_force) {
+  if (!h || !state_n || !state_np1 || !lam_np1 || !lam_n) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (lam_n == lam_np1) return fail(MACLAB_ERR_INVALID, "lam_n must not alias lam_np1");
+  DeviceGuard dg(h->device);
+  maclab_status s = ensure_adjoint(h);
+  if (s != MACLAB_OK) return s;
+  CUDA_TRY(launch_adjoint_step(h->g, h->precision, state_n, state_np1, lam_np1, lam_n,
+                               h->d_adj_scratch, h->force_lat, grad_force, h->stream),
+           "adjoint step");
+  return MACLAB_OK;
+}
+
+maclab_status maclab_adjoint_seed(maclab_handle h, const void* grad_rho, const void* grad_u,
+                                  int32_t dtype, const void* state_T, void* lam_T, double* dot_T) {
+  if (!h || !state_T || !lam_T) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (dtype != MACLAB_DTYPE_F64 && dtype != MACLAB_DTYPE_F32) return fail(MACLAB_ERR_INVALID, "bad dtype");
+  DeviceGuard dg(h->device);
+  maclab_status s = ensure_adjoint(h);
+  if (s != MACLAB_OK) return s;
+  CUDA_TRY(cudaMemsetAsync(h->d_adj_red, 0, sizeof(double), h->stream), "adjoint seed");
+  CUDA_TRY(launch_adjoint_seed(h->g, h->precision, grad_rho, grad_u, dtype, state_T, h->rho0, h->e,
+                               lam_T, h->d_adj_red, h->stream),
+           "adjoint seed");
+  double dot = 0;
+  CUDA_TRY(cudaMemcpyAsync(&dot, h->d_adj_red, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+           "adjoint seed D2H");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "adjoint seed sync");
+  if (dot_T) *dot_T = dot;
+  return MACLAB_OK;
+}
+
+maclab_status maclab_adjoint_finish(maclab_handle h, const void* lam_0, const void* state_0,
+                                    void* grad_rho0, void* grad_u0, int32_t dtype, double dot_T,
+                                    const double* grad_force_lat, double* grad_wall,
+                                    double* grad_scalars) {
+  if (!h || !lam_0 || !state_0) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (dtype != MACLAB_DTYPE_F64 && dtype != MACLAB_DTYPE_F32) return fail(MACLAB_ERR_INVALID, "bad dtype");
+  DeviceGuard dg(h->device);
+  maclab_status s = ensure_adjoint(h);
+  if (s != MACLAB_OK) return s;
+  const size_t nred = 1 + 4 * (size_t)h->n_wall_ids;
+  CUDA_TRY(cudaMemsetAsync(h->d_adj_red, 0, sizeof(double) * nred, h->stream), "adjoint finish");
+  CUDA_TRY(launch_adjoint_finish(h->g, h->precision, lam_0, state_0, h->d_node_type, h->n_wall_ids,
+                                 h->rho0, h->e, grad_rho0, grad_u0, dtype,
+                                 h->n_wall_ids ? h->d_adj_red + 1 : nullptr, h->d_adj_red, h->stream),
+           "adjoint finish");
+  std::vector<double> red(nred);
+  CUDA_TRY(cudaMemcpyAsync(red.data(), h->d_adj_red, sizeof(double) * nred, cudaMemcpyDeviceToHost,
+                           h->stream),
+           "adjoint finish D2H");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "adjoint finish sync");
+  if (grad_wall)
+    for (size_t k = 0; k < 4 * (size_t)h->n_wall_ids; ++k) grad_wall[k] = red[1 + k];
+  if (grad_scalars) {
+    // e enters through ut0 = u0 / e (inputs and walls), the output u = e ut and
+    // the force increment force * dt / e = force * dx / e^2.
+    double lf = 0;
+    for (int i = 0; i < h->g.d; ++i)
+      lf += (grad_force_lat ? grad_force_lat[i] : 0.0) * h->force_lat[i];
+    const double dLde = (dot_T - red[0] - 2.0 * lf) / h->e;
+    grad_scalars[0] = dLde * 6.0 / h->dx;  // e = 6 nu / dx
+    grad_scalars[1] = dLde;
+    for (int i = 0; i < 3; ++i)
+      grad_scalars[2 + i] =
+          (i < h->g.d && grad_force_lat) ? grad_force_lat[i] * h->dt / h->e : 0.0;
+  }
   return MACLAB_OK;
 }
 

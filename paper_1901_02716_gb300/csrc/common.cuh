@@ -133,6 +133,18 @@ int diag_blocks(int64_t n);
 cudaError_t launch_diagnostics(const Geometry& g, int precision, const void* cur, const void* prev,
                                double* partial, int nblocks, double* out, cudaStream_t st);
 
+// Defined in adjoint.cu.
+cudaError_t launch_adjoint_step(const Geometry& g, int precision, const void* state_n,
+                                const void* state_np1, const void* lam_np1, void* lam_n,
+                                void* scratch, const double force_lat[3], double* grad_force,
+                                cudaStream_t st);
+cudaError_t launch_adjoint_seed(const Geometry& g, int precision, const void* grho, const void* gu,
+                                int dtype, const void* state, double rho0, double e, void* lam,
+                                double* dot, cudaStream_t st);
+cudaError_t launch_adjoint_finish(const Geometry& g, int precision, const void* lam, const void* state,
+                                  const uint8_t* nt, int nw, double rho0, double e, void* grho,
+                                  void* gu, int dtype, double* wall, double* dot, cudaStream_t st);
+
 // Defined in convert.cu.
 cudaError_t launch_set_physical(const Geometry& g, int precision, const void* rho,
                                 const void* u, int dtype, double rho0, double e,
@@ -179,4 +191,6 @@ struct maclab_ctx {
   int graph_steps = 32;
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
+  void* d_adj_scratch = nullptr;   // adjoint: (L_r, L_m) at every node
+  double* d_adj_red = nullptr;     // adjoint: reductions (1 + 4 * n_wall_ids doubles)
 };

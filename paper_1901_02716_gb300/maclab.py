@@ -72,6 +72,13 @@ SIGNATURES = {
     "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "maclab_set_graph": (_S, [_H, ctypes.c_int32]),
     "maclab_diagnostics": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
+    "maclab_adjoint_bytes": (_S, [_H, ctypes.POINTER(ctypes.c_size_t)]),
+    "maclab_adjoint_step": (_S, [_H, _VP, _VP, _VP, _VP, _VP]),
+    "maclab_adjoint_seed": (_S, [_H, _VP, _VP, ctypes.c_int32, _VP, _VP,
+                                 ctypes.POINTER(ctypes.c_double)]),
+    "maclab_adjoint_finish": (_S, [_H, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
     "maclab_diagnostics_noalloc": (_S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _VP, _VP,
                                         _VP, _VP, _VP]),
     "maclab_kernel_info": (_S, [_H, ctypes.POINTER(ctypes.c_int32),
@@ -243,6 +250,50 @@ def maclab_diagnostics_noalloc(lattice, precision, n_nodes, state, prev_state, e
                   "maclab_diagnostics_noalloc")
 
 
+def maclab_adjoint_bytes(h):
+    n = ctypes.c_size_t()
+    _check(lib().maclab_adjoint_bytes(h, ctypes.byref(n)), "maclab_adjoint_bytes")
+    return n.value
+
+
+def maclab_adjoint_step(h, state_n, state_np1, lam_np1, lam_n, grad_force=None):
+    """Device pointers (ints) or tensors for every array argument."""
+    p = [_dev(a) for a in (state_n, state_np1, lam_np1, lam_n, grad_force)]
+    return _check(lib().maclab_adjoint_step(h, *p), "maclab_adjoint_step")
+
+
+def maclab_adjoint_seed(h, grad_rho, grad_u, state_T, lam_T):
+    dt = _dtype_code(grad_rho if grad_rho is not None else grad_u)
+    dot = ctypes.c_double()
+    _check(lib().maclab_adjoint_seed(h, _dev(grad_rho), _dev(grad_u), dt, _dev(state_T),
+                                     _dev(lam_T), ctypes.byref(dot)), "maclab_adjoint_seed")
+    return dot.value
+
+
+def maclab_adjoint_finish(h, lam_0, state_0, grad_rho0, grad_u0, dot_T, grad_force_lat,
+                          n_wall_ids):
+    dt = _dtype_code(grad_rho0 if grad_rho0 is not None else grad_u0)
+    gf = (ctypes.c_double * 3)(*([float(v) for v in grad_force_lat] + [0.0] * 3)[:3])
+    gw = (ctypes.c_double * max(1, 4 * n_wall_ids))()
+    sc = (ctypes.c_double * 5)()
+    _check(lib().maclab_adjoint_finish(h, _dev(lam_0), _dev(state_0), _dev(grad_rho0),
+                                       _dev(grad_u0), dt, float(dot_T), gf, gw, sc),
+           "maclab_adjoint_finish")
+    return {"wall": [list(gw[4 * k:4 * k + 4]) for k in range(n_wall_ids)],
+            "nu": sc[0], "e": sc[1], "accel": list(sc[2:5])}
+
+
+def _dev(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    p, where = _ptr(a)
+    if where != DEVICE:
+        raise ValueError("adjoint arrays must be device tensors")
+    return p
+
+
 def maclab_kernel_info(h):
     out = (ctypes.c_int32 * 4)()
     name = ctypes.c_char_p()
@@ -383,6 +434,9 @@ class Solver:
 
     def set_kernel(self, kernel):
         maclab_set_kernel(self.handle, kernel)
+
+    def adjoint_bytes(self):
+        return maclab_adjoint_bytes(self.handle)
 
     def set_graph(self, steps):
         maclab_set_graph(self.handle, steps)
