@@ -280,6 +280,7 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_extras:
         line["e2e"] = e2e_leg(M, case, prec, args, stream)
+        line["adjoint_forward"] = adjoint_leg(M, case, prec, args, stream)
         if args.precision != "f64":
             line["fp64"] = fp64_leg(M, case, args, stream, flush)
         mlups, steps, secs = oracle_rate(args.n, args.re)
@@ -322,6 +323,42 @@ def e2e_leg(M, case, prec, args, stream):
     nbytes = rho_h.numel() * 4 + u_h.numel() * 4
     return {"value": case.n_fluid * args.inner * k / dt / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+
+def adjoint_leg(M, case, prec, args, stream):
+    """Time of one reverse step (maclab_adjoint_step, states already stored)
+    against one forward step, same workload and storage type."""
+    import torch
+    s = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
+    nb = s.state_bytes()
+    s0 = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    s1 = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    s.step(20)
+    s.get_lattice_state(s0)
+    s.step(1)
+    s.get_lattice_state(s1)
+    ab = s.adjoint_bytes()
+    lam = [torch.zeros(ab, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    gf = torch.zeros(3, dtype=torch.float64, device="cuda")
+    k = 20
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(k):
+            fn(i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    t_fwd = timed(lambda i=0: s.step(1))
+    t_adj = timed(lambda i=0: M.maclab_adjoint_step(s.handle, s0, s1, lam[i & 1], lam[(i + 1) & 1], gf))
+    s.close()
+    return {"forward_ms": t_fwd, "adjoint_ms": t_adj, "ratio": t_adj / t_fwd,
+            "adjoint_launches_per_step": 2}
 
 
 def fp64_leg(M, case, args, stream, flush):

@@ -170,6 +170,48 @@ maclab_status maclab_diagnostics(maclab_handle h, double out[8]);
  * tile shape. */
 maclab_status maclab_set_graph(maclab_handle h, int32_t steps);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent domains advanced together: every maclab_batch_step is one
+ * kernel launch over the work items of all domains (D2Q9 domains whose nx is a
+ * multiple of 4), or one launch per domain otherwise, and runs of steps are
+ * captured in CUDA graphs.  Domains may differ in size, dx, nu, walls and
+ * force; they must share lattice, precision, device and stream. */
+typedef struct maclab_batch_ctx *maclab_batch;
+
+/* Create a batch from `count` configurations (see maclab_create).  Returns
+ * MACLAB_WARN_RLE if any member warned. */
+maclab_status maclab_batch_create(const maclab_config *cfgs, int32_t count, maclab_batch *out);
+maclab_status maclab_batch_destroy(maclab_batch b);
+
+/* Handle of member i, for maclab_set_state / get_state / diagnostics and the
+ * other per-domain calls.  The batch owns it (do not destroy it).  Stepping a
+ * member with maclab_step puts it out of step with the batch, which
+ * maclab_batch_step then reports as MACLAB_ERR_INVALID. */
+maclab_status maclab_batch_member(maclab_batch b, int32_t i, maclab_handle *out);
+
+/* Advance every member by n steps. */
+maclab_status maclab_batch_step(maclab_batch b, int64_t n);
+
+/* Rows of a domain per work item (the tuning knob of the single launch);
+ * 0 = library default.  Rebuilds the work list. */
+maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows);
+
+/* out[0] members, out[1] total nodes, out[2] fluid nodes, out[3] work items
+ * per launch (0 when one launch per member is used), out[4] rows per item,
+ * out[5] kernel launches per step. */
+maclab_status maclab_batch_info(maclab_batch b, int64_t out[6]);
+
+/* ---------------------------------------------------------------- tuning
+ * Time the candidate shapes of the tiled kernel (rows per tile, planes per
+ * block) on this handle's domain and keep the fastest; the state is saved
+ * before and restored after (temporary device buffers are allocated).
+ * Results are cached per (lattice, precision, dims, periodicity, wall mode,
+ * device) for the process.  out (may be NULL) receives the chosen ty, tz. */
+maclab_status maclab_tune(maclab_handle h, int32_t out[2]);
+
+/* The same for a batch: chooses the rows per work item. */
+maclab_status maclab_batch_tune(maclab_batch b, int32_t *rows);
+
 /* ---------------------------------------------------------------- adjoint
  * Reverse mode of maclab_step, for gradients of a loss on the final state
  * with respect to the initial fields, the wall values, the body force and nu.

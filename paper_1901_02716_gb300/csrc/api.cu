@@ -8,6 +8,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -620,6 +622,424 @@ maclab_status maclab_sync(maclab_handle h) {
   DeviceGuard dg(h->device);
   CUDA_TRY(cudaStreamSynchronize(h->stream), "sync");
   return MACLAB_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batches
+
+struct maclab_batch_ctx {
+  std::vector<maclab_ctx*> members;
+  int lattice = 0, precision = 0;
+  bool one_launch = false;     // all D2Q9 with nx % 4 == 0: one launch per step
+  void* d_insts = nullptr;
+  void* d_items = nullptr;
+  int n_items = 0;
+  int rows = 0;                // rows per work item
+  int blocks = 0;
+  int cur = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int graph_steps = 32;
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+void batch_drop_graphs(maclab_batch_ctx* b) {
+  for (int c = 0; c < 2; ++c)
+    if (b->graph_exec[c]) {
+      cudaGraphExecDestroy(b->graph_exec[c]);
+      b->graph_exec[c] = nullptr;
+    }
+}
+
+void batch_free(maclab_batch_ctx* b) {
+  if (!b) return;
+  batch_drop_graphs(b);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  cudaFree(b->d_insts);
+  cudaFree(b->d_items);
+  for (maclab_ctx* m : b->members) maclab_destroy(m);
+  delete b;
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 148;
+  }
+  return sms;
+}
+
+// (Re)build the work list for `rows` rows per item.
+maclab_status batch_build_items(maclab_batch_ctx* b, int rows) {
+  if (!b->one_launch) {
+    b->rows = rows;
+    return MACLAB_OK;
+  }
+  std::vector<int> items;
+  for (size_t i = 0; i < b->members.size(); ++i) batch_items((int)i, b->members[i]->g, rows, items);
+  void* d = nullptr;
+  if (cudaMalloc(&d, items.size() * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MACLAB_ERR_OOM, "batch work list allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(d, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "batch work list upload");
+  }
+  cudaFree(b->d_items);
+  b->d_items = d;
+  b->n_items = (int)(items.size() / 4);
+  b->rows = rows;
+  // resident warps: two 256-thread blocks per SM
+  const int want = (b->n_items + 7) / 8;
+  b->blocks = want < 2 * sm_count() ? (want > 0 ? want : 1) : 2 * sm_count();
+  batch_drop_graphs(b);
+  return MACLAB_OK;
+}
+
+cudaError_t batch_launch_one(maclab_batch_ctx* b, int c, cudaStream_t st) {
+  if (b->one_launch)
+    return launch_batch_step(b->precision, b->d_insts, b->d_items, b->n_items, c, b->blocks, st);
+  for (maclab_ctx* m : b->members) {
+    cudaError_t e = launch_step(step_launch(m, c), st, m->kernel);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+maclab_status batch_build_graph(maclab_batch_ctx* b, int c) {
+  if (!b->capture_stream &&
+      cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "capture stream");
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < b->graph_steps && err == cudaSuccess; ++k)
+    err = batch_launch_one(b, c ^ (k & 1), b->capture_stream);
+  cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &graph);
+  if (err != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(err != cudaSuccess ? err : e2, "batch graph capture");
+  }
+  err = cudaGraphInstantiate(&b->graph_exec[c], graph, 0);
+  cudaGraphDestroy(graph);
+  if (err != cudaSuccess) {
+    b->graph_exec[c] = nullptr;
+    return cuda_fail(err, "batch graph instantiate");
+  }
+  return MACLAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+maclab_status maclab_batch_create(const maclab_config* cfgs, int32_t count, maclab_batch* out) {
+  if (!out) return fail(MACLAB_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || count < 1) return fail(MACLAB_ERR_INVALID, "need at least one configuration");
+  maclab_batch_ctx* b = new (std::nothrow) maclab_batch_ctx();
+  if (!b) return fail(MACLAB_ERR_OOM, "host allocation failed");
+  b->lattice = cfgs[0].lattice;
+  b->precision = cfgs[0].precision;
+  b->stream = (cudaStream_t)cfgs[0].stream;
+  maclab_status warn = MACLAB_OK;
+  for (int i = 0; i < count; ++i) {
+    if (cfgs[i].lattice != b->lattice || cfgs[i].precision != b->precision ||
+        cfgs[i].stream != cfgs[0].stream) {
+      batch_free(b);
+      return fail(MACLAB_ERR_INVALID, "batch members must share lattice, precision and stream");
+    }
+    maclab_handle h = nullptr;
+    maclab_status s = maclab_create(&cfgs[i], &h);
+    if (s < 0) {
+      batch_free(b);
+      return s;
+    }
+    if (s > 0) warn = s;
+    b->members.push_back(h);
+  }
+  b->device = b->members[0]->device;
+  for (maclab_ctx* m : b->members)
+    if (m->device != b->device) {
+      batch_free(b);
+      return fail(MACLAB_ERR_INVALID, "batch members must be on one device");
+    }
+  DeviceGuard dg(b->device);
+  b->one_launch = b->lattice == MACLAB_D2Q9;
+  for (maclab_ctx* m : b->members) b->one_launch = b->one_launch && m->g.ilv == 1;
+  if (b->one_launch) {
+    std::vector<unsigned char> insts(batch_inst_bytes() * b->members.size());
+    for (size_t i = 0; i < b->members.size(); ++i) {
+      maclab_ctx* m = b->members[i];
+      batch_fill_inst(insts.data() + i * batch_inst_bytes(), m->g, m->buf[0], m->buf[1], m->force_lat);
+    }
+    if (cudaMalloc(&b->d_insts, insts.size()) != cudaSuccess) {
+      cudaGetLastError();
+      batch_free(b);
+      return fail(MACLAB_ERR_OOM, "batch descriptor allocation failed");
+    }
+    cudaError_t e = cudaMemcpy(b->d_insts, insts.data(), insts.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      batch_free(b);
+      return cuda_fail(e, "batch descriptor upload");
+    }
+  }
+  maclab_status s = batch_build_items(b, 16);
+  if (s != MACLAB_OK) {
+    batch_free(b);
+    return s;
+  }
+  *out = b;
+  return warn;
+}
+
+maclab_status maclab_batch_destroy(maclab_batch b) {
+  if (!b) return MACLAB_OK;
+  DeviceGuard dg(b->device);
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  return MACLAB_OK;
+}
+
+maclab_status maclab_batch_member(maclab_batch b, int32_t i, maclab_handle* out) {
+  if (!b || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (i < 0 || i >= (int)b->members.size()) return fail(MACLAB_ERR_INVALID, "member index out of range");
+  *out = b->members[i];
+  return MACLAB_OK;
+}
+
+maclab_status maclab_batch_step(maclab_batch b, int64_t n) {
+  if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
+  if (n < 0) return fail(MACLAB_ERR_INVALID, "n must be >= 0");
+  for (maclab_ctx* m : b->members)
+    if (m->cur != b->cur) return fail(MACLAB_ERR_INVALID, "a member was stepped outside the batch");
+  DeviceGuard dg(b->device);
+  int64_t done = 0;
+  while (b->graph_steps > 0 && n - done >= b->graph_steps) {
+    if (!b->graph_exec[b->cur]) {
+      maclab_status s = batch_build_graph(b, b->cur);
+      if (s != MACLAB_OK) return s;
+    }
+    CUDA_TRY(cudaGraphLaunch(b->graph_exec[b->cur], b->stream), "batch graph launch");
+    done += b->graph_steps;
+  }
+  for (; done < n; ++done) {
+    CUDA_TRY(batch_launch_one(b, b->cur, b->stream), "batch step launch");
+    b->cur ^= 1;
+  }
+  for (maclab_ctx* m : b->members) {
+    m->cur = b->cur;
+    m->steps += n;
+    if (n > 0) m->prev_valid = true;
+  }
+  return MACLAB_OK;
+}
+
+maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows) {
+  if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
+  if (rows < 0 || rows > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad row count");
+  DeviceGuard dg(b->device);
+  return batch_build_items(b, rows ? rows : 16);
+}
+
+maclab_status maclab_batch_info(maclab_batch b, int64_t out[6]) {
+  if (!b || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  int64_t nodes = 0, fluid = 0;
+  for (maclab_ctx* m : b->members) {
+    nodes += m->g.n;
+    fluid += m->n_fluid;
+  }
+  out[0] = (int64_t)b->members.size();
+  out[1] = nodes;
+  out[2] = fluid;
+  out[3] = b->one_launch ? b->n_items : 0;
+  out[4] = b->rows;
+  out[5] = b->one_launch ? 1 : (int64_t)b->members.size();
+  return MACLAB_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== tuning
+
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+std::string tune_key(const maclab_ctx* h) {
+  char buf[160];
+  snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%u/%d/%d", h->g.lattice, h->precision, h->g.nx, h->g.ny,
+           h->g.nz, h->g.periodic, h->g.wall_mode, h->device);
+  return buf;
+}
+
+// Median-free simple timing: events around `k` launches of fn after 2 warm-up calls.
+template <typename Fn>
+float time_ms(cudaStream_t st, int k, Fn fn) {
+  fn();
+  fn();
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, st);
+  for (int i = 0; i < k; ++i) fn();
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / k;
+}
+
+}  // namespace
+
+extern "C" {
+
+maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
+  if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  DeviceGuard dg(h->device);
+  const std::string key = tune_key(h);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      if (tiled_supported(h->g, h->precision, it->second.first, it->second.second)) {
+        drop_graphs(h);
+        h->kernel = MACLAB_KERNEL_TILED;
+        h->ty = it->second.first;
+        h->tz = it->second.second;
+      }
+      if (out) { out[0] = h->ty; out[1] = h->tz; }
+      return MACLAB_OK;
+    }
+  }
+  if (!tiled_supported(h->g, h->precision, 0, 0)) {
+    if (out) { out[0] = 0; out[1] = 0; }
+    return MACLAB_OK;  // only the reference kernel serves this domain
+  }
+  // save the state
+  void* saved = nullptr;
+  const size_t sb = state_bytes(h);
+  if (cudaMalloc(&saved, sb) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MACLAB_ERR_OOM, "tuning buffer allocation failed");
+  }
+  CUDA_TRY(cudaMemcpyAsync(saved, h->buf[h->cur], sb, cudaMemcpyDeviceToDevice, h->stream), "tune save");
+  const int64_t steps0 = h->steps;
+  const bool prev0 = h->prev_valid;
+  const int kernel0 = h->kernel, ty0 = h->ty, tz0 = h->tz;
+  const int tys3[] = {2, 4, 8};
+  const int tzs[] = {0, 4, 8, 16, 32};
+  float best = 1e30f;
+  int bty = 0, btz = 0;
+  drop_graphs(h);
+  h->kernel = MACLAB_KERNEL_TILED;
+  const int n_ty = h->g.d == 3 ? 3 : 1;
+  for (int a = 0; a < n_ty; ++a)
+    for (int tz : tzs) {
+      const int ty = h->g.d == 3 ? tys3[a] : 0;
+      if (!tiled_supported(h->g, h->precision, ty, tz)) continue;
+      h->ty = ty;
+      h->tz = tz;
+      const float ms = time_ms(h->stream, 10, [&]() {
+        launch_step(step_launch(h, h->cur), h->stream, h->kernel);
+        h->cur ^= 1;
+      });
+      if (ms < best) {
+        best = ms;
+        bty = ty;
+        btz = tz;
+      }
+    }
+  cudaError_t e = cudaGetLastError();
+  // restore
+  h->cur = 0;
+  cudaMemcpyAsync(h->buf[0], saved, sb, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(h->buf[1], saved, sb, cudaMemcpyDeviceToDevice, h->stream);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(saved);
+  h->steps = steps0;
+  h->prev_valid = false;  // both buffers now hold the restored state
+  (void)prev0;
+  if (e != cudaSuccess) {
+    h->kernel = kernel0;
+    h->ty = ty0;
+    h->tz = tz0;
+    return cuda_fail(e, "tuning launch");
+  }
+  h->ty = bty;
+  h->tz = btz;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {bty, btz};
+  }
+  if (out) { out[0] = bty; out[1] = btz; }
+  return MACLAB_OK;
+}
+
+maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
+  if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
+  DeviceGuard dg(b->device);
+  if (!b->one_launch) {
+    for (maclab_ctx* m : b->members) {
+      maclab_status s = maclab_tune(m, nullptr);
+      if (s != MACLAB_OK) return s;
+    }
+    batch_drop_graphs(b);
+    if (rows_out) *rows_out = 0;
+    return MACLAB_OK;
+  }
+  // save every member's state
+  std::vector<void*> saved(b->members.size(), nullptr);
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    maclab_ctx* m = b->members[i];
+    if (cudaMalloc(&saved[i], state_bytes(m)) != cudaSuccess) {
+      cudaGetLastError();
+      for (void* p : saved) cudaFree(p);
+      return fail(MACLAB_ERR_OOM, "tuning buffer allocation failed");
+    }
+    cudaMemcpyAsync(saved[i], m->buf[m->cur], state_bytes(m), cudaMemcpyDeviceToDevice, b->stream);
+  }
+  const int candidates[] = {4, 8, 16, 32, 64};
+  float best = 1e30f;
+  int best_rows = 16;
+  for (int rows : candidates) {
+    if (batch_build_items(b, rows) != MACLAB_OK) continue;
+    const float ms = time_ms(b->stream, 10, [&]() {
+      batch_launch_one(b, b->cur, b->stream);
+      b->cur ^= 1;
+    });
+    if (ms < best) {
+      best = ms;
+      best_rows = rows;
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  b->cur = 0;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    maclab_ctx* m = b->members[i];
+    cudaMemcpyAsync(m->buf[0], saved[i], state_bytes(m), cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(m->buf[1], saved[i], state_bytes(m), cudaMemcpyDeviceToDevice, b->stream);
+    m->cur = 0;
+    m->prev_valid = false;
+  }
+  cudaStreamSynchronize(b->stream);
+  for (void* p : saved) cudaFree(p);
+  if (e != cudaSuccess) return cuda_fail(e, "batch tuning launch");
+  maclab_status s = batch_build_items(b, best_rows);
+  if (rows_out) *rows_out = best_rows;
+  return s;
 }
 
 }  // extern "C"

@@ -145,6 +145,14 @@ cudaError_t launch_adjoint_finish(const Geometry& g, int precision, const void* 
                                   const uint8_t* nt, int nw, double rho0, double e, void* grho,
                                   void* gu, int dtype, double* wall, double* dot, cudaStream_t st);
 
+// Defined in batch.cu.
+cudaError_t launch_batch_step(int precision, const void* insts, const void* items, int n_items,
+                              int cur, int blocks, cudaStream_t st);
+size_t batch_inst_bytes();
+size_t batch_item_bytes();
+void batch_fill_inst(void* dst, const Geometry& g, void* buf0, void* buf1, const double force[3]);
+void batch_items(int inst, const Geometry& g, int rows, std::vector<int>& out4);
+
 // Defined in convert.cu.
 cudaError_t launch_set_physical(const Geometry& g, int precision, const void* rho,
                                 const void* u, int dtype, double rho0, double e,

@@ -72,6 +72,14 @@ SIGNATURES = {
     "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "maclab_set_graph": (_S, [_H, ctypes.c_int32]),
     "maclab_diagnostics": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
+    "maclab_batch_create": (_S, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_H)]),
+    "maclab_batch_destroy": (_S, [_H]),
+    "maclab_batch_member": (_S, [_H, ctypes.c_int32, ctypes.POINTER(_H)]),
+    "maclab_batch_step": (_S, [_H, ctypes.c_int64]),
+    "maclab_batch_set_rows": (_S, [_H, ctypes.c_int32]),
+    "maclab_batch_info": (_S, [_H, ctypes.POINTER(ctypes.c_int64)]),
+    "maclab_tune": (_S, [_H, ctypes.POINTER(ctypes.c_int32)]),
+    "maclab_batch_tune": (_S, [_H, ctypes.POINTER(ctypes.c_int32)]),
     "maclab_adjoint_bytes": (_S, [_H, ctypes.POINTER(ctypes.c_size_t)]),
     "maclab_adjoint_step": (_S, [_H, _VP, _VP, _VP, _VP, _VP]),
     "maclab_adjoint_seed": (_S, [_H, _VP, _VP, ctypes.c_int32, _VP, _VP,
@@ -283,6 +291,12 @@ def maclab_adjoint_finish(h, lam_0, state_0, grad_rho0, grad_u0, dot_T, grad_for
             "nu": sc[0], "e": sc[1], "accel": list(sc[2:5])}
 
 
+def maclab_tune(h):
+    out = (ctypes.c_int32 * 2)()
+    _check(lib().maclab_tune(h, out), "maclab_tune")
+    return int(out[0]), int(out[1])
+
+
 def _dev(a):
     if a is None:
         return None
@@ -441,6 +455,9 @@ class Solver:
     def set_graph(self, steps):
         maclab_set_graph(self.handle, steps)
 
+    def tune(self):
+        return maclab_tune(self.handle)
+
     def diagnostics(self, raise_nonfinite=True):
         return maclab_diagnostics(self.handle, raise_nonfinite)
 
@@ -463,3 +480,90 @@ class Solver:
 
     def sync(self):
         maclab_sync(self.handle)
+
+
+class _Member(Solver):
+    """A batch member: a Solver view of a handle the batch owns."""
+
+    def __init__(self, handle, lattice, dims, precision):
+        self.handle = handle
+        self.lattice = lattice
+        self.d = 2 if lattice == D2Q9 else 3
+        self.dims = tuple(dims)
+        self.grid = tuple(reversed(self.dims if self.d == 3 else self.dims[:2]))
+        self.precision = precision
+        self._owned = False
+
+    def close(self):
+        self.handle = None
+
+
+class Batch:
+    """Several domains advanced together (maclab_batch_*)."""
+
+    def __init__(self, configs):
+        """configs: list of dicts of Solver keyword arguments (lattice, dims, dx, nu,
+        precision, periodic, node_type, wall_rho, wall_u, body_force, rho0)."""
+        keep = []
+        arr = (maclab_config * len(configs))()
+        for i, c in enumerate(configs):
+            cfg, k = make_config(**c)
+            keep.append(k)
+            arr[i] = cfg
+        self._keep = keep
+        self.handle = _H()
+        s = lib().maclab_batch_create(arr, len(configs), ctypes.byref(self.handle))
+        _check(s, "maclab_batch_create")
+        self.members = []
+        for i, c in enumerate(configs):
+            h = _H()
+            _check(lib().maclab_batch_member(self.handle, i, ctypes.byref(h)), "maclab_batch_member")
+            self.members.append(_Member(h, c["lattice"], c["dims"], arr[i].precision))
+
+    @classmethod
+    def from_cases(cls, cases, precision=F32, dx=1.0, nu=1.0 / 6.0, stream=None):
+        e = 6.0 * nu / dx
+        dt = dx / e
+        cfgs = []
+        for case in cases:
+            cfgs.append(dict(lattice=case.lattice, dims=case.dims, dx=dx, nu=nu,
+                             precision=precision, periodic=case.periodic,
+                             node_type=case.node_type, wall_rho=case.wall_rho,
+                             wall_u=None if case.wall_u is None else np.asarray(case.wall_u) * e,
+                             body_force=None if case.force is None else [f * e / dt for f in case.force],
+                             stream=stream))
+        b = cls(cfgs)
+        for m, case in zip(b.members, cases):
+            m.set_state(np.ascontiguousarray(case.rho, dtype=np.float64),
+                        np.ascontiguousarray(case.u * e, dtype=np.float64))
+        return b
+
+    def step(self, n=1):
+        _check(lib().maclab_batch_step(self.handle, int(n)), "maclab_batch_step")
+
+    def set_rows(self, rows):
+        _check(lib().maclab_batch_set_rows(self.handle, int(rows)), "maclab_batch_set_rows")
+
+    def tune(self):
+        r = ctypes.c_int32()
+        _check(lib().maclab_batch_tune(self.handle, ctypes.byref(r)), "maclab_batch_tune")
+        return r.value
+
+    def info(self):
+        out = (ctypes.c_int64 * 6)()
+        _check(lib().maclab_batch_info(self.handle, out), "maclab_batch_info")
+        return {"members": out[0], "nodes": out[1], "fluid_nodes": out[2], "items": out[3],
+                "rows": out[4], "launches_per_step": out[5]}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for m in self.members:
+                m.handle = None
+            _check(lib().maclab_batch_destroy(self.handle), "maclab_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

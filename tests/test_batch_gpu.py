@@ -1,0 +1,124 @@
+"""Batched stepping and the autotuner.
+
+* every member of a batch advanced by one launch per step is bit-identical to
+  the same domain stepped on its own (same storage type, same arithmetic);
+* a member also matches the FP64 oracle;
+* batches that cannot use the single launch fall back to one launch per member;
+* tuning keeps the state and the results.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1901_02716_gb300 import inputs
+from paper_1901_02716_gb300 import maclab as M
+
+pytestmark = pytest.mark.gpu
+D2, D3 = inputs.D2Q9, inputs.D3Q19
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1901_02716_gb300 import _build
+    _build.build()
+
+
+def _cases():
+    sides, res, lids = inputs.batch_cavity_sides(6, seed=81)
+    cases = [inputs.cavity2d(n, lid=v) for n, v in zip(sides, lids)]
+    cases.append(inputs.random_case(D2, (136, 40), 0b11, seed=82, u_amp=0.05))
+    cases.append(inputs.random_case(D2, (124, 33), 0b01, seed=83, u_amp=0.05, walls="mixed",
+                                    force=(1e-4, -2e-4)))
+    return cases
+
+
+@pytest.mark.parametrize("precision", [M.F32, M.F64])
+def test_batch_members_equal_standalone_runs(precision):
+    cases = _cases()
+    b = M.Batch.from_cases(cases, precision)
+    info = b.info()
+    assert info["members"] == len(cases) and info["launches_per_step"] == 1
+    steps = 37                                 # one 32-step graph and 5 single launches
+    b.step(steps)
+    for m, case in zip(b.members, cases):
+        s = M.Solver.from_case(case, precision)
+        s.step(steps)
+        assert np.array_equal(s.get_lattice_state(), m.get_lattice_state())
+        assert m.params["steps"] == steps
+        s.close()
+    # and one member against the oracle
+    case = cases[-1]
+    r_g, u_g = b.members[-1].get_state()
+    r_o, u_o = orc.step(D2, case.rho, case.u, case.periodic, wall=case.wall_mask, force=case.force,
+                        nsteps=steps)
+    tol = 1e-11 if precision == M.F64 else 2e-5
+    assert np.sqrt(np.sum((u_g - u_o) ** 2) / np.sum(u_o ** 2)) < tol
+    b.close()
+
+
+def test_batch_fallback_and_3d():
+    cases = [inputs.random_case(D3, (12, 10, 9), 0b000, seed=84, walls="box"),
+             inputs.random_case(D3, (9, 8, 7), 0b111, seed=85)]
+    b = M.Batch.from_cases(cases, M.F32)
+    assert b.info()["launches_per_step"] == 2
+    b.step(5)
+    for m, case in zip(b.members, cases):
+        s = M.Solver.from_case(case, M.F32)
+        s.step(5)
+        assert np.array_equal(s.get_lattice_state(), m.get_lattice_state())
+        s.close()
+    b.close()
+
+
+def test_batch_rejects_mixed_lattices_and_foreign_steps():
+    c2 = inputs.random_case(D2, (16, 16), 0b11, seed=86)
+    c3 = inputs.random_case(D3, (8, 8, 8), 0b111, seed=87)
+    cfg = lambda c: dict(lattice=c.lattice, dims=c.dims, dx=1.0, nu=1 / 6, periodic=c.periodic)
+    with pytest.raises(M.MacLABError) as ei:
+        M.Batch([cfg(c2), cfg(c3)])
+    assert ei.value.status == M.ERR_INVALID
+    b = M.Batch.from_cases([c2, c2])
+    b.members[0].step(1)                       # stepped outside the batch
+    with pytest.raises(M.MacLABError) as ei:
+        b.step(1)
+    assert ei.value.status == M.ERR_INVALID
+    b.close()
+
+
+def test_batch_tune_keeps_state():
+    cases = _cases()
+    b = M.Batch.from_cases(cases, M.F32)
+    b.step(3)
+    before = [m.get_lattice_state().copy() for m in b.members]
+    rows = b.tune()
+    assert rows in (4, 8, 16, 32, 64)
+    for m, x in zip(b.members, before):
+        assert np.array_equal(m.get_lattice_state(), x)
+    b.step(4)
+    ref = M.Batch.from_cases(cases, M.F32)
+    ref.step(7)
+    for m, r in zip(b.members, ref.members):
+        assert np.array_equal(m.get_lattice_state(), r.get_lattice_state())
+    b.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("lat,dims,periodic,walls", [(D3, (32, 24, 20), 0b000, "box"),
+                                                     (D2, (64, 50), 0b01, "mixed")])
+def test_single_domain_tune(lat, dims, periodic, walls):
+    case = inputs.random_case(lat, dims, periodic, seed=88, walls=walls)
+    s = M.Solver.from_case(case, M.F32)
+    s.step(2)
+    x = s.get_lattice_state().copy()
+    ty, tz = s.tune()
+    assert np.array_equal(s.get_lattice_state(), x)
+    assert s.kernel_info()["kernel"] == M.KERNEL_TILED
+    s.step(3)
+    r_g, u_g = s.get_state()
+    r_o, u_o = orc.step(lat, case.rho, case.u, periodic, wall=case.wall_mask, nsteps=5)
+    assert np.sqrt(np.sum((u_g - u_o) ** 2) / np.sum(u_o ** 2)) < 1e-5
+    # a second handle of the same shape takes the cached choice
+    s2 = M.Solver.from_case(case, M.F32)
+    assert s2.tune() == (ty, tz)
+    s.close()
+    s2.close()
