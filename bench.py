@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=128, help="cavity side (nodes, walls included)")
+    p.add_argument("--side", type=int, default=128, help="cavity side (nodes, walls included)")
     p.add_argument("--re", type=float, default=100.0)
     p.add_argument("--inner", type=int, default=100, help="MacLAB steps per benchmark step")
     p.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "f16"])
@@ -170,7 +170,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from oracle import oracle as orc
-    case = cavity_case(args.n, args.re)
+    case = cavity_case(args.side, args.re)
     rho, u = case.rho.copy(), case.u.copy()
     for _ in range(args.warmup):
         rho, u = orc.step(case.lattice, rho, u, case.periodic, wall=case.wall_mask)
@@ -181,14 +181,14 @@ def run_reference(args, rank, world):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = case.n_fluid * args.steps / total / 1e6
-    sample = (f"{args.steps} MacLAB steps of the {args.n}^3 D3Q19 cavity (one per benchmark "
+    sample = (f"{args.steps} MacLAB steps of the {args.side}^3 D3Q19 cavity (one per benchmark "
               f"step), FP64 CPU oracle, single thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"3D lid-driven cavity D3Q19 {args.n}^3, Re={args.re:g}",
+        "config": {"workload": f"3D lid-driven cavity D3Q19 {args.side}^3, Re={args.re:g}",
                    "inner_steps": 1, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -209,7 +209,7 @@ def run_ours(args, rank, world, local_rank):
     if not os.path.exists(M.library_path()):
         _build.build()
     prec = M.PRECISION_NAMES[args.precision]
-    case = cavity_case(args.n, args.re)
+    case = cavity_case(args.side, args.re)
     stream = torch.cuda.current_stream()
     solver = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
     solver.set_kernel({"auto": M.KERNEL_AUTO, "reference": M.KERNEL_REFERENCE,
@@ -265,7 +265,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": f"3D lid-driven cavity D3Q19 {args.n}^3 (walls included), "
+        "config": {"workload": f"3D lid-driven cavity D3Q19 {args.side}^3 (walls included), "
                                f"Re={args.re:g}, {args.precision} storage",
                    "inner_steps": args.inner, "fluid_nodes": case.n_fluid,
                    "l2": "flushed (256 MiB write) before each timed step",
@@ -281,12 +281,13 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extras:
         line["e2e"] = e2e_leg(M, case, prec, args, stream)
         line["adjoint_forward"] = adjoint_leg(M, case, prec, args, stream)
+        line["suite"] = suite_leg(M, stream)
         if args.precision != "f64":
             line["fp64"] = fp64_leg(M, case, args, stream, flush)
-        mlups, steps, secs = oracle_rate(args.n, args.re)
+        mlups, steps, secs = oracle_rate(args.side, args.re)
         line["cpu_baseline"] = {
             "value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} MacLAB steps of the same {args.n}^3 cavity from rest "
+            "sample": f"{steps} MacLAB steps of the same {args.side}^3 cavity from rest "
                       f"({secs:.1f} s, FP64, single thread)"}
     solver.close()
     print(json.dumps(line), flush=True)
@@ -359,6 +360,58 @@ def adjoint_leg(M, case, prec, args, stream):
     s.close()
     return {"forward_ms": t_fwd, "adjoint_ms": t_adj, "ratio": t_adj / t_fwd,
             "adjoint_launches_per_step": 2}
+
+
+def _timed_steps(torch, stream, step, n, reps=3):
+    """Device time (ms) of `n` steps, best of `reps`, after one warm-up call."""
+    step(n)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def suite_leg(M, stream):
+    """The other configurations of the workload set, FP32, state L2/HBM resident
+    as it naturally is (no flush inside the timed steps): MLUPS each."""
+    import torch
+    from paper_1901_02716_gb300 import inputs
+    out = {}
+    # batched 2D cavities: 64 sides in {64..512}, Re log-uniform [100, 3200]
+    sides, res, lids = inputs.batch_cavity_sides(64, seed=4)
+    cases = [inputs.cavity2d(n, lid=v) for n, v in zip(sides, lids)]
+    b = M.Batch.from_cases(cases, M.F32, stream=ctypes_stream(stream))
+    rows = b.tune()
+    info = b.info()
+    n = 200
+    ms = _timed_steps(torch, stream, b.step, n)
+    out["batch_64_cavities"] = {"mlups": info["fluid_nodes"] * n / (ms * 1e-3) / 1e6,
+                                "fluid_nodes": info["fluid_nodes"], "rows_per_item": rows,
+                                "launches_per_step": info["launches_per_step"],
+                                "work_items": info["items"]}
+    b.close()
+    for name, case, steps in (
+            ("cavity2d_1024", inputs.cavity2d(1024, lid=inputs.lid_speed(1000.0, 1024)), 200),
+            ("cavity2d_256", inputs.cavity2d(256, lid=inputs.lid_speed(100.0, 256)), 400),
+            ("tgv3d_96", inputs.tgv3d(96, 0.02), 100),
+            ("cavity3d_512_hbm", inputs.cavity3d(512, lid=inputs.lid_speed(100.0, 512)), 10)):
+        s = M.Solver.from_case(case, M.F32, stream=ctypes_stream(stream))
+        s.tune()
+        ms = _timed_steps(torch, stream, s.step, steps)
+        bpl = 8 * (case.d + 1)
+        mlups = case.n_fluid * steps / (ms * 1e-3) / 1e6
+        out[name] = {"mlups": mlups, "fluid_nodes": case.n_fluid, "kernel": s.kernel_tag(),
+                     "hbm_frac_algorithmic": mlups * 1e6 * bpl / (peaks()[0] * 1e9)}
+        s.close()
+        del case
+    return out
 
 
 def fp64_leg(M, case, args, stream, flush):

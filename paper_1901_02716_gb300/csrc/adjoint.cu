@@ -18,7 +18,8 @@
 // gradient is the sum of lam_u' over fluid nodes.
 //
 // Two kernels: adj_lambda forms (L_r, L_m) at every node (zero at walls) into a
-// scratch array; adj_gather collects them at the sources.  Arithmetic in FP64
+// scratch array of one 4-value record per node (L_r, L_m x, L_m y, L_m z), so
+// that adj_gather reads each downstream neighbour with one vector load.  Arithmetic in FP64
 // for FP64 storage, FP32 otherwise; adjoint arrays are in that arithmetic
 // type, in the library's storage order.
 
@@ -38,6 +39,32 @@ __device__ __forceinline__ bool wall_at(const Geometry& g, int x, int y, int z, 
   return w;
 }
 
+// one 4-value record (16 bytes in FP32, 32 in FP64) read with vector loads
+template <typename C>
+struct Rec4;
+template <>
+struct Rec4<float> {
+  __device__ __forceinline__ static void ld(const float* p, float (&r)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  }
+  __device__ __forceinline__ static void st(float* p, const float (&r)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+};
+template <>
+struct Rec4<double> {
+  __device__ __forceinline__ static void ld(const double* p, double (&r)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
+  }
+  __device__ __forceinline__ static void st(double* p, const double (&r)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(r[2], r[3]);
+  }
+};
+
 template <int LAT, typename S>
 __global__ void __launch_bounds__(256) adj_lambda(Geometry g, const S* __restrict__ out_state,
                                                   const typename Store<S>::C* __restrict__ lam1,
@@ -54,22 +81,22 @@ __global__ void __launch_bounds__(256) adj_lambda(Geometry g, const S* __restric
     const int x = log_x(g, (int)(m % g.nx));
     const int y = (int)((m / g.nx) % g.ny);
     const int z = (int)(m / ((int64_t)g.nx * g.ny));
-    if (wall_at<LAT>(g, x, y, z, m)) {
-      for (int k = 0; k <= D; ++k) Lam[k * N + m] = C(0);
-      continue;
-    }
-    const C rho = C(1) + (C)Store<S>::from(out_state[m]);
-    const C inv = C(1) / rho;
-    C lr = lam1[m];
+    C rec[4] = {C(0), C(0), C(0), C(0)};
+    if (!wall_at<LAT>(g, x, y, z, m)) {
+      const C rho = C(1) + (C)Store<S>::from(out_state[m]);
+      const C inv = C(1) / rho;
+      C lr = lam1[m];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const C lu = lam1[(1 + i) * N + m];
-      const C um = (C)Store<S>::from(out_state[(1 + i) * N + m]) - force[i];  // m' / rho'
-      lr -= lu * um * inv;
-      Lam[(1 + i) * N + m] = lu * inv;
-      gf[i] += (double)lu;
+      for (int i = 0; i < D; ++i) {
+        const C lu = lam1[(1 + i) * N + m];
+        const C um = (C)Store<S>::from(out_state[(1 + i) * N + m]) - force[i];  // m' / rho'
+        lr -= lu * um * inv;
+        rec[1 + i] = lu * inv;
+        gf[i] += (double)lu;
+      }
+      rec[0] = lr;
     }
-    Lam[m] = lr;
+    Rec4<C>::st(Lam + 4 * m, rec);
   }
   if (grad_force) {
     __shared__ double red[3][256];
@@ -117,10 +144,12 @@ __global__ void __launch_bounds__(256) adj_gather(Geometry g, const S* __restric
         zs = zs < 0 ? zs + g.nz : zs - g.nz;
       }
       const int64_t s = ((int64_t)zs * g.ny + ys) * g.nx + mem_x(g, xs);
-      C ga = Lam[s];
+      C rec[4];
+      Rec4<C>::ld(Lam + 4 * s, rec);
+      C ga = rec[0];
 #pragma unroll
       for (int i = 0; i < D; ++i)
-        if (L::c(a, i) != 0) ga += C(L::c(a, i)) * Lam[(1 + i) * N + s];
+        if (L::c(a, i) != 0) ga += C(L::c(a, i)) * rec[1 + i];
       const C wg = ga * (C(L::w36(a)) / C(36));
       G0 += wg;
 #pragma unroll

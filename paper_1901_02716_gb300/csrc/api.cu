@@ -465,7 +465,9 @@ static size_t adjoint_bytes(const maclab_ctx* h) {
 
 static maclab_status ensure_adjoint(maclab_ctx* h) {
   if (!h->d_adj_scratch) {
-    if (cudaMalloc(&h->d_adj_scratch, adjoint_bytes(h)) != cudaSuccess) {
+    // one 4-value record per node
+    const size_t rec = 4 * (size_t)h->g.n * (h->precision == MACLAB_F64 ? 8 : 4);
+    if (cudaMalloc(&h->d_adj_scratch, rec) != cudaSuccess) {
       cudaGetLastError();
       h->d_adj_scratch = nullptr;
       return fail(MACLAB_ERR_OOM, "adjoint scratch allocation failed");
