@@ -496,9 +496,16 @@ maclab_status maclab_adjoint_step(maclab_handle h, const void* state_n, const vo
   DeviceGuard dg(h->device);
   maclab_status s = ensure_adjoint(h);
   if (s != MACLAB_OK) return s;
-  CUDA_TRY(launch_adjoint_step(h->g, h->precision, state_n, state_np1, lam_np1, lam_n,
-                               h->d_adj_scratch, h->force_lat, grad_force, h->stream),
-           "adjoint step");
+  // the tiled reverse step where it is built (unless the reference kernel was chosen)
+  if (h->kernel != MACLAB_KERNEL_REFERENCE && tiled_adjoint_supported(h->g, h->precision)) {
+    CUDA_TRY(launch_tiled_adjoint(h->g, h->precision, state_n, state_np1, lam_np1, lam_n,
+                                  h->d_adj_scratch, h->force_lat, grad_force, h->stream),
+             "adjoint step");
+  } else {
+    CUDA_TRY(launch_adjoint_step(h->g, h->precision, state_n, state_np1, lam_np1, lam_n,
+                                 h->d_adj_scratch, h->force_lat, grad_force, h->stream),
+             "adjoint step");
+  }
   return MACLAB_OK;
 }
 

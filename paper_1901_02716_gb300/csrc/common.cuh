@@ -138,6 +138,12 @@ cudaError_t launch_adjoint_step(const Geometry& g, int precision, const void* st
                                 const void* state_np1, const void* lam_np1, void* lam_n,
                                 void* scratch, const double force_lat[3], double* grad_force,
                                 cudaStream_t st);
+// Defined in adjoint_tiled.cu (domains with interleaved rows).
+bool tiled_adjoint_supported(const Geometry& g, int precision);
+cudaError_t launch_tiled_adjoint(const Geometry& g, int precision, const void* state_n,
+                                 const void* state_np1, const void* lam_np1, void* lam_n,
+                                 void* records, const double force_lat[3], double* grad_force,
+                                 cudaStream_t st);
 cudaError_t launch_adjoint_seed(const Geometry& g, int precision, const void* grho, const void* gu,
                                 int dtype, const void* state, double rho0, double e, void* lam,
                                 double* dot, cudaStream_t st);

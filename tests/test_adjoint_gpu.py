@@ -204,3 +204,46 @@ def test_body_force_gradient(torch):
         return float(np.sum(u * e * w))
     fd = fd4(lambda d: loss(accel + d), 1e-3 * accel)
     assert res["accel"][0] == pytest.approx(fd, rel=1e-7)
+
+
+@pytest.mark.parametrize("lat,dims,periodic,walls", [
+    (D2, (64, 37), 0b00, "box"), (D2, (96, 41), 0b01, "mixed"), (D2, (4, 9), 0b11, "none"),
+    (D2, (1024, 6), 0b10, "box"),
+    (D3, (32, 16, 7), 0b011, "box"), (D3, (20, 13, 17), 0b100, "mixed"), (D3, (8, 8, 5), 0b111, "none"),
+    (D3, (128, 12, 6), 0b000, "box"), (D3, (256, 6, 5), 0b101, "mixed"), (D3, (64, 8, 9), 0b111, "none")])
+@pytest.mark.parametrize("precision", [M.F64, M.F32])
+def test_tiled_adjoint_matches_reference_adjoint(torch, lat, dims, periodic, walls, precision):
+    """The tiled reverse step (pair records, staged pull gather) against the
+    reference two-kernel reverse step, on the same stored states."""
+    d = len(dims)
+    case = inputs.random_case(lat, dims, periodic, seed=76, u_amp=0.08, rho_amp=0.02, walls=walls,
+                              force=tuple([2e-4] * d))
+    out = []
+    for kern in (M.KERNEL_REFERENCE, M.KERNEL_AUTO):
+        s = M.Solver.from_case(case, precision)
+        s.set_kernel(kern)
+        s0 = _raw(torch, s)
+        s.step(1)
+        s1 = _raw(torch, s)
+        g = inputs.rng(77)
+        dt = torch.float64
+        lam1 = torch.empty(s.adjoint_bytes(), dtype=torch.uint8, device="cuda")
+        lam0 = torch.empty_like(lam1)
+        M.maclab_adjoint_seed(s.handle, torch.tensor(g.standard_normal(case.rho.shape), dtype=dt,
+                                                     device="cuda"),
+                              torch.tensor(g.standard_normal(case.u.shape), dtype=dt, device="cuda"),
+                              s1, lam1)
+        gf = torch.zeros(3, dtype=torch.float64, device="cuda")
+        M.maclab_adjoint_step(s.handle, s0, s1, lam1, lam0, gf)
+        gr = torch.empty(case.rho.shape, dtype=dt, device="cuda")
+        gu = torch.empty(case.u.shape, dtype=dt, device="cuda")
+        nw = 0 if case.wall_u is None else len(case.wall_u)
+        res = M.maclab_adjoint_finish(s.handle, lam0, s0, gr, gu, 0.0, gf.cpu().tolist(), nw)
+        out.append((gr.cpu().numpy(), gu.cpu().numpy(), res["wall"], gf.cpu().numpy()))
+        s.close()
+    (r1, u1, w1, f1), (r2, u2, w2, f2) = out
+    tol = 1e-12 if precision == M.F64 else 2e-6
+    assert np.abs(r1 - r2).max() <= tol * np.abs(r1).max()
+    assert np.abs(u1 - u2).max() <= tol * np.abs(u1).max()
+    assert np.allclose(w1, w2, rtol=tol * 10, atol=tol * max(np.abs(r1).max(), np.abs(u1).max()))
+    assert np.allclose(f1, f2, rtol=1e-6 if precision == M.F32 else 1e-12)
