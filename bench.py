@@ -359,7 +359,7 @@ def adjoint_leg(M, case, prec, args, stream):
     t_adj = timed(lambda i=0: M.maclab_adjoint_step(s.handle, s0, s1, lam[i & 1], lam[(i + 1) & 1], gf))
     s.close()
     return {"forward_ms": t_fwd, "adjoint_ms": t_adj, "ratio": t_adj / t_fwd,
-            "adjoint_launches_per_step": 2}
+            "adjoint_launches_per_step": 1}
 
 
 def _timed_steps(torch, stream, step, n, reps=3):

@@ -1,5 +1,5 @@
 // adjoint_tiled.cu -- host side of the tiled reverse step (adjoint_tiled.cuh):
-// block shapes, instantiations and the two launches.
+// block shapes, instantiations and the launch.
 
 #include "adjoint_tiled.cuh"
 
@@ -11,7 +11,8 @@ struct AdjShape {
   int bxc, ry, ty;
 };
 
-// Widths built: D2Q9 (BXC, 1); D3Q19 (BXC, TY + 2).  FP64 up to 64 quads per row.
+// Widths built: D2Q9 (BXC, 1); D3Q19 (BXC, TY + 2).  FP64 up to 64 quads per row in 3D,
+// 128 in 2D.
 bool adj_shape(const Geometry& g, int precision, AdjShape* s) {
   if (!g.ilv || precision == MACLAB_BF16_STORE || precision == MACLAB_F16_STORE) return false;
   const int bx = g.nx / 4;
@@ -49,36 +50,39 @@ int sms() {
 }
 
 template <int LAT, typename S>
-cudaError_t gather_dispatch(const AdjShape& s, const AdjArgs& A, const void* sn, const void* lam1,
-                            const void* rec, void* lam0, cudaStream_t st, dim3 grid) {
+cudaError_t tiled_dispatch(const AdjShape& s, const AdjArgs& A, const void* sn, const void* sn1,
+                           const void* lam1, void* lam0, double* gf, cudaStream_t st, int ytiles,
+                           int* resident) {
+#define MACLAB_ADJ_LAUNCH(BXC, RY) \
+  launch_adj_tiled<LAT, S, BXC, RY>(A, sn, sn1, lam1, lam0, gf, st, ytiles, resident)
   if (LAT == kD2Q9) {
     switch (s.bxc) {
-      case 16: return launch_adj_gather<LAT, S, 16, 1>(A, sn, lam1, rec, lam0, st, grid);
-      case 32: return launch_adj_gather<LAT, S, 32, 1>(A, sn, lam1, rec, lam0, st, grid);
-      case 64: return launch_adj_gather<LAT, S, 64, 1>(A, sn, lam1, rec, lam0, st, grid);
-      case 128: return launch_adj_gather<LAT, S, 128, 1>(A, sn, lam1, rec, lam0, st, grid);
+      case 16: return MACLAB_ADJ_LAUNCH(16, 1);
+      case 32: return MACLAB_ADJ_LAUNCH(32, 1);
+      case 64: return MACLAB_ADJ_LAUNCH(64, 1);
+      case 128: return MACLAB_ADJ_LAUNCH(128, 1);
       case 256:
-        if constexpr (sizeof(S) == 4) return launch_adj_gather<LAT, S, 256, 1>(A, sn, lam1, rec, lam0, st, grid);
+        if constexpr (sizeof(S) == 4) return MACLAB_ADJ_LAUNCH(256, 1);
         break;
     }
     return cudaErrorInvalidValue;
   }
   switch (s.bxc * 100 + s.ry) {
-    case 1610: return launch_adj_gather<LAT, S, 16, 10>(A, sn, lam1, rec, lam0, st, grid);
-    case 3206: return launch_adj_gather<LAT, S, 32, 6>(A, sn, lam1, rec, lam0, st, grid);
-    case 6406: return launch_adj_gather<LAT, S, 64, 6>(A, sn, lam1, rec, lam0, st, grid);
+    case 1610: return MACLAB_ADJ_LAUNCH(16, 10);
+    case 3206: return MACLAB_ADJ_LAUNCH(32, 6);
+    case 6406: return MACLAB_ADJ_LAUNCH(64, 6);
     case 12804:
-      if constexpr (sizeof(S) == 4) return launch_adj_gather<LAT, S, 128, 4>(A, sn, lam1, rec, lam0, st, grid);
+      if constexpr (sizeof(S) == 4) return MACLAB_ADJ_LAUNCH(128, 4);
       break;
   }
+#undef MACLAB_ADJ_LAUNCH
   return cudaErrorInvalidValue;
 }
 
 template <int LAT, typename S>
 cudaError_t tiled_adjoint_t(const Geometry& g, const AdjShape& s, const void* sn, const void* sn1,
-                            const void* lam1, void* lam0, void* rec, const double* force,
-                            double* gf, cudaStream_t st) {
-  using C = typename Store<S>::C;
+                            const void* lam1, void* lam0, const double* force, double* gf,
+                            cudaStream_t st) {
   AdjArgs A{};
   A.nx = g.nx;
   A.ny = g.d == 3 ? g.ny : 1;
@@ -92,24 +96,20 @@ cudaError_t tiled_adjoint_t(const Geometry& g, const AdjShape& s, const void* sn
   A.wall_mode = g.wall_mode;
   A.mask = g.mask;
   for (int i = 0; i < 3; ++i) A.force[i] = force[i];
-  const int64_t nquads = g.n / 4;
-  int64_t rb = (nquads + 255) / 256;
-  if (rb > 8 * sms()) rb = 8 * sms();
-  adj_records<LAT, S><<<(unsigned)(rb < 1 ? 1 : rb), 256, 0, st>>>(A, (const S*)sn1, (const C*)lam1,
-                                                                  (C*)rec, gf);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   const int ytiles = g.d == 3 ? (A.ny + s.ty - 1) / s.ty : 1;
-  // about 8 planes per block, rounded up to whole waves of two blocks per SM
+  int resident = 0;
+  cudaError_t e = tiled_dispatch<LAT, S>(s, A, sn, sn1, lam1, lam0, gf, st, ytiles, &resident);
+  if (e != cudaSuccess) return e;
+  // about 8 planes per block, rounded up to whole waves of resident blocks
   int nzc = (A.nplanes + 7) / 8;
-  const long slots = 2L * sms();
+  const long slots = (long)resident * sms();
   const long blocks = (long)nzc * ytiles;
   const long waves = (blocks + slots - 1) / slots;
   nzc = (int)((waves * slots) / ytiles);
   if (nzc > A.nplanes / 2) nzc = A.nplanes / 2 > 0 ? A.nplanes / 2 : 1;
   if (nzc < 1) nzc = 1;
   A.nzc = nzc;
-  return gather_dispatch<LAT, S>(s, A, sn, lam1, rec, lam0, st, dim3(nzc, ytiles));
+  return tiled_dispatch<LAT, S>(s, A, sn, sn1, lam1, lam0, gf, st, ytiles, nullptr);
 }
 
 }  // namespace
@@ -121,18 +121,17 @@ bool tiled_adjoint_supported(const Geometry& g, int precision) {
 
 cudaError_t launch_tiled_adjoint(const Geometry& g, int precision, const void* state_n,
                                  const void* state_np1, const void* lam_np1, void* lam_n,
-                                 void* records, const double force_lat[3], double* grad_force,
-                                 cudaStream_t st) {
+                                 const double force_lat[3], double* grad_force, cudaStream_t st) {
   AdjShape s;
   if (!adj_shape(g, precision, &s)) return cudaErrorInvalidValue;
   if (g.lattice == kD2Q9) {
     if (precision == MACLAB_F64)
-      return tiled_adjoint_t<kD2Q9, double>(g, s, state_n, state_np1, lam_np1, lam_n, records, force_lat, grad_force, st);
-    return tiled_adjoint_t<kD2Q9, float>(g, s, state_n, state_np1, lam_np1, lam_n, records, force_lat, grad_force, st);
+      return tiled_adjoint_t<kD2Q9, double>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, st);
+    return tiled_adjoint_t<kD2Q9, float>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, st);
   }
   if (precision == MACLAB_F64)
-    return tiled_adjoint_t<kD3Q19, double>(g, s, state_n, state_np1, lam_np1, lam_n, records, force_lat, grad_force, st);
-  return tiled_adjoint_t<kD3Q19, float>(g, s, state_n, state_np1, lam_np1, lam_n, records, force_lat, grad_force, st);
+    return tiled_adjoint_t<kD3Q19, double>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, st);
+  return tiled_adjoint_t<kD3Q19, float>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, st);
 }
 
 }  // namespace maclab

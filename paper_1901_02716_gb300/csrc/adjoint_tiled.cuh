@@ -7,18 +7,21 @@
 //   lam_u(y)   = rho (3 G1 + 9 G2 u - 3 u G0),
 // plus lam' passed through at wall nodes.
 //
-//  * adj_records: one thread per quad (4 stored nodes = node pairs a, b) forms
-//    (L_r, L_m) on paired FP32 lanes and writes them pair-major: per quad,
-//    pair a's (L_r, L_mx, L_my, L_mz) as four lane pairs, then pair b's
-//    (64 bytes in FP32).
-//  * adj_gather_tiled: blocks span the x extent and TY rows (+ a halo row on
-//    each side) and march the slowest axis; the records of three planes are
-//    staged in shared memory with per-thread cp.async copies (one barrier per
-//    plane); each destination pair pulls its 19 neighbours' records (two
-//    16-byte loads each) and accumulates the moments on lane pairs with the
-//    integer weights w36 (divided out at the end).  Across the seam between
-//    the two half rows the lanes swap: the end threads of each row stage a
-//    lane-swapped copy of their edge pair in two extra columns.
+// One launch.  Blocks span the x extent and TY rows (+ a halo row on each
+// side) and march the slowest axis.  Every thread forms (L_r, L_m) of its own
+// quad (4 stored nodes = node pairs a, b) on paired FP32 lanes from the
+// post-step state and lam', and writes them into a ring of four staged planes
+// in shared memory; the destination pairs then pull their 19 neighbours'
+// records from the three planes around them and accumulate the moments with
+// the integer weights w36 (divided out at the end).  The loads of plane q + 2
+// are issued before the gather of plane q and staged after it, so one barrier
+// per plane suffices.
+//
+// Shared layout: [stage][row][pair][unit][column] of 16-byte units, a unit
+// holding two components (FP32) or one (FP64) of a pair's record, so that the
+// threads of a warp read consecutive units.  Across the seam between the two
+// half rows the lanes swap: the end threads of each row also write a
+// lane-swapped copy of their edge pair into two extra columns.
 #pragma once
 #include "step_tiled.cuh"
 
@@ -35,128 +38,68 @@ struct AdjArgs {
   double force[3];
 };
 
-// ------------------------------------------------------------------ records
-
-template <int LAT, typename S>
-__global__ void __launch_bounds__(256) adj_records(AdjArgs A, const S* __restrict__ out_state,
-                                                   const typename Store<S>::C* __restrict__ lam1,
-                                                   typename Store<S>::C* __restrict__ rec,
-                                                   double* __restrict__ grad_force) {
-  using C = typename Store<S>::C;
-  using O = Pair<C>;
-  using P = typename O::P;
-  constexpr int D = Lattice<LAT>::D;
-  const int64_t nquads = A.n >> 2;
-  double gf[3] = {0.0, 0.0, 0.0};
-  P force[3];
-  for (int i = 0; i < 3; ++i) force[i] = O::splat(C(A.force[i]));
-  for (int64_t qd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qd < nquads;
-       qd += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = qd << 2;
-    // wall flags of the quad's lanes (a.x, a.y, b.x, b.y)
-    bool wall[4] = {false, false, false, false};
-    if (A.wall_mode == kWallMask) {
-      const uchar4 mk = *reinterpret_cast<const uchar4*>(A.mask + m);
-      wall[0] = mk.x != 0; wall[1] = mk.y != 0; wall[2] = mk.z != 0; wall[3] = mk.w != 0;
-    } else if (A.wall_mode == kWallBox) {
-      const int64_t row = m / A.nx;
-      const int t = (int)(m - row * A.nx) >> 2;
-      const int y = (int)(row % A.ny), z = (int)(row / A.ny);
-      bool rw = false;
-      if (D == 3) {
-        if (!A.py) rw |= (y == 0) | (y == A.ny - 1);
-        if (!A.pz) rw |= (z == 0) | (z == A.nplanes - 1);
-      } else {
-        if (!A.pz) rw |= (z == 0) | (z == A.nplanes - 1);  // 2D: rows along the march axis
-      }
-      for (int k = 0; k < 4; ++k) wall[k] = rw;
-      if (!A.px) {
-        wall[0] |= t == 0;                       // x = 0
-        wall[3] |= t == (A.nx >> 2) - 1;         // x = nx - 1
-      }
-    }
-    P st[D + 1][2], lm[D + 1][2];
-#pragma unroll
-    for (int f = 0; f <= D; ++f) {
-      Quad<S>::ld(out_state + f * A.n + m, st[f][0], st[f][1]);
-      Quad<C>::ld(lam1 + f * A.n + m, lm[f][0], lm[f][1]);
-    }
-    P out[2][4];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const P inv = O::rcp(O::add(O::splat(C(1)), st[0][q]));
-      P lr = lm[0][q];
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const P um = O::sub(st[1 + i][q], force[i]);           // m' / rho'
-        lr = O::sub(lr, O::mul(O::mul(lm[1 + i][q], um), inv));
-        out[q][1 + i] = O::mul(lm[1 + i][q], inv);
-      }
-      out[q][0] = lr;
-      if (D == 2) out[q][3] = O::splat(C(0));
-      // walls carry no (L_r, L_m)
-      const bool w0 = wall[2 * q], w1 = wall[2 * q + 1];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (w0) out[q][k].x = C(0);
-        if (w1) out[q][k].y = C(0);
-      }
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        if (!w0) gf[i] += (double)lm[1 + i][q].x;
-        if (!w1) gf[i] += (double)lm[1 + i][q].y;
-      }
-    }
-    C* dst = rec + qd * 16;
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int k = 0; k < 4; k += 2) Quad<C>::st(dst + q * 8 + 2 * k, out[q][k], out[q][k + 1]);
+// 16-byte unit <-> lane pairs
+template <typename P>
+struct AdjUnit;
+template <>
+struct AdjUnit<float2> {
+  static constexpr int G = 2;
+  __device__ __forceinline__ static void st(uint4* u, const float2* v) {
+    *reinterpret_cast<float4*>(u) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
   }
-  if (grad_force) {
-    __shared__ double red[3][256];
-    for (int i = 0; i < 3; ++i) red[i][threadIdx.x] = gf[i];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if ((int)threadIdx.x < s)
-        for (int i = 0; i < 3; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + s];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0)
-      for (int i = 0; i < D; ++i) atomicAdd(grad_force + i, red[i][0]);
+  __device__ __forceinline__ static void st_swapped(uint4* u, const float2* v) {
+    *reinterpret_cast<float4*>(u) = make_float4(v[0].y, v[0].x, v[1].y, v[1].x);
   }
-}
-
-// ------------------------------------------------------------------ gather
-
-// Stage layout: [kAdjStages][RY][W = BXC + 2][2 pairs][4 components] lane pairs.
-constexpr int kAdjStages = 4;
-
-template <typename C, int BXC, int RY>
-__host__ __device__ constexpr size_t adj_stage_bytes() {
-  return sizeof(typename Pair<C>::P) * (size_t)kAdjStages * RY * (BXC + 2) * 2 * 4;
-}
+  __device__ __forceinline__ static void ld(const uint4* u, float2* v) {
+    const float4 t = *reinterpret_cast<const float4*>(u);
+    v[0] = make_float2(t.x, t.y);
+    v[1] = make_float2(t.z, t.w);
+  }
+};
+template <>
+struct AdjUnit<double2> {
+  static constexpr int G = 1;
+  __device__ __forceinline__ static void st(uint4* u, const double2* v) { *reinterpret_cast<double2*>(u) = v[0]; }
+  __device__ __forceinline__ static void st_swapped(uint4* u, const double2* v) {
+    *reinterpret_cast<double2*>(u) = make_double2(v[0].y, v[0].x);
+  }
+  __device__ __forceinline__ static void ld(const uint4* u, double2* v) { v[0] = *reinterpret_cast<const double2*>(u); }
+};
 
 template <int LAT, typename S, int BXC, int RY>
-__global__ void __launch_bounds__(BXC * RY) adj_gather_tiled(AdjArgs A, const S* __restrict__ in_state,
-                                                             const typename Store<S>::C* __restrict__ lam1,
-                                                             const typename Store<S>::C* __restrict__ rec,
-                                                             typename Store<S>::C* __restrict__ lam0) {
+struct AdjTile {
   using C = typename Store<S>::C;
+  using P = typename Pair<C>::P;
+  static constexpr int D = Lattice<LAT>::D;
+  static constexpr int K = D + 1;                 // record components: L_r, L_m
+  static constexpr int G = AdjUnit<P>::G;         // components per unit
+  static constexpr int NU = (K + G - 1) / G;      // units per pair record
+  static constexpr int W = BXC + 2;               // columns, with the two seam copies
+  static constexpr int SEAM_L = BXC, SEAM_R = BXC + 1;
+  static constexpr int STAGES = 4;
+  static constexpr int STAGE = RY * 2 * NU * W;   // units per stage
+  static constexpr int THREADS = BXC * RY;
+  static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;
+  __host__ __device__ static constexpr size_t smem_bytes() { return (size_t)16 * STAGES * STAGE; }
+  __device__ __forceinline__ static constexpr int unit(int k, int rr, int pr, int u, int col) {
+    return (((k * RY + rr) * 2 + pr) * NU + u) * W + col;
+  }
+};
+
+template <int LAT, typename S, int BXC, int RY>
+__global__ void __launch_bounds__(BXC * RY, (AdjTile<LAT, S, BXC, RY>::MIN_BLOCKS))
+    adj_step_tiled(AdjArgs A, const S* __restrict__ in_state, const S* __restrict__ out_state,
+                   const typename Store<S>::C* __restrict__ lam1, typename Store<S>::C* __restrict__ lam0,
+                   double* __restrict__ grad_force) {
+  using T = AdjTile<LAT, S, BXC, RY>;
+  using C = typename T::C;
   using O = Pair<C>;
   using P = typename O::P;
+  using U = AdjUnit<P>;
   using L = Lattice<LAT>;
   using F = Frame<LAT>;
-  constexpr int D = L::D;
-  constexpr int K = D + 1;
-  constexpr int W = BXC + 2;
-  constexpr int SEAM_L = BXC, SEAM_R = BXC + 1;
-  constexpr int PAIR = 4;                 // lane pairs per node-pair record
-  constexpr int COL = 2 * PAIR;           // lane pairs per column (pairs a and b)
-  constexpr int ROW = W * COL;
-  constexpr int STAGE = RY * ROW;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  P* stg = reinterpret_cast<P*>(smem_raw);
+  constexpr int D = T::D, K = T::K, G = T::G, NU = T::NU;
+  extern __shared__ __align__(16) uint4 units[];
   const int tx = threadIdx.x, r = threadIdx.y;
   const int bxr = A.nx >> 2;
   const bool active = tx < bxr;
@@ -173,85 +116,135 @@ __global__ void __launch_bounds__(BXC * RY) adj_gather_tiled(AdjArgs A, const S*
     }
   }
   interior = interior && active;
-  const bool stages_own = active && (D == 2 || r < RY) && row_exists;
-  const int64_t row_off = (int64_t)row_mem * A.nx + 4 * tx;     // storage index of the quad
-  const int64_t rec_row = (int64_t)row_mem * (A.nx >> 2) + tx;  // record (quad) index
+  const bool stages_own = active && row_exists;
+  const int64_t row_off = (int64_t)row_mem * A.nx + 4 * tx;  // storage index of the quad in a plane
 
   const int z0 = (int)(((int64_t)blockIdx.x * A.nplanes) / A.nzc);
   const int z1 = (int)(((int64_t)(blockIdx.x + 1) * A.nplanes) / A.nzc);
   auto plane_exists = [&](int p) { return (p >= 0 && p < A.nplanes) || A.pz; };
   auto plane_mem = [&](int p) { return p < 0 ? p + A.nplanes : (p >= A.nplanes ? p - A.nplanes : p); };
-  const int64_t rec_plane = (int64_t)(A.nx >> 2) * (D == 3 ? A.ny : 1);
 
-  // this thread's column in stage k
-  auto col_ptr = [&](int k, int rr, int col) { return stg + k * STAGE + rr * ROW + col * COL; };
-  const uint32_t own_sh = (uint32_t)__cvta_generic_to_shared(col_ptr(0, r, tx));
-  constexpr uint32_t kStageBytes = STAGE * sizeof(P);
+  // wall lanes (a.x, a.y, b.x, b.y) as bits 0..3; box walls off the march axis are fixed per thread
+  uint32_t box_bits = 0;
+  if (A.wall_mode == kWallBox) {
+    if (!A.px) box_bits |= (tx == 0 ? 1u : 0u) | (tx == bxr - 1 ? 8u : 0u);
+    if (D == 3 && !A.py && (row_mem == 0 || row_mem == A.ny - 1)) box_bits = 15u;
+  }
 
-  // start copying plane p into stage p & 3 (or zero it when the plane/row is absent)
-  auto fetch = [&](int p) {
-    const int k = p & (kAdjStages - 1);
-    if (active) {
-      if (stages_own && plane_exists(p)) {
-        const C* src = rec + ((int64_t)plane_mem(p) * rec_plane + rec_row) * 16;
-        const uint32_t sh = own_sh + k * kStageBytes;
+  P force[3];
 #pragma unroll
-        for (int j = 0; j < 16 * (int)sizeof(C) / 16; ++j) cp_async16(sh + 16 * j, src + j * (16 / sizeof(C)));
-      } else {
-        P* d = col_ptr(k, r, tx);
+  for (int i = 0; i < 3; ++i) force[i] = O::splat(C(A.force[i]));
+  C gfp[3] = {C(0), C(0), C(0)};
+  double gfd[3] = {0.0, 0.0, 0.0};
+
+  // post-step state and lam' of this thread's quad in one plane
+  struct Raw {
+    P st[K][2], lm[K][2];
+    uint32_t wall;
+    bool have;
+  };
+  auto load_raw = [&](int p, Raw& R) {
+    R.have = stages_own && plane_exists(p);
+    R.wall = 0;
+    if (R.have) {
+      const int pm = plane_mem(p);
+      const int64_t off = (int64_t)pm * A.plane_stride + row_off;
 #pragma unroll
-        for (int j = 0; j < COL; ++j) d[j] = O::splat(C(0));
+      for (int f = 0; f < K; ++f) {
+        Quad<S>::ld(out_state + f * A.n + off, R.st[f][0], R.st[f][1]);
+        Quad<C>::ld(lam1 + f * A.n + off, R.lm[f][0], R.lm[f][1]);
       }
-    }
-    cp_async_commit();
-  };
-  // after the copies of plane p landed: lane-swapped seam copies
-  auto seam = [&](int p) {
-    const int k = p & (kAdjStages - 1);
-    if (!active) return;
-    if (tx == bxr - 1) {  // swapped pair b -> SEAM_L (left neighbour of thread 0's pair a)
-      const P* s = col_ptr(k, r, tx) + PAIR;
-      P* d = col_ptr(k, r, SEAM_L) + PAIR;
-#pragma unroll
-      for (int j = 0; j < PAIR; ++j) d[j] = O::swap(s[j]);
-    }
-    if (tx == 0) {        // swapped pair a -> SEAM_R (right neighbour of the last pair b)
-      const P* s = col_ptr(k, r, tx);
-      P* d = col_ptr(k, r, SEAM_R);
-#pragma unroll
-      for (int j = 0; j < PAIR; ++j) d[j] = O::swap(s[j]);
-    }
-  };
-  const int col_l = tx == 0 ? SEAM_L : tx - 1;
-  const int col_r = tx == bxr - 1 ? SEAM_R : tx + 1;
-
-  // destination state and lam' (walls) of plane q for this quad
-  const bool x_lo_wall = A.wall_mode == kWallBox && !A.px && tx == 0;
-  const bool x_hi_wall = A.wall_mode == kWallBox && !A.px && tx == bxr - 1;
-  const bool row_wall = D == 3 && !A.py && (row == 0 || row == A.ny - 1);
-
-  fetch(z0 - 1);
-  fetch(z0);
-  for (int q = z0; q < z1; ++q) {
-    fetch(q + 1);
-    cp_async_wait<0>();
-    seam(q - 1);
-    seam(q);
-    seam(q + 1);
-    __syncthreads();
-    if (interior) {
-      const int64_t off = (int64_t)q * A.plane_stride + row_off;
-      P st[K][2];
-#pragma unroll
-      for (int f = 0; f < K; ++f) Quad<S>::ld(in_state + f * A.n + off, st[f][0], st[f][1]);
-      bool wall[4] = {x_lo_wall, false, false, x_hi_wall};
-      const bool plane_wall = !A.pz && (q == 0 || q == A.nplanes - 1);
-      if (row_wall || plane_wall) wall[0] = wall[1] = wall[2] = wall[3] = true;
       if (A.wall_mode == kWallMask) {
         const uchar4 mk = *reinterpret_cast<const uchar4*>(A.mask + off);
-        wall[0] = mk.x != 0; wall[1] = mk.y != 0; wall[2] = mk.z != 0; wall[3] = mk.w != 0;
+        R.wall = (mk.x ? 1u : 0u) | (mk.y ? 2u : 0u) | (mk.z ? 4u : 0u) | (mk.w ? 8u : 0u);
+      } else if (A.wall_mode == kWallBox) {
+        R.wall = (!A.pz && (pm == 0 || pm == A.nplanes - 1)) ? 15u : box_bits;
       }
-      const bool any_wall = wall[0] || wall[1] || wall[2] || wall[3];
+    }
+  };
+
+  uint32_t wq = 0;  // wall bits of the last three staged planes, newest in bits 0..3
+  // records of plane p into stage p & 3 (zeros where the row or plane is absent)
+  auto stage = [&](int p, const Raw& R) {
+    wq = (wq << 4) | R.wall;
+    if (!active) return;
+    const int k = p & (T::STAGES - 1);
+    P rec[2][NU * G];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int c = 0; c < NU * G; ++c) rec[q][c] = O::splat(C(0));
+    if (R.have) {
+      const bool counted = interior && p >= z0 && p < z1 && grad_force;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const P inv = O::rcp(O::add(O::splat(C(1)), R.st[0][q]));
+        P lr = R.lm[0][q];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const P um = O::sub(R.st[1 + i][q], force[i]);  // m' / rho'
+          lr = O::sub(lr, O::mul(O::mul(R.lm[1 + i][q], um), inv));
+          rec[q][1 + i] = O::mul(R.lm[1 + i][q], inv);
+        }
+        rec[q][0] = lr;
+        const bool w0 = (R.wall >> (2 * q)) & 1u, w1 = (R.wall >> (2 * q + 1)) & 1u;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {  // walls carry no (L_r, L_m)
+          if (w0) rec[q][c].x = C(0);
+          if (w1) rec[q][c].y = C(0);
+        }
+        if (counted)
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+            gfp[i] += (w0 ? C(0) : R.lm[1 + i][q].x) + (w1 ? C(0) : R.lm[1 + i][q].y);
+      }
+      if (counted && ((p - z0) & 7) == 7)
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          gfd[i] += (double)gfp[i];
+          gfp[i] = C(0);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int u = 0; u < NU; ++u) U::st(&units[T::unit(k, r, q, u, tx)], &rec[q][u * G]);
+    if (tx == bxr - 1)  // swapped pair b: left neighbour of thread 0's pair a
+#pragma unroll
+      for (int u = 0; u < NU; ++u) U::st_swapped(&units[T::unit(k, r, 1, u, T::SEAM_L)], &rec[1][u * G]);
+    if (tx == 0)        // swapped pair a: right neighbour of the last thread's pair b
+#pragma unroll
+      for (int u = 0; u < NU; ++u) U::st_swapped(&units[T::unit(k, r, 0, u, T::SEAM_R)], &rec[0][u * G]);
+  };
+
+  const int col_l = tx == 0 ? T::SEAM_L : tx - 1;
+  const int col_r = tx == bxr - 1 ? T::SEAM_R : tx + 1;
+
+  {
+    Raw R0, R1;
+    load_raw(z0 - 1, R0);
+    load_raw(z0, R1);
+    stage(z0 - 1, R0);
+    load_raw(z0 + 1, R0);
+    stage(z0, R1);
+    stage(z0 + 1, R0);
+  }
+  Raw R;
+  for (int q = z0; q < z1; ++q) {
+    const bool next = q + 2 <= z1;
+    if (next) load_raw(q + 2, R);
+    const int64_t off = (int64_t)q * A.plane_stride + row_off;
+    const uint32_t wd = (wq >> 4) & 15u;  // wall lanes of plane q
+    P st[K][2], l1[K][2];
+    if (interior) {
+#pragma unroll
+      for (int f = 0; f < K; ++f) Quad<S>::ld(in_state + f * A.n + off, st[f][0], st[f][1]);
+      if (wd)
+#pragma unroll
+        for (int f = 0; f < K; ++f) Quad<C>::ld(lam1 + f * A.n + off, l1[f][0], l1[f][1]);
+    }
+    __syncthreads();  // stages of planes q - 1, q, q + 1 are complete
+    if (interior) {
       P res[K][2];
 #pragma unroll
       for (int qp = 0; qp < 2; ++qp) {
@@ -265,20 +258,22 @@ __global__ void __launch_bounds__(BXC * RY) adj_gather_tiled(AdjArgs A, const S*
         static_for<0, L::Q>([&](auto Ia) {
           constexpr int a = decltype(Ia)::value;
           constexpr int cx = F::fx(a), cy = F::fy(a), cz = F::fz(a);
-          // neighbour y + c_a: stage of plane q + cz, row r + cy, pair by cx
-          const int k = (q + cz) & (kAdjStages - 1);
+          // neighbour y + c_a: stage of plane q + cz, row r + cy, column and pair by cx
+          const int k = (q + cz) & (T::STAGES - 1);
           const int rr = r + cy;
           int col, pr;
           if constexpr (cx == 0) { col = tx; pr = qp; }
           else if constexpr (cx == 1) { if (qp == 0) { col = tx; pr = 1; } else { col = col_r; pr = 0; } }
           else { if (qp == 1) { col = tx; pr = 0; } else { col = col_l; pr = 1; } }
-          const P* rp = col_ptr(k, rr, col) + pr * PAIR;
-          P g = rp[0];
+          P v[NU * G];
+#pragma unroll
+          for (int u = 0; u < NU; ++u) U::ld(&units[T::unit(k, rr, pr, u, col)], &v[u * G]);
+          P g = v[0];
           static_for<0, D>([&](auto Ii) {
             constexpr int i = decltype(Ii)::value;
             constexpr int c = L::c(a, i);
-            if constexpr (c == 1) g = O::add(g, rp[1 + i]);
-            else if constexpr (c == -1) g = O::sub(g, rp[1 + i]);
+            if constexpr (c == 1) g = O::add(g, v[1 + i]);
+            else if constexpr (c == -1) g = O::sub(g, v[1 + i]);
           });
           constexpr int w = L::w36(a);
           const P wg = w == 1 ? g : O::mul(g, O::splat(C(w)));
@@ -327,40 +322,76 @@ __global__ void __launch_bounds__(BXC * RY) adj_gather_tiled(AdjArgs A, const S*
           res[1 + i][qp] = O::mul(rk, t);
         }
       }
-      if (any_wall) {  // a wall node's output is its input: pass lam' through
-        P l1[K][2];
-#pragma unroll
-        for (int f = 0; f < K; ++f) Quad<C>::ld(lam1 + f * A.n + off, l1[f][0], l1[f][1]);
+      if (wd) {  // a wall node's output is its input: pass lam' through
 #pragma unroll
         for (int f = 0; f < K; ++f) {
-          if (wall[0]) res[f][0].x += l1[f][0].x;
-          if (wall[1]) res[f][0].y += l1[f][0].y;
-          if (wall[2]) res[f][1].x += l1[f][1].x;
-          if (wall[3]) res[f][1].y += l1[f][1].y;
+          if (wd & 1u) res[f][0].x += l1[f][0].x;
+          if (wd & 2u) res[f][0].y += l1[f][0].y;
+          if (wd & 4u) res[f][1].x += l1[f][1].x;
+          if (wd & 8u) res[f][1].y += l1[f][1].y;
         }
       }
 #pragma unroll
       for (int f = 0; f < K; ++f) Quad<C>::st(lam0 + f * A.n + off, res[f][0], res[f][1]);
     }
-    __syncthreads();  // stage of plane q - 1 is refilled by the next iteration's fetch
+    if (next) stage(q + 2, R);  // stage (q + 2) & 3 was last read in the gather of plane q - 1
   }
-  cp_async_wait<0>();
+
+  if (grad_force) {
+    // block sum of the force gradient: warp shuffles, then one value per warp
+    __shared__ double red[3][32];
+    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double v = gfd[i] + (double)gfp[i];
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xffffffffu, v, s);
+      if (lane == 0) red[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+      for (int i = 0; i < D; ++i) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += red[i][w];
+        atomicAdd(grad_force + i, s);
+      }
+  }
 }
 
-// Launch helpers (instantiated in adjoint_tiled.cu).
+// Launch helper (instantiated in adjoint_tiled.cu).  Returns the number of
+// blocks of this shape one SM holds through *resident.
 template <int LAT, typename S, int BXC, int RY>
-cudaError_t launch_adj_gather(const AdjArgs& A, const void* in_state, const void* lam1,
-                              const void* rec, void* lam0, cudaStream_t st, dim3 grid) {
-  using C = typename Store<S>::C;
-  auto kern = adj_gather_tiled<LAT, S, BXC, RY>;
-  constexpr size_t smem = adj_stage_bytes<C, BXC, RY>();
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_adj_tiled(const AdjArgs& A, const void* in_state, const void* out_state,
+                             const void* lam1, void* lam0, double* grad_force, cudaStream_t st,
+                             int ytiles, int* resident_out) {
+  using T = AdjTile<LAT, S, BXC, RY>;
+  using C = typename T::C;
+  auto kern = adj_step_tiled<LAT, S, BXC, RY>;
+  constexpr size_t smem = T::smem_bytes();
+  static int resident_dev[64] = {};  // per instantiation and device
+  int dev = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 != cudaSuccess) return e0;
+  int& resident = resident_dev[dev & 63];
+  if (!resident) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int nb = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, T::THREADS, smem);
     if (e != cudaSuccess) return e;
+    resident = nb < 1 ? 1 : nb;
   }
-  kern<<<grid, dim3(BXC, RY), smem, st>>>(A, static_cast<const S*>(in_state),
-                                          static_cast<const C*>(lam1), static_cast<const C*>(rec),
-                                          static_cast<C*>(lam0));
+  if (resident_out) {  // sizing query only
+    *resident_out = resident;
+    return cudaSuccess;
+  }
+  kern<<<dim3(A.nzc, ytiles), dim3(BXC, RY), smem, st>>>(
+      A, static_cast<const S*>(in_state), static_cast<const S*>(out_state), static_cast<const C*>(lam1),
+      static_cast<C*>(lam0), grad_force);
   return cudaGetLastError();
 }
 

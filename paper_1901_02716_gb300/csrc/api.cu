@@ -463,8 +463,9 @@ static size_t adjoint_bytes(const maclab_ctx* h) {
   return (size_t)(h->g.d + 1) * (size_t)h->g.n * (h->precision == MACLAB_F64 ? 8 : 4);
 }
 
-static maclab_status ensure_adjoint(maclab_ctx* h) {
-  if (!h->d_adj_scratch) {
+// records: the per-node (L_r, L_m) buffer that only the reference kernels use
+static maclab_status ensure_adjoint(maclab_ctx* h, bool records = false) {
+  if (records && !h->d_adj_scratch) {
     // one 4-value record per node
     const size_t rec = 4 * (size_t)h->g.n * (h->precision == MACLAB_F64 ? 8 : 4);
     if (cudaMalloc(&h->d_adj_scratch, rec) != cudaSuccess) {
@@ -494,12 +495,13 @@ maclab_status maclab_adjoint_step(maclab_handle h, const void* state_n, const vo
   if (!h || !state_n || !state_np1 || !lam_np1 || !lam_n) return fail(MACLAB_ERR_INVALID, "NULL argument");
   if (lam_n == lam_np1) return fail(MACLAB_ERR_INVALID, "lam_n must not alias lam_np1");
   DeviceGuard dg(h->device);
-  maclab_status s = ensure_adjoint(h);
-  if (s != MACLAB_OK) return s;
   // the tiled reverse step where it is built (unless the reference kernel was chosen)
-  if (h->kernel != MACLAB_KERNEL_REFERENCE && tiled_adjoint_supported(h->g, h->precision)) {
+  const bool tiled = h->kernel != MACLAB_KERNEL_REFERENCE && tiled_adjoint_supported(h->g, h->precision);
+  maclab_status s = ensure_adjoint(h, !tiled);
+  if (s != MACLAB_OK) return s;
+  if (tiled) {
     CUDA_TRY(launch_tiled_adjoint(h->g, h->precision, state_n, state_np1, lam_np1, lam_n,
-                                  h->d_adj_scratch, h->force_lat, grad_force, h->stream),
+                                  h->force_lat, grad_force, h->stream),
              "adjoint step");
   } else {
     CUDA_TRY(launch_adjoint_step(h->g, h->precision, state_n, state_np1, lam_np1, lam_n,

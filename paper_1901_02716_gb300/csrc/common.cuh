@@ -142,8 +142,7 @@ cudaError_t launch_adjoint_step(const Geometry& g, int precision, const void* st
 bool tiled_adjoint_supported(const Geometry& g, int precision);
 cudaError_t launch_tiled_adjoint(const Geometry& g, int precision, const void* state_n,
                                  const void* state_np1, const void* lam_np1, void* lam_n,
-                                 void* records, const double force_lat[3], double* grad_force,
-                                 cudaStream_t st);
+                                 const double force_lat[3], double* grad_force, cudaStream_t st);
 cudaError_t launch_adjoint_seed(const Geometry& g, int precision, const void* grho, const void* gu,
                                 int dtype, const void* state, double rho0, double e, void* lam,
                                 double* dot, cudaStream_t st);
@@ -205,6 +204,6 @@ struct maclab_ctx {
   int graph_steps = 32;
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
-  void* d_adj_scratch = nullptr;   // adjoint: (L_r, L_m) at every node
+  void* d_adj_scratch = nullptr;   // reference adjoint: (L_r, L_m) at every node
   double* d_adj_red = nullptr;     // adjoint: reductions (1 + 4 * n_wall_ids doubles)
 };
