@@ -38,6 +38,13 @@ struct AdjArgs {
   double force[3];
 };
 
+// a - b as fma(b, -1, a): the same correctly rounded difference, written
+// without inline assembly so the compiler schedules it freely
+template <typename C>
+__device__ __forceinline__ typename Pair<C>::P adj_sub(typename Pair<C>::P a, typename Pair<C>::P b) {
+  return Pair<C>::fma(b, Pair<C>::splat(C(-1)), a);
+}
+
 // 16-byte unit <-> lane pairs
 template <typename P>
 struct AdjUnit;
@@ -182,8 +189,8 @@ __global__ void __launch_bounds__(BXC * RY, (AdjTile<LAT, S, BXC, RY>::MIN_BLOCK
         P lr = R.lm[0][q];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-          const P um = O::sub(R.st[1 + i][q], force[i]);  // m' / rho'
-          lr = O::sub(lr, O::mul(O::mul(R.lm[1 + i][q], um), inv));
+          const P um = adj_sub<C>(R.st[1 + i][q], force[i]);  // m' / rho'
+          lr = adj_sub<C>(lr, O::mul(O::mul(R.lm[1 + i][q], um), inv));
           rec[q][1 + i] = O::mul(R.lm[1 + i][q], inv);
         }
         rec[q][0] = lr;
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(BXC * RY, (AdjTile<LAT, S, BXC, RY>::MIN_BLOCK
             constexpr int i = decltype(Ii)::value;
             constexpr int c = L::c(a, i);
             if constexpr (c == 1) g = O::add(g, v[1 + i]);
-            else if constexpr (c == -1) g = O::sub(g, v[1 + i]);
+            else if constexpr (c == -1) g = adj_sub<C>(g, v[1 + i]);
           });
           constexpr int w = L::w36(a);
           const P wg = w == 1 ? g : O::mul(g, O::splat(C(w)));
@@ -282,12 +289,12 @@ __global__ void __launch_bounds__(BXC * RY, (AdjTile<LAT, S, BXC, RY>::MIN_BLOCK
             constexpr int i = decltype(Ii)::value;
             constexpr int ci = L::c(a, i);
             if constexpr (ci != 0) {
-              G1[i] = ci > 0 ? O::add(G1[i], wg) : O::sub(G1[i], wg);
+              G1[i] = ci > 0 ? O::add(G1[i], wg) : adj_sub<C>(G1[i], wg);
               G2[i][i] = O::add(G2[i][i], wg);
               static_for<i + 1, D>([&](auto Ij) {
                 constexpr int j = decltype(Ij)::value;
                 constexpr int cj = L::c(a, j);
-                if constexpr (cj != 0) G2[i][j] = ci * cj > 0 ? O::add(G2[i][j], wg) : O::sub(G2[i][j], wg);
+                if constexpr (cj != 0) G2[i][j] = ci * cj > 0 ? O::add(G2[i][j], wg) : adj_sub<C>(G2[i][j], wg);
               });
             }
           });
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(BXC * RY, (AdjTile<LAT, S, BXC, RY>::MIN_BLOCK
 #pragma unroll
         for (int i = 0; i < D; ++i) {
           P t = O::fma(G2u[i], O::splat(C(9)), O::mul(G1[i], O::splat(C(3))));
-          t = O::sub(t, O::mul(O::mul(u[i], G0), O::splat(C(3))));
+          t = adj_sub<C>(t, O::mul(O::mul(u[i], G0), O::splat(C(3))));
           res[1 + i][qp] = O::mul(rk, t);
         }
       }

@@ -799,20 +799,31 @@ __global__ void __launch_bounds__(BXC * RY, TiledMinBlocks<BXC, RY>::value)
     store_plane<LAT, S>(op, mrow, ta, (int64_t)(z1 - 1) * ps, x_lo_wall, x_hi_wall,
                         store_skip(z1 - 1), B, force);
   };
-  // roles rotate with period 3 and buffers alternate: unroll by 6
-  for (int p = z0;; p += 6) {
-    step(1, p, R0, R1, R2);
-    if (p + 1 >= z1) { last(0, R1); break; }
-    step(0, p + 1, R1, R2, R0);
-    if (p + 2 >= z1) { last(1, R2); break; }
-    step(1, p + 2, R2, R0, R1);
-    if (p + 3 >= z1) { last(0, R0); break; }
-    step(0, p + 3, R0, R1, R2);
-    if (p + 4 >= z1) { last(1, R1); break; }
-    step(1, p + 4, R1, R2, R0);
-    if (p + 5 >= z1) { last(0, R2); break; }
-    step(0, p + 5, R2, R0, R1);
-    if (p + 6 >= z1) { last(1, R0); break; }
+  // roles rotate with period 3 (and, double buffered, the exchange arrays alternate)
+  if constexpr (kDoubleBuffer) {
+    for (int p = z0;; p += 6) {
+      step(1, p, R0, R1, R2);
+      if (p + 1 >= z1) { last(0, R1); break; }
+      step(0, p + 1, R1, R2, R0);
+      if (p + 2 >= z1) { last(1, R2); break; }
+      step(1, p + 2, R2, R0, R1);
+      if (p + 3 >= z1) { last(0, R0); break; }
+      step(0, p + 3, R0, R1, R2);
+      if (p + 4 >= z1) { last(1, R1); break; }
+      step(1, p + 4, R1, R2, R0);
+      if (p + 5 >= z1) { last(0, R2); break; }
+      step(0, p + 5, R2, R0, R1);
+      if (p + 6 >= z1) { last(1, R0); break; }
+    }
+  } else {  // one exchange array: unroll by 3 only (half the code of the loop above)
+    for (int p = z0;; p += 3) {
+      step(0, p, R0, R1, R2);
+      if (p + 1 >= z1) { last(0, R1); break; }
+      step(0, p + 1, R1, R2, R0);
+      if (p + 2 >= z1) { last(0, R2); break; }
+      step(0, p + 2, R2, R0, R1);
+      if (p + 3 >= z1) { last(0, R0); break; }
+    }
   }
   cp_async_wait<0>();
 }
