@@ -292,6 +292,15 @@ maclab_status maclab_diagnostics_noalloc(int32_t lattice, int32_t precision, int
                                          const uint8_t *exclude, double *out_sums,
                                          void *stream);
 
+/* Self-check of the reciprocal the FP32 kernels use for u' = m' / rho'
+ * (Eq. (5)): evaluates it on the device at n points spaced geometrically over
+ * [lo, hi] (0 < lo < hi, 1 <= n <= 2^24) and stores the largest relative error
+ * against 1/x in FP64 in *max_rel_err.  No paper counterpart: it checks an
+ * implementation choice (a hardware approximation refined by one
+ * Newton-Raphson step).  Runs on the current device, synchronously.
+ * Errors: MACLAB_ERR_INVALID (arguments), MACLAB_ERR_OOM, MACLAB_ERR_CUDA. */
+maclab_status maclab_check_reciprocal(float lo, float hi, int32_t n, double *max_rel_err);
+
 /* Run the handle's stream to completion and report any CUDA error. */
 maclab_status maclab_sync(maclab_handle h);
 

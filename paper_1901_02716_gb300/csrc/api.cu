@@ -126,6 +126,27 @@ const char* maclab_status_string(maclab_status s) {
 
 const char* maclab_version(void) { return "maclab sm_103a"; }
 
+maclab_status maclab_check_reciprocal(float lo, float hi, int32_t n, double* max_rel_err) {
+  if (!max_rel_err) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (!(lo > 0.0f) || !(hi > lo) || !isfinite(hi) || n < 1 || n > (1 << 24))
+    return fail(MACLAB_ERR_INVALID, "need 0 < lo < hi (finite) and 1 <= n <= 2^24");
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MACLAB_ERR_OOM, "reciprocal check allocation failed");
+  }
+  unsigned long long bits = 0;
+  cudaError_t e = cudaMemset(d, 0, sizeof(bits));
+  if (e == cudaSuccess) e = launch_check_reciprocal(lo, hi, n, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "reciprocal check");
+  double v;
+  memcpy(&v, &bits, sizeof(v));
+  *max_rel_err = v;
+  return MACLAB_OK;
+}
+
 const char* maclab_last_error(void) { return g_last_error.c_str(); }
 
 maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {

@@ -138,6 +138,10 @@ cudaError_t launch_adjoint_step(const Geometry& g, int precision, const void* st
                                 const void* state_np1, const void* lam_np1, void* lam_n,
                                 void* scratch, const double force_lat[3], double* grad_force,
                                 cudaStream_t st);
+// Defined in selfcheck.cu: the largest relative error of the FP32 pair
+// reciprocal over n points in [lo, hi], as double bits, into *d_worst.
+cudaError_t launch_check_reciprocal(float lo, float hi, int n, unsigned long long* d_worst,
+                                    cudaStream_t st);
 // Defined in adjoint_tiled.cu (domains with interleaved rows).
 bool tiled_adjoint_supported(const Geometry& g, int precision);
 cudaError_t launch_tiled_adjoint(const Geometry& g, int precision, const void* state_n,

@@ -1,0 +1,37 @@
+// selfcheck.cu -- device check of the paired FP32 reciprocal (Pair<float>::rcp)
+// that the tiled and batched kernels use for u' = m' / rho' (Eq. (5)).
+
+#include "step_tiled.cuh"
+
+namespace maclab {
+
+namespace {
+
+// x_i = lo (hi / lo)^(i / (n - 1)); the largest |rcp(x) x - 1| over all points,
+// as the bit pattern of a non-negative double (ordered like unsigned integers).
+__global__ void rcp_check_k(double lo, double ratio, int n, unsigned long long* worst) {
+  const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= n) return;
+  const int i1 = i0 + 1 < n ? i0 + 1 : i0;
+  const double den = n > 1 ? (double)(n - 1) : 1.0;
+  const float x0 = (float)(lo * pow(ratio, i0 / den));
+  const float x1 = (float)(lo * pow(ratio, i1 / den));
+  const float2 r = Pair<float>::rcp(make_float2(x0, x1));
+  const double e0 = fabs((double)r.x * (double)x0 - 1.0);
+  const double e1 = fabs((double)r.y * (double)x1 - 1.0);
+  const double e = e0 > e1 ? e0 : e1;
+  atomicMax(worst, (unsigned long long)__double_as_longlong(e));
+}
+
+}  // namespace
+
+cudaError_t launch_check_reciprocal(float lo, float hi, int n, unsigned long long* d_worst,
+                                    cudaStream_t st) {
+  const int pairs = (n + 1) / 2;
+  const int threads = 256;
+  rcp_check_k<<<(pairs + threads - 1) / threads, threads, 0, st>>>((double)lo, (double)hi / (double)lo, n,
+                                                                   d_worst);
+  return cudaGetLastError();
+}
+
+}  // namespace maclab

@@ -104,7 +104,20 @@ struct Pair<float> {
   }
   __device__ __forceinline__ static P mul(P a, P b) { return __fmul2_rn(a, b); }
   __device__ __forceinline__ static P fma(P a, P b, P c) { return __ffma2_rn(a, b, c); }
-  __device__ __forceinline__ static P rcp(P a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+  // 1/a on both lanes: the hardware approximation r0 (rcp.approx, relative
+  // error below 2^-22) refined by one Newton-Raphson step for f(r) = 1/r - a,
+  // r1 = r0 + r0 (1 - a r0), on the paired FMA datapath.  The residual
+  // 1 - a r0 is formed exactly by the FMA, so r1 is within about half an ulp
+  // of 1/a (checked by maclab_check_reciprocal).  The arguments here are
+  // 36 + R and 1 + drho, far from zero, infinities and subnormals.
+  __device__ __forceinline__ static P rcp(P a) {
+    float r0, r1;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(a.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(a.y));
+    const P r = make_float2(r0, r1);
+    const P e = __ffma2_rn(make_float2(-a.x, -a.y), r, make_float2(1.f, 1.f));
+    return __ffma2_rn(r, e, r);
+  }
   __device__ __forceinline__ static P swap(P a) { return make_float2(a.y, a.x); }
 };
 

@@ -93,6 +93,8 @@ SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_char_p)]),
     "maclab_status_string": (ctypes.c_char_p, [_S]),
     "maclab_version": (ctypes.c_char_p, []),
+    "maclab_check_reciprocal": (_S, [ctypes.c_float, ctypes.c_float, ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_double)]),
     "maclab_last_error": (ctypes.c_char_p, []),
 }
 
@@ -322,6 +324,14 @@ def maclab_status_string(s):
 
 def maclab_version():
     return lib().maclab_version().decode()
+
+
+def maclab_check_reciprocal(lo, hi, n):
+    """Largest relative error of the FP32 kernels' reciprocal over n points in [lo, hi]."""
+    out = ctypes.c_double()
+    _check(lib().maclab_check_reciprocal(float(lo), float(hi), int(n), ctypes.byref(out)),
+           "maclab_check_reciprocal")
+    return out.value
 
 
 # ---------------------------------------------------------------- solver object

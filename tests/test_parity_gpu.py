@@ -237,3 +237,12 @@ def test_full_size_box_walls(lat, n):
     dims = (n,) * (3 if lat == D3 else 2)
     case = inputs.random_case(lat, dims, 0, seed=36, u_amp=0.08, rho_amp=0.02, walls="box")
     assert_parity(*run_both(case, M.F32, 3), M.F32)
+
+
+@pytest.mark.parametrize("lo,hi", [(0.5, 2.0), (30.0, 42.0), (1e-3, 1e3)])
+def test_pair_reciprocal_error_bound(lo, hi):
+    """The FP32 kernels divide by 1 + drho' and 36 + R through a hardware
+    reciprocal refined by one Newton-Raphson step: within one ulp (2^-23
+    relative) of 1/x over the ranges those arguments take, and beyond."""
+    err = M.maclab_check_reciprocal(lo, hi, 1 << 20)
+    assert 0.0 <= err <= 2.0 ** -23
