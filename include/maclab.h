@@ -130,23 +130,27 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
 
 /* Step kernels.  MACLAB_KERNEL_AUTO lets the library choose (the default);
  * MACLAB_KERNEL_REFERENCE is the simple one-thread-per-node gather, kept as the
- * GPU-side yardstick; MACLAB_KERNEL_TILED is the staged, vectorised kernel.
- * Both compute Eqs. (4)-(5) with the same arithmetic per node. */
+ * GPU-side yardstick; MACLAB_KERNEL_TILED is the staged, vectorised kernel;
+ * MACLAB_KERNEL_FOLDED is its D3Q19 FP32 form without halo-row threads (the
+ * tile's edge rows fold their halo rows in; needs ny divisible by the tile's
+ * rows).  All compute Eqs. (4)-(5) with the same terms per node (the folded
+ * kernel sums them in another order). */
 #define MACLAB_KERNEL_AUTO 0
 #define MACLAB_KERNEL_REFERENCE 1
 #define MACLAB_KERNEL_TILED 2
+#define MACLAB_KERNEL_FOLDED 3
 
 /* Choose the step kernel.  MACLAB_ERR_UNSUPPORTED if the tiled kernel cannot
  * serve this domain (then the handle keeps its previous choice). */
 maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel);
 
-/* Tile shape of the tiled kernel: ty rows of y per block (3D only) and tz
+/* Tile shape of the tiled (or folded) kernel in use: ty rows of y per block (3D only) and tz
  * planes of the slowest axis per block; 0 keeps the library's default.
  * MACLAB_ERR_UNSUPPORTED if no built instance has that shape for this domain
  * (the previous shape is kept). */
 maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz);
 
-/* Describe the kernel in use: out[0] = kernel id (REFERENCE or TILED),
+/* Describe the kernel in use: out[0] = kernel id (REFERENCE, TILED or FOLDED),
  * out[1] = time steps advanced per launch, out[2] = kernel launches per
  * launch group, out[3] = threads per block (out[3] = 0 and out[1..2] = 1 for
  * the reference kernel's grid-stride launch of 256-thread blocks).  *name (may be NULL) receives a
@@ -202,8 +206,9 @@ maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows);
 maclab_status maclab_batch_info(maclab_batch b, int64_t out[6]);
 
 /* ---------------------------------------------------------------- tuning
- * Time the candidate shapes of the tiled kernel (rows per tile, planes per
- * block) on this handle's domain and keep the fastest; the state is saved
+ * Time the candidate shapes of the tiled and folded kernels (rows per tile,
+ * planes per block) on this handle's domain and keep the fastest kernel and
+ * shape; the state is saved
  * before and restored after (temporary device buffers are allocated).
  * Results are cached per (lattice, precision, dims, periodicity, wall mode,
  * device) for the process.  out (may be NULL) receives the chosen ty, tz. */

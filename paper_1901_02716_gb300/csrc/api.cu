@@ -619,19 +619,23 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
     h->kernel = pick_step_kernel(h->g, h->precision);
     return MACLAB_OK;
   }
-  if (kernel != MACLAB_KERNEL_REFERENCE && kernel != MACLAB_KERNEL_TILED)
+  if (kernel != MACLAB_KERNEL_REFERENCE && kernel != MACLAB_KERNEL_TILED && kernel != MACLAB_KERNEL_FOLDED)
     return fail(MACLAB_ERR_INVALID, "unknown kernel id");
   if (!step_kernel_supported(h->g, h->precision, kernel))
     return fail(MACLAB_ERR_UNSUPPORTED, "kernel does not support this domain");
   h->kernel = kernel;
+  // a tile shape the new kernel lacks falls back to its default
+  if (kernel == MACLAB_KERNEL_FOLDED && !fold_supported(h->g, h->precision, h->ty)) h->ty = 0;
+  if (kernel == MACLAB_KERNEL_TILED && !tiled_supported(h->g, h->precision, h->ty, h->tz)) h->ty = 0;
   return MACLAB_OK;
 }
 
 maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (ty < 0 || tz < 0 || tz > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad tile shape");
-  if (!tiled_supported(h->g, h->precision, ty, tz))
-    return fail(MACLAB_ERR_UNSUPPORTED, "no built tiled instance has this shape");
+  const bool ok = h->kernel == MACLAB_KERNEL_FOLDED ? fold_supported(h->g, h->precision, ty)
+                                                    : tiled_supported(h->g, h->precision, ty, tz);
+  if (!ok) return fail(MACLAB_ERR_UNSUPPORTED, "no built tiled instance has this shape");
   drop_graphs(h);
   h->ty = ty;
   h->tz = tz;
@@ -906,7 +910,15 @@ maclab_status maclab_batch_info(maclab_batch b, int64_t out[6]) {
 namespace {
 
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune_cache;
+struct TuneChoice {
+  int kernel, ty, tz;
+};
+std::map<std::string, TuneChoice> g_tune_cache;
+
+bool shape_supported(const maclab_ctx* h, int kernel, int ty, int tz) {
+  return kernel == MACLAB_KERNEL_FOLDED ? fold_supported(h->g, h->precision, ty)
+                                        : tiled_supported(h->g, h->precision, ty, tz);
+}
 
 std::string tune_key(const maclab_ctx* h) {
   char buf[160];
@@ -946,11 +958,11 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      if (tiled_supported(h->g, h->precision, it->second.first, it->second.second)) {
+      if (shape_supported(h, it->second.kernel, it->second.ty, it->second.tz)) {
         drop_graphs(h);
-        h->kernel = MACLAB_KERNEL_TILED;
-        h->ty = it->second.first;
-        h->tz = it->second.second;
+        h->kernel = it->second.kernel;
+        h->ty = it->second.ty;
+        h->tz = it->second.tz;
       }
       if (out) { out[0] = h->ty; out[1] = h->tz; }
       return MACLAB_OK;
@@ -974,26 +986,28 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
   const int tys3[] = {2, 4, 8};
   const int tzs[] = {0, 4, 8, 16, 32};
   float best = 1e30f;
-  int bty = 0, btz = 0;
+  int bkernel = MACLAB_KERNEL_TILED, bty = 0, btz = 0;
   drop_graphs(h);
-  h->kernel = MACLAB_KERNEL_TILED;
   const int n_ty = h->g.d == 3 ? 3 : 1;
-  for (int a = 0; a < n_ty; ++a)
-    for (int tz : tzs) {
-      const int ty = h->g.d == 3 ? tys3[a] : 0;
-      if (!tiled_supported(h->g, h->precision, ty, tz)) continue;
-      h->ty = ty;
-      h->tz = tz;
-      const float ms = time_ms(h->stream, 10, [&]() {
-        launch_step(step_launch(h, h->cur), h->stream, h->kernel);
-        h->cur ^= 1;
-      });
-      if (ms < best) {
-        best = ms;
-        bty = ty;
-        btz = tz;
+  for (int kernel : {MACLAB_KERNEL_TILED, MACLAB_KERNEL_FOLDED})
+    for (int a = 0; a < n_ty; ++a)
+      for (int tz : tzs) {
+        const int ty = h->g.d == 3 ? tys3[a] : 0;
+        if (!shape_supported(h, kernel, ty, tz)) continue;
+        h->kernel = kernel;
+        h->ty = ty;
+        h->tz = tz;
+        const float ms = time_ms(h->stream, 10, [&]() {
+          launch_step(step_launch(h, h->cur), h->stream, h->kernel);
+          h->cur ^= 1;
+        });
+        if (ms < best) {
+          best = ms;
+          bkernel = kernel;
+          bty = ty;
+          btz = tz;
+        }
       }
-    }
   cudaError_t e = cudaGetLastError();
   // restore
   h->cur = 0;
@@ -1010,11 +1024,12 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
     h->tz = tz0;
     return cuda_fail(e, "tuning launch");
   }
+  h->kernel = bkernel;
   h->ty = bty;
   h->tz = btz;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = {bty, btz};
+    g_tune_cache[key] = TuneChoice{bkernel, bty, btz};
   }
   if (out) { out[0] = bty; out[1] = btz; }
   return MACLAB_OK;

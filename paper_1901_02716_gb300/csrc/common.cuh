@@ -107,7 +107,7 @@ struct StepLaunch {
 
 // Defined in step.cu.  Kernel ids follow MACLAB_KERNEL_* of maclab.h.
 struct KernelInfo {
-  int id;                // MACLAB_KERNEL_REFERENCE / MACLAB_KERNEL_TILED
+  int id;                // MACLAB_KERNEL_REFERENCE / _TILED / _FOLDED
   int steps_per_launch;  // time steps one launch group advances
   int launches;          // kernel launches in one group
   int threads;           // threads per block
@@ -123,6 +123,11 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel);
 bool tiled_supported(const Geometry& g, int precision, int ty, int tz);
 cudaError_t launch_tiled(const StepLaunch& s, cudaStream_t stream, int ty, int tz);
 int tiled_threads(const Geometry& g, int precision, int ty, int tz);
+
+// Defined in step_fold.cu (D3Q19 FP32 without halo-row threads).
+bool fold_supported(const Geometry& g, int precision, int ty);
+int fold_threads(const Geometry& g, int precision, int ty);
+cudaError_t launch_fold(const StepLaunch& s, cudaStream_t stream, int ty, int tz);
 
 // Defined in api.cu: message returned by maclab_last_error on this thread.
 void record_error(const char* msg);

@@ -121,15 +121,20 @@ static cudaError_t launch_naive_lat(const StepLaunch& s, cudaStream_t stream) {
 bool step_kernel_supported(const Geometry& g, int precision, int kernel) {
   if (kernel == MACLAB_KERNEL_REFERENCE) return true;
   if (kernel == MACLAB_KERNEL_TILED) return tiled_supported(g, precision, 0, 0);
+  if (kernel == MACLAB_KERNEL_FOLDED) return fold_supported(g, precision, 0);
   return false;
 }
 
+// The folded kernel where it is built (D3Q19 FP32, ny a multiple of its tile
+// rows), else the tiled one, else the reference kernel.
 int pick_step_kernel(const Geometry& g, int precision) {
+  if (step_kernel_supported(g, precision, MACLAB_KERNEL_FOLDED)) return MACLAB_KERNEL_FOLDED;
   return step_kernel_supported(g, precision, MACLAB_KERNEL_TILED) ? MACLAB_KERNEL_TILED
                                                                  : MACLAB_KERNEL_REFERENCE;
 }
 
 static const char* kernel_name(const Geometry& g, int precision, int kernel) {
+  if (kernel == MACLAB_KERNEL_FOLDED) return "step_fold<D3Q19,f32>";
   static const char* names[2][2][4] = {
       {{"step_naive<D2Q9,f64>", "step_naive<D2Q9,f32>", "step_naive<D2Q9,bf16>",
         "step_naive<D2Q9,f16>"},
@@ -146,6 +151,9 @@ KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, in
   if (kernel == MACLAB_KERNEL_TILED)
     return KernelInfo{MACLAB_KERNEL_TILED, 1, 1, tiled_threads(g, precision, ty, tz),
                       kernel_name(g, precision, kernel)};
+  if (kernel == MACLAB_KERNEL_FOLDED)
+    return KernelInfo{MACLAB_KERNEL_FOLDED, 1, 1, fold_threads(g, precision, ty),
+                      kernel_name(g, precision, kernel)};
   return KernelInfo{MACLAB_KERNEL_REFERENCE, 1, 1, 256, kernel_name(g, precision, kernel)};
 }
 
@@ -156,6 +164,8 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel) {
                                   : launch_naive_lat<kD3Q19>(s, stream);
     case MACLAB_KERNEL_TILED:
       return launch_tiled(s, stream, s.ty, s.tz);
+    case MACLAB_KERNEL_FOLDED:
+      return launch_fold(s, stream, s.ty, s.tz);
     default:
       return cudaErrorInvalidValue;
   }

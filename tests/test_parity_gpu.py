@@ -127,6 +127,71 @@ def test_tiled_matches_reference_kernel(lat, dims, periodic, walls):
     assert np.abs(u1 - u2).max() < 2e-6 * np.abs(u1).max()
 
 
+# The folded D3Q19 kernel (no halo-row threads): FP32, x a multiple of 4 up to
+# 256, ny a multiple of the tile's rows; one-tile y extents wrap onto themselves.
+FOLD_CASES = [
+    ((8, 8, 5), 0b111, "none", 0),
+    ((12, 8, 9), 0b000, "box", 0),
+    ((16, 16, 19), 0b101, "mixed", 0),
+    ((32, 16, 7), 0b011, "box", 0),
+    ((128, 8, 6), 0b000, "box", 0),
+    ((96, 12, 10), 0b010, "mixed", 0),
+    ((256, 8, 5), 0b111, "none", 0),
+    ((4, 8, 3), 0b111, "none", 0),
+    ((20, 16, 17), 0b100, "mixed", 0),
+    ((128, 4, 9), 0b111, "none", 0),
+    ((128, 16, 11), 0b000, "box", 8),
+    ((64, 24, 13), 0b110, "mixed", 8),
+]
+
+
+@pytest.mark.parametrize("dims,periodic,walls,ty", FOLD_CASES)
+@pytest.mark.parametrize("steps", [1, 5])
+def test_folded_kernel(dims, periodic, walls, ty, steps):
+    case = inputs.random_case(D3, dims, periodic, seed=41, u_amp=0.08, rho_amp=0.02,
+                              walls=walls, force=(1e-4, -2e-4, 3e-4))
+    s = M.Solver.from_case(case, M.F32)
+    s.set_kernel(M.KERNEL_FOLDED)
+    if ty:
+        s.set_tile(ty, 0)
+    assert s.kernel_info()["kernel"] == M.KERNEL_FOLDED
+    s.step(steps)
+    r_g, u_g = s.get_state()
+    s.close()
+    r_o, u_o = orc.step(D3, case.rho, case.u, case.periodic, wall=case.wall_mask,
+                        force=case.force, nsteps=steps)
+    assert_parity(r_g, u_g, r_o, u_o, M.F32)
+
+
+@pytest.mark.parametrize("dims,periodic,walls,ty", FOLD_CASES)
+def test_folded_matches_tiled_kernel(dims, periodic, walls, ty):
+    """Same terms, summed in another order: FP32 results agree to rounding."""
+    case = inputs.random_case(D3, dims, periodic, seed=42, u_amp=0.08, rho_amp=0.02, walls=walls)
+    out = []
+    for kern in (M.KERNEL_TILED, M.KERNEL_FOLDED):
+        s = M.Solver.from_case(case, M.F32)
+        s.set_kernel(kern)
+        s.step(10)
+        out.append(s.get_state())
+        s.close()
+    (r1, u1), (r2, u2) = out
+    assert np.abs(r1 - r2).max() < 1e-6
+    assert np.abs(u1 - u2).max() < 2e-6 * np.abs(u1).max()
+
+
+@pytest.mark.parametrize("precision,dims", [(M.F64, (32, 8, 5)), (M.F32, (32, 6, 5)),
+                                            (M.F32, (16, 12, 5))])
+def test_folded_rejects_unsupported(precision, dims):
+    case = inputs.random_case(D3, dims, 0b111, seed=43)
+    s = M.Solver.from_case(case, precision)
+    before = s.kernel_info()["kernel"]
+    with pytest.raises(M.MacLABError) as ei:
+        s.set_kernel(M.KERNEL_FOLDED)
+    assert ei.value.status == M.ERR_UNSUPPORTED
+    assert s.kernel_info()["kernel"] == before
+    s.close()
+
+
 def test_tiled_rejects_unsupported_shape():
     case = inputs.random_case(D2, (17, 13), 0b11, seed=39)
     s = M.Solver.from_case(case, M.F32)
