@@ -11,13 +11,13 @@ namespace {
 struct FoldShape {
   int bxc, ty;
 };
-constexpr FoldShape kFoldShapes[] = {{16, 8}, {32, 4}, {32, 8}, {64, 4}};
+constexpr FoldShape kFoldShapes[] = {{16, 8}, {32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}};
 
 bool fold_shape(const Geometry& g, int precision, int ty_req, FoldShape* out) {
   if (g.d != 3 || g.lattice != kD3Q19 || !g.ilv || precision != MACLAB_F32) return false;
   const int bx = g.nx / 4;
   int bxc = 0;
-  for (int c : {16, 32, 64})
+  for (int c : {16, 32, 64, 128})
     if (bx <= c) { bxc = c; break; }
   if (!bxc) return false;
   for (const FoldShape& s : kFoldShapes) {
@@ -37,6 +37,8 @@ cudaError_t fold_dispatch(const FoldShape& s, const TiledArgs& ta, const void* i
     case 3204: return launch_fold_shape<S, 32, 4>(ta, in, out, st, grid, resident);
     case 3208: return launch_fold_shape<S, 32, 8>(ta, in, out, st, grid, resident);
     case 6404: return launch_fold_shape<S, 64, 4>(ta, in, out, st, grid, resident);
+    case 6408: return launch_fold_shape<S, 64, 8>(ta, in, out, st, grid, resident);
+    case 12804: return launch_fold_shape<S, 128, 4>(ta, in, out, st, grid, resident);
   }
   return cudaErrorInvalidValue;
 }
@@ -51,13 +53,17 @@ int sm_count() {
   return sms;
 }
 
-// Chunks of the march axis: an explicit tz gives ceil(nplanes / tz); by
-// default about 8 planes per chunk, the block count rounded up to whole waves
-// of resident blocks, chunks of at least 4 planes.
+// Chunks of the march axis: an explicit tz gives ceil(nplanes / tz).  By
+// default the chunks are as long as possible (every chunk re-reads and
+// half-processes a plane at each end) while the grid still fills two waves of
+// resident blocks: 32 planes, halved down to 8 until it does; then the block
+// count is rounded up to whole waves and chunks are kept to at least 4 planes.
 int fold_chunks(int nplanes, int ytiles, int tz_req, int per_sm) {
   if (tz_req > 0) return (nplanes + tz_req - 1) / tz_req;
   const long slots = (long)sm_count() * (per_sm < 1 ? 1 : per_sm);
-  const long blocks = (long)((nplanes + 7) / 8) * ytiles;
+  int tz = 32;
+  while (tz > 8 && (long)((nplanes + tz - 1) / tz) * ytiles < 2 * slots) tz /= 2;
+  const long blocks = (long)((nplanes + tz - 1) / tz) * ytiles;
   const long waves = (blocks + slots - 1) / slots;
   int nzc = (int)((waves * slots) / ytiles);
   const int max_chunks = nplanes / 4 > 0 ? nplanes / 4 : 1;

@@ -88,12 +88,13 @@ __device__ __forceinline__ void fold_halo(const typename Pair<C>::P (&hs)[4][2],
   }
 }
 
-// One source plane.  st: the thread's own quad; hs: its halo quad (first and
-// last row only, halo = +1 lower / -1 upper / 0 none); ap/ac/an: sums of the
-// destination planes p - 1, p, p + 1.
-template <typename C, int MODE, int BXC, int TY>
+// One source plane.  st: the thread's own quad; hsrc: its staged halo quad
+// (first and last row only, halo = +1 lower / -1 upper / 0 none; field f at
+// hsrc + f * fstride bytes), read only where it is folded in; ap/ac/an: sums
+// of the destination planes p - 1, p, p + 1.
+template <typename S, typename C, int MODE, int BXC, int TY>
 __device__ __forceinline__ void fold_update(const typename Pair<C>::P (&st)[4][2],
-                                            const typename Pair<C>::P (&hs)[4][2], int halo,
+                                            const unsigned char* hsrc, uint32_t fstride, int halo,
                                             typename Pair<C>::P (&ap)[2][4], typename Pair<C>::P (&ac)[2][4],
                                             typename Pair<C>::P (&an)[2][4],
                                             const SmemBase<typename Pair<C>::P>& sb, int r, bool live) {
@@ -149,8 +150,14 @@ __device__ __forceinline__ void fold_update(const typename Pair<C>::P (&st)[4][2
         }
       });
     }
-    if (halo == 1) fold_halo<C, MODE, BXC, TY, 1>(hs, ap, ac, an, sb);
-    else if (halo == -1) fold_halo<C, MODE, BXC, TY, -1>(hs, ap, ac, an, sb);
+    if (halo != 0) {
+      P hs[4][2];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        Quad<S>::lds(reinterpret_cast<const S*>(hsrc + f * fstride), hs[f][0], hs[f][1]);
+      if (halo == 1) fold_halo<C, MODE, BXC, TY, 1>(hs, ap, ac, an, sb);
+      else fold_halo<C, MODE, BXC, TY, -1>(hs, ap, ac, an, sb);
+    }
   }
   __syncthreads();
   if (live) {
@@ -290,20 +297,20 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
     }
     cp_async_commit();
   };
-  P st[K][2], hs[K][2];
-  auto take = [&](int i) {     // wait for plane z0 - 1 + i and read it
+  P st[K][2];
+  const unsigned char* hsrc = stage0 + halo_off;  // the halo quad of the plane taken last
+  auto take = [&](int i) {     // wait for plane z0 - 1 + i and read the own quad
     cp_async_wait<kStages - 1>();
     const int p = z0 - 1 + i;
     const bool ok = active && plane_exists(p);
     const unsigned char* base = stage0 + (size_t)(i & (kStages - 1)) * kSlotStride;
+    hsrc = base + halo_off;
 #pragma unroll
     for (int f = 0; f < K; ++f) {
       if (ok) {
         Quad<S>::lds(reinterpret_cast<const S*>(base + f * kFieldStride + own_off), st[f][0], st[f][1]);
-        if (halo != 0)
-          Quad<S>::lds(reinterpret_cast<const S*>(base + f * kFieldStride + halo_off), hs[f][0], hs[f][1]);
       } else {
-        st[f][0] = st[f][1] = hs[f][0] = hs[f][1] = O::splat(C(0));
+        st[f][0] = st[f][1] = O::splat(C(0));
       }
     }
   };
@@ -320,7 +327,11 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
   // into destination plane z0 (= R1 of the first step)
   fetch(kStages - 1);
   take(0);
-  if (plane_exists(z0 - 1)) fold_update<C, kFirst, BXC, TY>(st, hs, halo, R0, R2, R1, sb, r, active);
+  if (plane_exists(z0 - 1)) fold_update<S, C, kFirst, BXC, TY>(st, hsrc, kFieldStride, halo, R0, R2, R1, sb, r, active);
+
+  auto store = [&](int q, P(&acc)[2][K]) {
+    store_plane<kD3Q19, S>(op, mrow, ta, (int64_t)q * ps, x_lo_wall, x_hi_wall, store_skip(q), acc, force);
+  };
 
   // full plane p: contributions to the sums A (dest p - 1), B (dest p), N (dest
   // p + 1); then A is complete
@@ -328,10 +339,8 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
     const int i = p - z0 + 1;
     fetch(i + kStages - 1);
     take(i);
-    fold_update<C, kMid, BXC, TY>(st, hs, halo, A, B, N, sb, r, active);
-    if (p - 1 >= z0)
-      store_plane<kD3Q19, S>(op, mrow, ta, (int64_t)(p - 1) * ps, x_lo_wall, x_hi_wall, store_skip(p - 1), A,
-                             force);
+    fold_update<S, C, kMid, BXC, TY>(st, hsrc, kFieldStride, halo, A, B, N, sb, r, active);
+    if (p - 1 >= z0) store(p - 1, A);
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -342,9 +351,8 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
     const int i = np - 1;
     fetch(i + kStages - 1);
     take(i);
-    if (plane_exists(z1)) fold_update<C, kLast, BXC, TY>(st, hs, halo, B, R0, R0, sb, r, active);
-    store_plane<kD3Q19, S>(op, mrow, ta, (int64_t)(z1 - 1) * ps, x_lo_wall, x_hi_wall, store_skip(z1 - 1), B,
-                           force);
+    if (plane_exists(z1)) fold_update<S, C, kLast, BXC, TY>(st, hsrc, kFieldStride, halo, B, R0, R0, sb, r, active);
+    store(z1 - 1, B);
   };
   // the three plane sums rotate with period 3
   for (int p = z0;; p += 3) {

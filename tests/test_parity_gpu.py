@@ -128,7 +128,7 @@ def test_tiled_matches_reference_kernel(lat, dims, periodic, walls):
 
 
 # The folded D3Q19 kernel (no halo-row threads): FP32, x a multiple of 4 up to
-# 256, ny a multiple of the tile's rows; one-tile y extents wrap onto themselves.
+# 512, ny a multiple of the tile's rows; one-tile y extents wrap onto themselves.
 FOLD_CASES = [
     ((8, 8, 5), 0b111, "none", 0),
     ((12, 8, 9), 0b000, "box", 0),
@@ -142,6 +142,8 @@ FOLD_CASES = [
     ((128, 4, 9), 0b111, "none", 0),
     ((128, 16, 11), 0b000, "box", 8),
     ((64, 24, 13), 0b110, "mixed", 8),
+    ((512, 8, 4), 0b000, "box", 0),
+    ((256, 16, 5), 0b101, "mixed", 8),
 ]
 
 
