@@ -396,6 +396,7 @@ def suite_leg(M, stream):
     out["batch_64_cavities"] = {"mlups": info["fluid_nodes"] * n / (ms * 1e-3) / 1e6,
                                 "fluid_nodes": info["fluid_nodes"], "rows_per_item": rows,
                                 "launches_per_step": info["launches_per_step"],
+                                "steps_per_launch": info["steps_per_launch"],
                                 "work_items": info["items"]}
     b.close()
     for name, case, steps in (

@@ -193,28 +193,39 @@ maclab_status maclab_batch_destroy(maclab_batch b);
  * maclab_batch_step then reports as MACLAB_ERR_INVALID. */
 maclab_status maclab_batch_member(maclab_batch b, int32_t i, maclab_handle *out);
 
-/* Advance every member by n steps. */
+/* Advance every member by n steps.  With two steps per launch
+ * (maclab_batch_set_depth) the last of the n steps is a one-step launch, so
+ * every member's other buffer holds step n - 1 as after single steps. */
 maclab_status maclab_batch_step(maclab_batch b, int64_t n);
 
 /* Rows of a domain per work item (the tuning knob of the single launch);
  * 0 = library default.  Rebuilds the work list. */
 maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows);
 
+/* Time steps per launch of the single launch (temporal blocking): 1 (0 =
+ * the default, 1) or 2.  With 2, each warp carries its row segment through two
+ * updates of Eqs. (4)-(5) in registers, a two-quad and two-row halo wide, and
+ * the intermediate state never goes to memory; results are bit-identical to
+ * single steps.  MACLAB_ERR_UNSUPPORTED unless the batch uses one launch per
+ * step, stores FP32 or FP64 and every nx >= 8.  Rebuilds the work list. */
+maclab_status maclab_batch_set_depth(maclab_batch b, int32_t depth);
+
 /* out[0] members, out[1] total nodes, out[2] fluid nodes, out[3] work items
  * per launch (0 when one launch per member is used), out[4] rows per item,
- * out[5] kernel launches per step. */
-maclab_status maclab_batch_info(maclab_batch b, int64_t out[6]);
+ * out[5] kernel launches per step, out[6] time steps per launch. */
+maclab_status maclab_batch_info(maclab_batch b, int64_t out[7]);
 
 /* ---------------------------------------------------------------- tuning
  * Time the candidate shapes of the tiled and folded kernels (rows per tile,
  * planes per block) on this handle's domain and keep the fastest kernel and
- * shape; the state is saved
- * before and restored after (temporary device buffers are allocated).
+ * shape; the state is saved before and restored after (temporary device
+ * buffers are allocated).
  * Results are cached per (lattice, precision, dims, periodicity, wall mode,
  * device) for the process.  out (may be NULL) receives the chosen ty, tz. */
 maclab_status maclab_tune(maclab_handle h, int32_t out[2]);
 
-/* The same for a batch: chooses the rows per work item. */
+/* The same for a batch: chooses the rows per work item and the time steps per
+ * launch (1 or 2, compared per step); *rows receives the rows. */
 maclab_status maclab_batch_tune(maclab_batch b, int32_t *rows);
 
 /* ---------------------------------------------------------------- adjoint

@@ -672,6 +672,7 @@ struct maclab_batch_ctx {
   void* d_items = nullptr;
   int n_items = 0;
   int rows = 0;                // rows per work item
+  int depth = 1;               // time steps per launch (1 or 2)
   int blocks = 0;
   int cur = 0;
   cudaStream_t stream = nullptr;
@@ -712,14 +713,23 @@ int sm_count() {
   return sms;
 }
 
-// (Re)build the work list for `rows` rows per item.
-maclab_status batch_build_items(maclab_batch_ctx* b, int rows) {
+// Two steps per launch need FP32 or FP64 storage and rows of at least two quads.
+bool batch_depth2_ok(const maclab_batch_ctx* b) {
+  if (!b->one_launch || (b->precision != MACLAB_F32 && b->precision != MACLAB_F64)) return false;
+  for (const maclab_ctx* m : b->members)
+    if (m->g.nx < 8) return false;
+  return true;
+}
+
+// (Re)build the work list for `rows` rows per item and `depth` steps per launch.
+maclab_status batch_build_items(maclab_batch_ctx* b, int rows, int depth) {
   if (!b->one_launch) {
     b->rows = rows;
+    b->depth = 1;
     return MACLAB_OK;
   }
   std::vector<int> items;
-  for (size_t i = 0; i < b->members.size(); ++i) batch_items((int)i, b->members[i]->g, rows, items);
+  for (size_t i = 0; i < b->members.size(); ++i) batch_items((int)i, b->members[i]->g, rows, depth, items);
   void* d = nullptr;
   if (cudaMalloc(&d, items.size() * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -734,22 +744,37 @@ maclab_status batch_build_items(maclab_batch_ctx* b, int rows) {
   b->d_items = d;
   b->n_items = (int)(items.size() / 4);
   b->rows = rows;
-  // resident warps: two 256-thread blocks per SM
-  const int want = (b->n_items + 7) / 8;
-  b->blocks = want < 2 * sm_count() ? (want > 0 ? want : 1) : 2 * sm_count();
+  b->depth = depth;
+  // resident warps: two 256-thread blocks per SM (one step per launch) or
+  // three 128-thread blocks (two steps)
+  const int warps_per_block = depth == 2 ? 4 : 8, per_sm = depth == 2 ? 3 : 2;
+  const int want = (b->n_items + warps_per_block - 1) / warps_per_block;
+  b->blocks = want < per_sm * sm_count() ? (want > 0 ? want : 1) : per_sm * sm_count();
   batch_drop_graphs(b);
   return MACLAB_OK;
 }
 
-cudaError_t batch_launch_one(maclab_batch_ctx* b, int c, cudaStream_t st) {
+// One launch of `steps` time steps (1, or b->depth) from buffer c.
+cudaError_t batch_launch_steps(maclab_batch_ctx* b, int c, int steps, cudaStream_t st) {
+  if (b->one_launch && steps == 2)
+    return launch_batch_step2(b->precision, b->d_insts, b->d_items, b->n_items, c, b->blocks, st);
   if (b->one_launch)
-    return launch_batch_step(b->precision, b->d_insts, b->d_items, b->n_items, c, b->blocks, st);
+    return launch_batch_step(b->precision, b->d_insts, b->d_items, b->n_items, c, b->blocks,
+                             b->depth == 2 ? kBatchSegW2 : kBatchSegW1, st);
   for (maclab_ctx* m : b->members) {
     cudaError_t e = launch_step(step_launch(m, c), st, m->kernel);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
+
+// One launch of b->depth steps.
+cudaError_t batch_launch_one(maclab_batch_ctx* b, int c, cudaStream_t st) {
+  return batch_launch_steps(b, c, b->one_launch ? b->depth : 1, st);
+}
+
+// Launches in one graph: graph_steps / depth, each of depth steps.
+int batch_graph_launches(const maclab_batch_ctx* b) { return b->graph_steps / b->depth; }
 
 maclab_status batch_build_graph(maclab_batch_ctx* b, int c) {
   if (!b->capture_stream &&
@@ -758,7 +783,7 @@ maclab_status batch_build_graph(maclab_batch_ctx* b, int c) {
   cudaGraph_t graph = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeRelaxed), "begin capture");
   cudaError_t err = cudaSuccess;
-  for (int k = 0; k < b->graph_steps && err == cudaSuccess; ++k)
+  for (int k = 0; k < batch_graph_launches(b) && err == cudaSuccess; ++k)
     err = batch_launch_one(b, c ^ (k & 1), b->capture_stream);
   cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &graph);
   if (err != cudaSuccess || e2 != cudaSuccess) {
@@ -829,7 +854,7 @@ maclab_status maclab_batch_create(const maclab_config* cfgs, int32_t count, macl
       return cuda_fail(e, "batch descriptor upload");
     }
   }
-  maclab_status s = batch_build_items(b, 16);
+  maclab_status s = batch_build_items(b, 16, 1);
   if (s != MACLAB_OK) {
     batch_free(b);
     return s;
@@ -859,17 +884,28 @@ maclab_status maclab_batch_step(maclab_batch b, int64_t n) {
   for (maclab_ctx* m : b->members)
     if (m->cur != b->cur) return fail(MACLAB_ERR_INVALID, "a member was stepped outside the batch");
   DeviceGuard dg(b->device);
+  // With two steps per launch the last step is a one-step launch, so that the
+  // other buffer holds step n - 1 as after single steps (the residual reads it).
+  const int k = b->one_launch ? b->depth : 1;
+  const int64_t bulk = k > 1 && n > 0 ? n - 1 : n;
+  const int launches = batch_graph_launches(b);
+  const int64_t gsteps = (int64_t)launches * k;
   int64_t done = 0;
-  while (b->graph_steps > 0 && n - done >= b->graph_steps) {
+  while (gsteps > 0 && bulk - done >= gsteps) {
     if (!b->graph_exec[b->cur]) {
       maclab_status s = batch_build_graph(b, b->cur);
       if (s != MACLAB_OK) return s;
     }
     CUDA_TRY(cudaGraphLaunch(b->graph_exec[b->cur], b->stream), "batch graph launch");
-    done += b->graph_steps;
+    if (launches & 1) b->cur ^= 1;
+    done += gsteps;
+  }
+  for (; bulk - done >= k; done += k) {
+    CUDA_TRY(batch_launch_one(b, b->cur, b->stream), "batch step launch");
+    b->cur ^= 1;
   }
   for (; done < n; ++done) {
-    CUDA_TRY(batch_launch_one(b, b->cur, b->stream), "batch step launch");
+    CUDA_TRY(batch_launch_steps(b, b->cur, 1, b->stream), "batch step launch");
     b->cur ^= 1;
   }
   for (maclab_ctx* m : b->members) {
@@ -884,10 +920,21 @@ maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows) {
   if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
   if (rows < 0 || rows > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad row count");
   DeviceGuard dg(b->device);
-  return batch_build_items(b, rows ? rows : 16);
+  return batch_build_items(b, rows ? rows : 16, b->depth);
 }
 
-maclab_status maclab_batch_info(maclab_batch b, int64_t out[6]) {
+maclab_status maclab_batch_set_depth(maclab_batch b, int32_t depth) {
+  if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
+  if (depth < 0 || depth > 2) return fail(MACLAB_ERR_INVALID, "depth must be 0, 1 or 2");
+  if (depth == 0) depth = 1;
+  if (depth == 2 && !batch_depth2_ok(b))
+    return fail(MACLAB_ERR_UNSUPPORTED,
+                "two steps per launch need one launch per step, FP32 or FP64 storage and nx >= 8");
+  DeviceGuard dg(b->device);
+  return batch_build_items(b, b->rows ? b->rows : 16, depth);
+}
+
+maclab_status maclab_batch_info(maclab_batch b, int64_t out[7]) {
   if (!b || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
   int64_t nodes = 0, fluid = 0;
   for (maclab_ctx* m : b->members) {
@@ -900,6 +947,7 @@ maclab_status maclab_batch_info(maclab_batch b, int64_t out[6]) {
   out[3] = b->one_launch ? b->n_items : 0;
   out[4] = b->rows;
   out[5] = b->one_launch ? 1 : (int64_t)b->members.size();
+  out[6] = b->one_launch ? b->depth : 1;
   return MACLAB_OK;
 }
 
@@ -929,21 +977,26 @@ std::string tune_key(const maclab_ctx* h) {
 
 // Median-free simple timing: events around `k` launches of fn after 2 warm-up calls.
 template <typename Fn>
+// Milliseconds per call of fn: the best of three runs of k calls, after three
+// warm-up calls.
 float time_ms(cudaStream_t st, int k, Fn fn) {
-  fn();
-  fn();
+  for (int i = 0; i < 3; ++i) fn();
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  cudaEventRecord(a, st);
-  for (int i = 0; i < k; ++i) fn();
-  cudaEventRecord(b, st);
-  cudaEventSynchronize(b);
-  float ms = 0;
-  cudaEventElapsedTime(&ms, a, b);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(a, st);
+    for (int i = 0; i < k; ++i) fn();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) best = ms;
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  return ms / k;
+  return best / k;
 }
 
 }  // namespace
@@ -1058,20 +1111,24 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
     }
     cudaMemcpyAsync(saved[i], m->buf[m->cur], state_bytes(m), cudaMemcpyDeviceToDevice, b->stream);
   }
-  const int candidates[] = {4, 8, 16, 32, 64};
+  // rows per work item x time steps per launch, compared per time step
+  const int candidates[] = {2, 4, 8, 16, 32, 64};
   float best = 1e30f;
-  int best_rows = 16;
-  for (int rows : candidates) {
-    if (batch_build_items(b, rows) != MACLAB_OK) continue;
-    const float ms = time_ms(b->stream, 10, [&]() {
-      batch_launch_one(b, b->cur, b->stream);
-      b->cur ^= 1;
-    });
-    if (ms < best) {
-      best = ms;
-      best_rows = rows;
+  int best_rows = 16, best_depth = 1;
+  const int max_depth = batch_depth2_ok(b) ? 2 : 1;
+  for (int depth = 1; depth <= max_depth; ++depth)
+    for (int rows : candidates) {
+      if (batch_build_items(b, rows, depth) != MACLAB_OK) continue;
+      const float ms = time_ms(b->stream, 20, [&]() {
+        batch_launch_one(b, b->cur, b->stream);
+        b->cur ^= 1;
+      }) / depth;
+      if (ms < best) {
+        best = ms;
+        best_rows = rows;
+        best_depth = depth;
+      }
     }
-  }
   cudaError_t e = cudaGetLastError();
   b->cur = 0;
   for (size_t i = 0; i < b->members.size(); ++i) {
@@ -1084,7 +1141,7 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
   cudaStreamSynchronize(b->stream);
   for (void* p : saved) cudaFree(p);
   if (e != cudaSuccess) return cuda_fail(e, "batch tuning launch");
-  maclab_status s = batch_build_items(b, best_rows);
+  maclab_status s = batch_build_items(b, best_rows, best_depth);
   if (rows_out) *rows_out = best_rows;
   return s;
 }

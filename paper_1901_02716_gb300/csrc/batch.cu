@@ -114,10 +114,12 @@ __device__ __forceinline__ void batch_row_update(const typename Pair<C>::P (&st)
   });
 }
 
+// segw: quads per work item's segment (30, or fewer when the work list was cut
+// for two steps per launch)
 template <typename S>
 __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restrict__ insts,
                                                        const BatchItem* __restrict__ items,
-                                                       int n_items, int cur) {
+                                                       int n_items, int cur, int segw) {
   using C = typename Store<S>::C;
   using O = Pair<C>;
   using P = typename O::P;
@@ -134,8 +136,8 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
     const S* in = static_cast<const S*>(I.buf[cur]);
     S* out = const_cast<S*>(static_cast<const S*>(I.buf[cur ^ 1]));
     const int nq = I.nx >> 2;
-    const int n_int = min(30, nq - 30 * item.seg);
-    int t = 30 * item.seg - 1 + lane;              // quad of this lane
+    const int n_int = min(segw, nq - segw * item.seg);
+    int t = segw * item.seg - 1 + lane;            // quad of this lane
     const bool interior = lane >= 1 && lane <= n_int;
     const bool active = lane <= n_int + 1;          // interior or halo
     bool swapped = false;
@@ -246,22 +248,288 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
   }
 }
 
+// ------------------------------------------------------------------ two steps per launch
+//
+// Temporal blocking of depth 2: the warp's work item covers 28 quads of its row
+// segment with two halo quads on each side (lanes 0-1 and 30-31) and marches
+// the rows y0 - 2 .. y1 + 1 of the input.  A first update turns each input row
+// into the intermediate state of rows y0 - 1 .. y1 (kept in registers, never
+// stored); a second update, fed row by row as they complete, gives the state
+// two steps on for rows y0 .. y1 - 1.  Every value of the intermediate state
+// the second update reads is what a single step would have stored (its
+// dependence reaches one quad and one row per step), walls keep their input
+// values and rows beyond a closed y boundary are zero, and both updates sum in
+// the order of batch_step_d2q9: the results are bit-identical to two launches
+// of it.  FP32 and FP64 storage (16-bit storage would round the intermediate
+// state on its way through memory).
+
+constexpr int kSegW2 = kBatchSegW2;  // output quads per warp at depth 2
+
+// Intermediate state of one row from its sums (the arithmetic of the store of
+// batch_step_d2q9), with wall lanes (bits a.x, a.y, b.x, b.y) keeping the
+// row's input state `in`; zero for a row that does not exist.
+template <typename C>
+__device__ __forceinline__ void batch_emit(const typename Pair<C>::P (&acc)[2][3],
+                                           const typename Pair<C>::P (&in)[3][2], uint32_t wall,
+                                           bool exists, const typename Pair<C>::P (&force)[2],
+                                           typename Pair<C>::P (&out)[3][2]) {
+  using O = Pair<C>;
+  using P = typename O::P;
+  if (!exists) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) out[f][0] = out[f][1] = O::splat(C(0));
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const P inv = O::rcp(O::add(O::splat(C(36)), acc[q][0]));
+    out[0][q] = O::mul(acc[q][0], O::splat(C(1.0 / 36.0)));
+    out[1][q] = O::fma(acc[q][1], inv, force[0]);
+    out[2][q] = O::fma(acc[q][2], inv, force[1]);
+  }
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    if (wall & 1u) out[f][0].x = in[f][0].x;
+    if (wall & 2u) out[f][0].y = in[f][0].y;
+    if (wall & 4u) out[f][1].x = in[f][1].x;
+    if (wall & 8u) out[f][1].y = in[f][1].y;
+  }
+}
+
+template <typename P>
+__device__ __forceinline__ void zero_sums(P (&a)[2][3]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a[q][k] = P{0, 0};
+}
+
+// FP32: three blocks per SM; FP64 needs more registers (two blocks)
+template <typename S>
+__global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(const BatchInst* __restrict__ insts,
+                                                           const BatchItem* __restrict__ items,
+                                                           int n_items, int cur) {
+  using C = typename Store<S>::C;
+  using O = Pair<C>;
+  using P = typename O::P;
+  constexpr int K = 3;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+
+  for (int it = warp; it < n_items; it += nwarps) {
+    const BatchItem item = items[it];
+    const BatchInst& I = insts[item.inst];
+    const S* in = static_cast<const S*>(I.buf[cur]);
+    S* out = const_cast<S*>(static_cast<const S*>(I.buf[cur ^ 1]));
+    const int nq = I.nx >> 2;                        // >= 2 (checked by the host)
+    const int n_int = min(kSegW2, nq - kSegW2 * item.seg);
+    int t = kSegW2 * item.seg - 2 + lane;            // quad of this lane
+    const bool interior = lane >= 2 && lane <= n_int + 1;
+    const bool active = lane <= n_int + 3;           // interior or halo
+    bool swapped = false;
+    if (t < 0) { t += nq; swapped = true; }
+    if (t >= nq) { t -= nq; swapped = true; }
+    const int64_t n = I.n;
+    P force[2];
+    if constexpr (sizeof(C) == 8) {
+      force[0] = O::splat(C(I.force64[0]));
+      force[1] = O::splat(C(I.force64[1]));
+    } else {
+      force[0] = O::splat(C(I.force[0]));
+      force[1] = O::splat(C(I.force[1]));
+    }
+    // box walls at x = 0 and x = nx - 1 in lane order (a wrapped quad is lane-swapped)
+    uint32_t xwall = 0;
+    if (I.wall_mode == kWallBox && !I.px) {
+      if (t == 0) xwall |= swapped ? 2u : 1u;
+      if (t == nq - 1) xwall |= swapped ? 4u : 8u;
+    }
+    const bool x_lo_wall = I.wall_mode == kWallBox && !I.px && t == 0 && interior;
+    const bool x_hi_wall = I.wall_mode == kWallBox && !I.px && t == nq - 1 && interior;
+
+    auto row_exists = [&](int y) { return (y >= 0 && y < I.ny) || I.py; };
+    auto row_mem = [&](int y) { return y < 0 ? y + I.ny : (y >= I.ny ? y - I.ny : y); };
+    // a row of the input (zeros where absent) and the wall lanes of this quad in it
+    auto load = [&](int y, P (&st)[K][2], uint32_t& wall) {
+      const bool ok = active && row_exists(y);
+      const int ym = row_mem(y);
+      const int64_t off = (int64_t)ym * I.nx + 4 * t;
+      wall = 0;
+#pragma unroll
+      for (int f = 0; f < K; ++f) {
+        if (ok) {
+          Quad<S>::ld(in + f * n + off, st[f][0], st[f][1]);
+          if (swapped) {
+            st[f][0] = O::swap(st[f][0]);
+            st[f][1] = O::swap(st[f][1]);
+          }
+        } else {
+          st[f][0] = O::splat(C(0));
+          st[f][1] = O::splat(C(0));
+        }
+      }
+      if (ok) {
+        if (I.wall_mode == kWallMask) {
+          const uchar4 m = *reinterpret_cast<const uchar4*>(I.mask + off);
+          wall = swapped ? ((m.y ? 1u : 0u) | (m.x ? 2u : 0u) | (m.w ? 4u : 0u) | (m.z ? 8u : 0u))
+                         : ((m.x ? 1u : 0u) | (m.y ? 2u : 0u) | (m.z ? 4u : 0u) | (m.w ? 8u : 0u));
+        } else if (I.wall_mode == kWallBox) {
+          wall = (!I.py && (ym == 0 || ym == I.ny - 1)) ? 15u : xwall;
+        }
+      }
+    };
+    // final rows: the store of batch_step_d2q9
+    auto store = [&](int y, P (&acc)[2][K]) {
+      if (!interior) return;
+      if (!I.py && (y == 0 || y == I.ny - 1)) return;
+      const int64_t off = (int64_t)y * I.nx + 4 * t;
+      bool wall[4] = {x_lo_wall, false, false, x_hi_wall};
+      bool any = x_lo_wall || x_hi_wall;
+      if (I.wall_mode == kWallMask) {
+        const uchar4 m = *reinterpret_cast<const uchar4*>(I.mask + off);
+        wall[0] = m.x != 0; wall[1] = m.y != 0; wall[2] = m.z != 0; wall[3] = m.w != 0;
+        any = wall[0] || wall[1] || wall[2] || wall[3];
+      }
+      P v[K][2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const P inv = O::rcp(O::add(O::splat(C(36)), acc[q][0]));
+        v[0][q] = O::mul(acc[q][0], O::splat(C(1.0 / 36.0)));
+        v[1][q] = O::fma(acc[q][1], inv, force[0]);
+        v[2][q] = O::fma(acc[q][2], inv, force[1]);
+      }
+      if (!any) {
+#pragma unroll
+        for (int f = 0; f < K; ++f) Quad<S>::st(out + f * n + off, v[f][0], v[f][1]);
+      } else {
+#pragma unroll
+        for (int f = 0; f < K; ++f) {
+          if (!wall[0]) Quad<S>::st1(out + f * n + off + 0, v[f][0].x);
+          if (!wall[1]) Quad<S>::st1(out + f * n + off + 1, v[f][0].y);
+          if (!wall[2]) Quad<S>::st1(out + f * n + off + 2, v[f][1].x);
+          if (!wall[3]) Quad<S>::st1(out + f * n + off + 3, v[f][1].y);
+        }
+      }
+    };
+
+    // sums of the first update for row d in A[(d - y0 + 3) % 3], of the second in B[...]
+    const int y0 = item.y0, y1 = item.y1;
+    P A0[2][K], A1[2][K], A2[2][K], B0[2][K], B1[2][K], B2[2][K];
+    zero_sums(A0); zero_sums(A1); zero_sums(A2);
+    zero_sums(B0); zero_sums(B1); zero_sums(B2);
+    P st[K][2], nxt[K][2], prev[K][2], mid[K][2];
+    uint32_t w_st = 0, w_nxt = 0, w_prev = 0;
+    auto advance = [&](int y_next) {  // st <- the prefetched row, prefetch row y_next
+#pragma unroll
+      for (int f = 0; f < K; ++f) {
+        st[f][0] = nxt[f][0];
+        st[f][1] = nxt[f][1];
+      }
+      w_st = w_nxt;
+      load(y_next, nxt, w_nxt);
+    };
+    auto keep = [&]() {  // prev <- st: the input of the row the next emission completes
+#pragma unroll
+      for (int f = 0; f < K; ++f) {
+        prev[f][0] = st[f][0];
+        prev[f][1] = st[f][1];
+      }
+      w_prev = w_st;
+    };
+
+    // input row y0 - 2: only its sums into row y0 - 1
+    load(y0 - 2, st, w_st);
+    load(y0 - 1, nxt, w_nxt);
+    if (row_exists(y0 - 2)) batch_row_update<C, kFirst>(st, A0, A1, A2);
+    // input row y0 - 1 (row y0 - 2 of the first update is not needed)
+    advance(y0);
+    batch_row_update<C, kMid>(st, A1, A2, A0);
+    zero_sums(A1);
+    keep();
+    // input row y0 completes intermediate row y0 - 1, the second update's first source
+    advance(y0 + 1);
+    batch_row_update<C, kMid>(st, A2, A0, A1);
+    batch_emit<C>(A2, prev, w_prev, row_exists(y0 - 1), force, mid);
+    zero_sums(A2);
+    keep();
+    if (row_exists(y0 - 1)) batch_row_update<C, kFirst>(mid, B1, B2, B0);
+
+    // input row ys: intermediate row ys - 1 complete, fed to the second update,
+    // which completes final row ys - 2.  Ap/Ac/An: first-update sums of rows
+    // ys - 1, ys, ys + 1; Bp/Bc/Bn: second-update sums of rows ys - 2, ys - 1, ys.
+    auto body = [&](int ys, P(&Ap)[2][K], P(&Ac)[2][K], P(&An)[2][K], P(&Bp)[2][K], P(&Bc)[2][K],
+                    P(&Bn)[2][K]) {
+      advance(ys + 1);
+      batch_row_update<C, kMid>(st, Ap, Ac, An);
+      batch_emit<C>(Ap, prev, w_prev, row_exists(ys - 1), force, mid);
+      zero_sums(Ap);
+      keep();
+      batch_row_update<C, kMid>(mid, Bp, Bc, Bn);
+      if (ys - 2 >= y0) store(ys - 2, Bp);
+      zero_sums(Bp);
+    };
+    // input row y1 + 1: completes intermediate row y1 and final row y1 - 1
+    auto last = [&](P(&Ap)[2][K], P(&Ac)[2][K], P(&An)[2][K], P(&Bp)[2][K], P(&Bc)[2][K],
+                    P(&Bn)[2][K]) {
+#pragma unroll
+      for (int f = 0; f < K; ++f) {
+        st[f][0] = nxt[f][0];
+        st[f][1] = nxt[f][1];
+      }
+      if (row_exists(y1 + 1)) batch_row_update<C, kLast>(st, Ap, Ac, An);
+      batch_emit<C>(Ap, prev, w_prev, row_exists(y1), force, mid);
+      if (row_exists(y1)) batch_row_update<C, kLast>(mid, Bp, Bc, Bn);
+      store(y1 - 1, Bp);
+    };
+    // the sums rotate with period 3
+    for (int ys = y0 + 1;;) {
+      if (ys > y1) { last(A0, A1, A2, B2, B0, B1); break; }
+      body(ys++, A0, A1, A2, B2, B0, B1);
+      if (ys > y1) { last(A1, A2, A0, B0, B1, B2); break; }
+      body(ys++, A1, A2, A0, B0, B1, B2);
+      if (ys > y1) { last(A2, A0, A1, B1, B2, B0); break; }
+      body(ys++, A2, A0, A1, B1, B2, B0);
+    }
+  }
+}
+
+template <typename S>
+static cudaError_t launch_batch2_t(const BatchInst* insts, const BatchItem* items, int n_items,
+                                   int cur, int blocks, cudaStream_t st) {
+  batch_step2_d2q9<S><<<blocks, 128, 0, st>>>(insts, items, n_items, cur);
+  return cudaGetLastError();
+}
+
 template <typename S>
 static cudaError_t launch_batch_t(const BatchInst* insts, const BatchItem* items, int n_items,
-                                  int cur, int blocks, cudaStream_t st) {
-  batch_step_d2q9<S><<<blocks, 256, 0, st>>>(insts, items, n_items, cur);
+                                  int cur, int blocks, int segw, cudaStream_t st) {
+  batch_step_d2q9<S><<<blocks, 256, 0, st>>>(insts, items, n_items, cur, segw);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_step(int precision, const void* insts, const void* items, int n_items,
-                              int cur, int blocks, cudaStream_t st) {
+                              int cur, int blocks, int segw, cudaStream_t st) {
+  const BatchInst* I = static_cast<const BatchInst*>(insts);
+  const BatchItem* T = static_cast<const BatchItem*>(items);
+  if (segw < 1 || segw > 30) return cudaErrorInvalidValue;
+  switch (precision) {
+    case MACLAB_F64: return launch_batch_t<double>(I, T, n_items, cur, blocks, segw, st);
+    case MACLAB_F32: return launch_batch_t<float>(I, T, n_items, cur, blocks, segw, st);
+    case MACLAB_BF16_STORE: return launch_batch_t<__nv_bfloat16>(I, T, n_items, cur, blocks, segw, st);
+    case MACLAB_F16_STORE: return launch_batch_t<__half>(I, T, n_items, cur, blocks, segw, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Two steps per launch: FP32 and FP64 storage only.
+cudaError_t launch_batch_step2(int precision, const void* insts, const void* items, int n_items,
+                               int cur, int blocks, cudaStream_t st) {
   const BatchInst* I = static_cast<const BatchInst*>(insts);
   const BatchItem* T = static_cast<const BatchItem*>(items);
   switch (precision) {
-    case MACLAB_F64: return launch_batch_t<double>(I, T, n_items, cur, blocks, st);
-    case MACLAB_F32: return launch_batch_t<float>(I, T, n_items, cur, blocks, st);
-    case MACLAB_BF16_STORE: return launch_batch_t<__nv_bfloat16>(I, T, n_items, cur, blocks, st);
-    case MACLAB_F16_STORE: return launch_batch_t<__half>(I, T, n_items, cur, blocks, st);
+    case MACLAB_F64: return launch_batch2_t<double>(I, T, n_items, cur, blocks, st);
+    case MACLAB_F32: return launch_batch2_t<float>(I, T, n_items, cur, blocks, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -287,10 +555,12 @@ void batch_fill_inst(void* dst, const Geometry& g, void* buf0, void* buf1, const
   b->force64[1] = force[1];
 }
 
-// Work items of one domain with `rows` rows per chunk.
-void batch_items(int inst, const Geometry& g, int rows, std::vector<int>& out4) {
+// Work items of one domain with `rows` rows per chunk; segments of 30 quads
+// (one step per launch) or 28 (two steps per launch).
+void batch_items(int inst, const Geometry& g, int rows, int depth, std::vector<int>& out4) {
   const int nq = g.nx / 4;
-  const int nseg = (nq + 29) / 30;
+  const int segw = depth == 2 ? kBatchSegW2 : kBatchSegW1;
+  const int nseg = (nq + segw - 1) / segw;
   for (int y0 = 0; y0 < g.ny; y0 += rows) {
     const int y1 = y0 + rows < g.ny ? y0 + rows : g.ny;
     for (int s = 0; s < nseg; ++s) {

@@ -160,12 +160,17 @@ cudaError_t launch_adjoint_finish(const Geometry& g, int precision, const void* 
                                   void* gu, int dtype, double* wall, double* dot, cudaStream_t st);
 
 // Defined in batch.cu.
+// segw: quads per segment of the work list (30 when it was cut for one step per launch)
 cudaError_t launch_batch_step(int precision, const void* insts, const void* items, int n_items,
-                              int cur, int blocks, cudaStream_t st);
+                              int cur, int blocks, int segw, cudaStream_t st);
+constexpr int kBatchSegW1 = 30, kBatchSegW2 = 28;
+// two time steps per launch (FP32 / FP64 storage, every nx >= 8), 128-thread blocks
+cudaError_t launch_batch_step2(int precision, const void* insts, const void* items, int n_items,
+                               int cur, int blocks, cudaStream_t st);
 size_t batch_inst_bytes();
 size_t batch_item_bytes();
 void batch_fill_inst(void* dst, const Geometry& g, void* buf0, void* buf1, const double force[3]);
-void batch_items(int inst, const Geometry& g, int rows, std::vector<int>& out4);
+void batch_items(int inst, const Geometry& g, int rows, int depth, std::vector<int>& out4);
 
 // Defined in convert.cu.
 cudaError_t launch_set_physical(const Geometry& g, int precision, const void* rho,

@@ -77,6 +77,7 @@ SIGNATURES = {
     "maclab_batch_member": (_S, [_H, ctypes.c_int32, ctypes.POINTER(_H)]),
     "maclab_batch_step": (_S, [_H, ctypes.c_int64]),
     "maclab_batch_set_rows": (_S, [_H, ctypes.c_int32]),
+    "maclab_batch_set_depth": (_S, [_H, ctypes.c_int32]),
     "maclab_batch_info": (_S, [_H, ctypes.POINTER(ctypes.c_int64)]),
     "maclab_tune": (_S, [_H, ctypes.POINTER(ctypes.c_int32)]),
     "maclab_batch_tune": (_S, [_H, ctypes.POINTER(ctypes.c_int32)]),
@@ -554,16 +555,20 @@ class Batch:
     def set_rows(self, rows):
         _check(lib().maclab_batch_set_rows(self.handle, int(rows)), "maclab_batch_set_rows")
 
+    def set_depth(self, depth):
+        """Time steps per launch of the single launch (1 or 2)."""
+        _check(lib().maclab_batch_set_depth(self.handle, int(depth)), "maclab_batch_set_depth")
+
     def tune(self):
         r = ctypes.c_int32()
         _check(lib().maclab_batch_tune(self.handle, ctypes.byref(r)), "maclab_batch_tune")
         return r.value
 
     def info(self):
-        out = (ctypes.c_int64 * 6)()
+        out = (ctypes.c_int64 * 7)()
         _check(lib().maclab_batch_info(self.handle, out), "maclab_batch_info")
         return {"members": out[0], "nodes": out[1], "fluid_nodes": out[2], "items": out[3],
-                "rows": out[4], "launches_per_step": out[5]}
+                "rows": out[4], "launches_per_step": out[5], "steps_per_launch": out[6]}
 
     def close(self):
         if getattr(self, "handle", None):

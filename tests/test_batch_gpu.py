@@ -91,7 +91,7 @@ def test_batch_tune_keeps_state():
     b.step(3)
     before = [m.get_lattice_state().copy() for m in b.members]
     rows = b.tune()
-    assert rows in (4, 8, 16, 32, 64)
+    assert rows in (2, 4, 8, 16, 32, 64)
     for m, x in zip(b.members, before):
         assert np.array_equal(m.get_lattice_state(), x)
     b.step(4)
@@ -123,3 +123,74 @@ def test_single_domain_tune(lat, dims, periodic, walls):
     assert s2.tune() == (ty, tz) and s2.kernel_info()["kernel"] == kernel
     s.close()
     s2.close()
+
+
+def _depth_cases():
+    """Members that exercise the two-step launch: a 28-quad segment boundary
+    (nx = 136: segments of 28 and 6 quads), the narrowest rows (nx = 8, 12),
+    every wall mode, periodic and closed axes, a force and a cavity."""
+    sides, res, lids = inputs.batch_cavity_sides(3, seed=91)
+    cases = [inputs.cavity2d(n, lid=v) for n, v in zip(sides, lids)]
+    cases += [inputs.random_case(D2, (136, 40), 0b11, seed=92, u_amp=0.05),
+              inputs.random_case(D2, (124, 33), 0b01, seed=93, u_amp=0.05, walls="mixed",
+                                 force=(1e-4, -2e-4)),
+              inputs.random_case(D2, (8, 11), 0b11, seed=94, u_amp=0.05),
+              inputs.random_case(D2, (12, 9), 0b00, seed=95, u_amp=0.05, walls="box"),
+              inputs.random_case(D2, (232, 17), 0b10, seed=96, u_amp=0.05, walls="mixed")]
+    return cases
+
+
+@pytest.mark.parametrize("precision", [M.F32, M.F64])
+@pytest.mark.parametrize("steps,rows", [(1, 16), (2, 4), (7, 16), (37, 8), (64, 64)])
+def test_two_steps_per_launch_bit_identical(precision, steps, rows):
+    """Two updates per launch (temporal blocking) give the same bits as one
+    update per launch: same sums in the same order, walls and closed
+    boundaries reproduced in the intermediate rows."""
+    cases = _depth_cases()
+    ref = M.Batch.from_cases(cases, precision)
+    ref.set_rows(rows)
+    ref.step(steps)
+    b = M.Batch.from_cases(cases, precision)
+    b.set_rows(rows)
+    b.set_depth(2)
+    assert b.info()["steps_per_launch"] == 2
+    b.step(steps)
+    for m, r in zip(b.members, ref.members):
+        assert np.array_equal(m.get_lattice_state(), r.get_lattice_state())
+        assert m.params["steps"] == steps
+    # the other buffer holds step n - 1 as after single steps: same residual
+    for m, r in zip(b.members, ref.members):
+        assert m.diagnostics()["residual"] == r.diagnostics()["residual"]
+    b.close()
+    ref.close()
+
+
+def test_two_steps_per_launch_against_oracle():
+    case = inputs.random_case(D2, (72, 29), 0b01, seed=97, u_amp=0.05, walls="mixed",
+                              force=(2e-4, 1e-4))
+    b = M.Batch.from_cases([case, case], M.F64)
+    b.set_depth(2)
+    b.step(9)
+    r_g, u_g = b.members[0].get_state()
+    r_o, u_o = orc.step(D2, case.rho, case.u, case.periodic, wall=case.wall_mask, force=case.force,
+                        nsteps=9)
+    assert np.abs(u_g - u_o).max() <= 1e-12 * np.abs(u_o).max()
+    assert np.abs(r_g - r_o).max() <= 1e-12 * np.abs(r_o).max()
+    b.close()
+
+
+@pytest.mark.parametrize("kind", ["bf16", "narrow", "3d"])
+def test_two_steps_per_launch_refused(kind):
+    if kind == "bf16":
+        b = M.Batch.from_cases(_cases()[:2], M.BF16_STORE)
+    elif kind == "narrow":
+        b = M.Batch.from_cases([inputs.random_case(D2, (4, 9), 0b11, seed=98),
+                                inputs.random_case(D2, (16, 9), 0b11, seed=99)], M.F32)
+    else:
+        b = M.Batch.from_cases([inputs.random_case(D3, (8, 8, 8), 0b111, seed=100)], M.F32)
+    with pytest.raises(M.MacLABError) as ei:
+        b.set_depth(2)
+    assert ei.value.status == M.ERR_UNSUPPORTED
+    assert b.info()["steps_per_launch"] == 1
+    b.step(3)
+    b.close()
