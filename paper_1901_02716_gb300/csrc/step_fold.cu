@@ -7,11 +7,12 @@ namespace maclab {
 
 namespace {
 
-// Instantiated (BXC, TY) for FP32 storage.
+// Instantiated (BXC, TY) for FP32 storage, in order of preference for each
+// width (the first whose TY divides ny is the default).
 struct FoldShape {
   int bxc, ty;
 };
-constexpr FoldShape kFoldShapes[] = {{16, 8}, {32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}};
+constexpr FoldShape kFoldShapes[] = {{16, 8}, {32, 8}, {32, 4}, {64, 4}, {64, 8}, {128, 4}};
 
 bool fold_shape(const Geometry& g, int precision, int ty_req, FoldShape* out) {
   if (g.d != 3 || g.lattice != kD3Q19 || !g.ilv || precision != MACLAB_F32) return false;

@@ -30,8 +30,14 @@ struct FoldLayout {
   static constexpr int NXS = NXO + 2;            // + the halo row's (+x, -x) slots
   static constexpr int NYS = F::count_y();
   static constexpr int RS = TY + 2;              // staged rows: lower halo, TY own, upper halo
-  static constexpr size_t xe_pairs = (size_t)NXS * TY * W;
-  static constexpr size_t ye_pairs = (size_t)NYS * TY * 2 * W;
+  // Rows that fit in a warp (BXC <= 32) exchange x-crossing equilibria by
+  // shuffles and double-buffer the y exchange (one barrier per plane); wider
+  // rows use the shared x exchange and one y buffer (two barriers).
+  static constexpr bool XSH = BXC <= 32;
+  static constexpr int YROW = 2 * BXC + 1;       // XSH y row: pairs a, pairs b, one seam copy
+  static constexpr size_t ye_buf_pairs = (size_t)NYS * (TY - 1) * YROW;
+  static constexpr size_t xe_pairs = XSH ? 0 : (size_t)NXS * TY * W;
+  static constexpr size_t ye_pairs = XSH ? 2 * ye_buf_pairs : (size_t)NYS * TY * 2 * W;
   static constexpr size_t exch_bytes = ((sizeof(P) * (xe_pairs + ye_pairs) + 15) / 16) * 16;
   static constexpr size_t stage_bytes = (size_t)kStages * 4 * RS * BXC * Quad<S>::BYTES;
   static constexpr size_t smem = exch_bytes + stage_bytes;
@@ -204,6 +210,179 @@ __device__ __forceinline__ void fold_update(const typename Pair<C>::P (&st)[4][2
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ rows within a warp
+// Per-thread constants of the shuffle x exchange and the compact y exchange.
+template <typename P>
+struct FoldXs {
+  P* ye;               // y exchange buffer of the current plane
+  int tx;
+  int li, ri;          // y-row column of the left neighbour's pair b / right one's pair a (or the seam copy)
+  int src_l, src_r;    // lanes (within the row's segment) of the left / right neighbour
+  bool swap_l, swap_r; // receiving across the seam: thread 0 from the left, the last thread from the right
+  bool wl, wr;         // writing the seam copy: the last thread (+x), thread 0 (-x)
+};
+
+template <int WIDTH, typename P>
+__device__ __forceinline__ P fold_shfl(P v, int src) {
+  P r;
+  r.x = __shfl_sync(0xffffffffu, v.x, src, WIDTH);
+  r.y = __shfl_sync(0xffffffffu, v.y, src, WIDTH);
+  return r;
+}
+
+// index of an x-crossing direction among those with the same c_x (c_y = 0)
+__host__ __device__ constexpr int fold_xidx(int a) {
+  using F = Frame<kD3Q19>;
+  int k = 0;
+  for (int b = 0; b < a; ++b) k += (F::fy(b) == 0 && F::fx(b) == F::fx(a)) ? 1 : 0;
+  return k;
+}
+
+// Halo row (FY = +1 lower, -1 upper) with the shuffle exchange: in-thread
+// moves go into the sums, the pair crossing to a neighbour into hb (+x) / ha (-x).
+template <typename C, int MODE, int FY>
+__device__ __forceinline__ void fold_halo_xs(const typename Pair<C>::P (&hs)[4][2],
+                                             typename Pair<C>::P (&ap)[2][4], typename Pair<C>::P (&ac)[2][4],
+                                             typename Pair<C>::P (&an)[2][4], typename Pair<C>::P& hb,
+                                             typename Pair<C>::P& ha) {
+  using L = Lattice<kD3Q19>;
+  using F = Frame<kD3Q19>;
+  using P = typename Pair<C>::P;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    Terms<3, C> t;
+    const P u[3] = {hs[1][q], hs[2][q], hs[3][q]};
+    make_terms<3, C>(hs[0][q], u, t);
+    static_for<0, L::Q>([&](auto I) {
+      constexpr int a = decltype(I)::value;
+      if constexpr (mode_allows<kD3Q19, MODE>(a) && F::fy(a) == FY) {
+        constexpr int fx = F::fx(a), fz = F::fz(a);
+        const P T = term<kD3Q19, C, a>(t);
+        const int qd = q + fx;
+        if (qd >= 0 && qd < 2) accum<kD3Q19, C, a>(pick<fz>(ap, ac, an)[qd], T);
+        else if constexpr (fx == 1) hb = T;
+        else if constexpr (fx == -1) ha = T;
+      }
+    });
+  }
+}
+
+// One source plane, rows within a warp.  Every lane runs the first phase and
+// the shuffles (lanes past the row end hold zeros and are never read); the y
+// exchange goes through this plane's buffer, and the one barrier suffices
+// because consecutive planes use different buffers.
+template <typename S, typename C, int MODE, int BXC, int TY>
+__device__ __forceinline__ void fold_update_xs(const typename Pair<C>::P (&st)[4][2],
+                                               const unsigned char* hsrc, uint32_t fstride, int halo,
+                                               typename Pair<C>::P (&ap)[2][4], typename Pair<C>::P (&ac)[2][4],
+                                               typename Pair<C>::P (&an)[2][4], const FoldXs<typename Pair<C>::P>& xs,
+                                               int r, bool live) {
+  using L = Lattice<kD3Q19>;
+  using F = Frame<kD3Q19>;
+  using O = Pair<C>;
+  using P = typename O::P;
+  constexpr int YROW = 2 * BXC + 1;
+  constexpr int SEAM = 2 * BXC;
+  P xb[3], xa[3];  // x-crossing equilibria leaving pair b (+x) and pair a (-x)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) xb[k] = xa[k] = O::splat(C(0));
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    Terms<3, C> t;
+    const P u[3] = {st[1][q], st[2][q], st[3][q]};
+    make_terms<3, C>(st[0][q], u, t);
+    static_for<0, L::Q>([&](auto I) {
+      constexpr int a = decltype(I)::value;
+      if constexpr (mode_allows<kD3Q19, MODE>(a)) {
+        constexpr int fx = F::fx(a);
+        if constexpr (F::ycross(a)) {
+          // rows of the tile only: what leaves it is formed by the next tile's halo
+          constexpr int fy = F::fy(a);
+          if (fy == 1 ? r < TY - 1 : r > 0) {
+            const P T = term<kD3Q19, C, a>(t);
+            P* row = xs.ye + (F::yslot(a) * (TY - 1) + (fy == 1 ? r : r - 1)) * YROW;
+            row[q * BXC + xs.tx] = T;
+            if constexpr (fx == 1) {
+              if (q == 1 && xs.wl) row[SEAM] = O::swap(T);
+            } else if constexpr (fx == -1) {
+              if (q == 0 && xs.wr) row[SEAM] = O::swap(T);
+            }
+          }
+        } else {
+          constexpr int fz = F::fz(a);
+          const P T = term<kD3Q19, C, a>(t);
+          const int qd = q + fx;
+          if (qd >= 0 && qd < 2) accum<kD3Q19, C, a>(pick<fz>(ap, ac, an)[qd], T);
+          else if constexpr (fx == 1) xb[fold_xidx(a)] = T;
+          else if constexpr (fx == -1) xa[fold_xidx(a)] = T;
+        }
+      }
+    });
+  }
+  P hb = O::splat(C(0)), ha = O::splat(C(0));
+  if (live && halo != 0) {
+    P hs[4][2];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) Quad<S>::lds(reinterpret_cast<const S*>(hsrc + f * fstride), hs[f][0], hs[f][1]);
+    if (halo == 1) fold_halo_xs<C, MODE, 1>(hs, ap, ac, an, hb, ha);
+    else fold_halo_xs<C, MODE, -1>(hs, ap, ac, an, hb, ha);
+  }
+  // x exchange: +x from the left neighbour's pair b into pair a, -x from the
+  // right neighbour's pair a into pair b (lane-swapped across the seam)
+  static_for<0, L::Q>([&](auto I) {
+    constexpr int a = decltype(I)::value;
+    if constexpr (mode_allows<kD3Q19, MODE>(a) && F::fy(a) == 0 && F::fx(a) != 0) {
+      constexpr int fx = F::fx(a), fz = F::fz(a);
+      if constexpr (fx == 1) {
+        P v = fold_shfl<BXC>(xb[fold_xidx(a)], xs.src_l);
+        if (xs.swap_l) v = O::swap(v);
+        accum<kD3Q19, C, a>(pick<fz>(ap, ac, an)[0], v);
+      } else {
+        P v = fold_shfl<BXC>(xa[fold_xidx(a)], xs.src_r);
+        if (xs.swap_r) v = O::swap(v);
+        accum<kD3Q19, C, a>(pick<fz>(ap, ac, an)[1], v);
+      }
+    }
+  });
+  if constexpr (MODE == kMid) {  // the halo row's crossing pairs (c_z = 0 only)
+    P v = fold_shfl<BXC>(hb, xs.src_l);
+    P w = fold_shfl<BXC>(ha, xs.src_r);
+    if (xs.swap_l) v = O::swap(v);
+    if (xs.swap_r) w = O::swap(w);
+    if (halo == 1) {
+      accum<kD3Q19, C, fold_dir<1, 1>()>(ac[0], v);
+      accum<kD3Q19, C, fold_dir<-1, 1>()>(ac[1], w);
+    } else if (halo == -1) {
+      accum<kD3Q19, C, fold_dir<1, -1>()>(ac[0], v);
+      accum<kD3Q19, C, fold_dir<-1, -1>()>(ac[1], w);
+    }
+  }
+  __syncthreads();
+  if (live) {
+    static_for<0, L::Q>([&](auto I) {
+      constexpr int a = decltype(I)::value;
+      if constexpr (mode_allows<kD3Q19, MODE>(a) && F::ycross(a)) {
+        constexpr int fz = F::fz(a), fx = F::fx(a), fy = F::fy(a);
+        auto& dst = pick<fz>(ap, ac, an);
+        // source row r - fy: a row of the tile (the halo rows were folded in already)
+        if (fy == 1 ? r > 0 : r < TY - 1) {
+          const P* row = xs.ye + (F::yslot(a) * (TY - 1) + (fy == 1 ? r - 1 : r)) * YROW;
+          if constexpr (fx == 0) {
+            accum<kD3Q19, C, a>(dst[0], row[xs.tx]);
+            accum<kD3Q19, C, a>(dst[1], row[BXC + xs.tx]);
+          } else if constexpr (fx == 1) {
+            accum<kD3Q19, C, a>(dst[0], row[xs.li]);          // left neighbour's pair b
+            accum<kD3Q19, C, a>(dst[1], row[xs.tx]);          // own pair a
+          } else {
+            accum<kD3Q19, C, a>(dst[0], row[BXC + xs.tx]);    // own pair b
+            accum<kD3Q19, C, a>(dst[1], row[xs.ri]);          // right neighbour's pair a
+          }
+        }
+      }
+    });
+  }
+}
+
 template <typename S, int BXC, int TY>
 __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
     step_fold(TiledArgs ta, const S* __restrict__ in, S* __restrict__ out) {
@@ -235,6 +414,18 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
   sb.y_r = Ye + r * 2 * W + col_r;
   sb.y_sl = Ye + r * 2 * W + Cols<BXC>::SEAM_L;
   sb.y_sr = Ye + r * 2 * W + Cols<BXC>::SEAM_R;
+  FoldXs<P> xs;  // rows within a warp: shuffle x exchange, alternating y buffers
+  xs.ye = Ye;
+  xs.tx = tx;
+  xs.li = tx == 0 ? 2 * BXC : BXC + tx - 1;
+  xs.ri = tx == bxr - 1 ? 2 * BXC : tx + 1;
+  xs.src_l = tx == 0 ? bxr - 1 : tx - 1;
+  xs.src_r = tx == bxr - 1 ? 0 : tx + 1;
+  xs.swap_l = tx == 0;
+  xs.swap_r = tx == bxr - 1;
+  xs.wl = tx == bxr - 1;
+  xs.wr = tx == 0;
+  int ybuf = 0;
 
   // own row (every row of the tile exists: ny % TY == 0) and the halo row of
   // the first (+1: row - 1) and last (-1: row + 1) rows
@@ -315,6 +506,18 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
     }
   };
 
+  // one source plane into the sums of destination planes p - 1, p, p + 1
+  auto update = [&](auto mode, P(&ap)[2][K], P(&ac)[2][K], P(&an)[2][K]) {
+    constexpr int MODE = decltype(mode)::value;
+    if constexpr (Lay::XSH) {
+      xs.ye = Ye + ybuf * Lay::ye_buf_pairs;
+      ybuf ^= 1;
+      fold_update_xs<S, C, MODE, BXC, TY>(st, hsrc, kFieldStride, halo, ap, ac, an, xs, r, active);
+    } else {
+      fold_update<S, C, MODE, BXC, TY>(st, hsrc, kFieldStride, halo, ap, ac, an, sb, r, active);
+    }
+  };
+
   P R0[2][K], R1[2][K], R2[2][K];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
@@ -327,7 +530,7 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
   // into destination plane z0 (= R1 of the first step)
   fetch(kStages - 1);
   take(0);
-  if (plane_exists(z0 - 1)) fold_update<S, C, kFirst, BXC, TY>(st, hsrc, kFieldStride, halo, R0, R2, R1, sb, r, active);
+  if (plane_exists(z0 - 1)) update(std::integral_constant<int, kFirst>{}, R0, R2, R1);
 
   auto store = [&](int q, P(&acc)[2][K]) {
     store_plane<kD3Q19, S>(op, mrow, ta, (int64_t)q * ps, x_lo_wall, x_hi_wall, store_skip(q), acc, force);
@@ -339,7 +542,7 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
     const int i = p - z0 + 1;
     fetch(i + kStages - 1);
     take(i);
-    fold_update<S, C, kMid, BXC, TY>(st, hsrc, kFieldStride, halo, A, B, N, sb, r, active);
+    update(std::integral_constant<int, kMid>{}, A, B, N);
     if (p - 1 >= z0) store(p - 1, A);
 #pragma unroll
     for (int q = 0; q < 2; ++q)
@@ -351,7 +554,7 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
     const int i = np - 1;
     fetch(i + kStages - 1);
     take(i);
-    if (plane_exists(z1)) fold_update<S, C, kLast, BXC, TY>(st, hsrc, kFieldStride, halo, B, R0, R0, sb, r, active);
+    if (plane_exists(z1)) update(std::integral_constant<int, kLast>{}, B, R0, R0);
     store(z1 - 1, B);
   };
   // the three plane sums rotate with period 3
