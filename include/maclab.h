@@ -133,12 +133,17 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * GPU-side yardstick; MACLAB_KERNEL_TILED is the staged, vectorised kernel;
  * MACLAB_KERNEL_FOLDED is its D3Q19 FP32 form without halo-row threads (the
  * tile's edge rows fold their halo rows in; needs ny divisible by the tile's
- * rows).  All compute Eqs. (4)-(5) with the same terms per node (the folded
- * kernel sums them in another order). */
+ * rows); MACLAB_KERNEL_SEGMENT is the batched D2Q9 kernel run on one domain
+ * (a warp per 30-quad row segment, x exchange by warp shuffles, no shared
+ * memory; nx % 4 == 0; the tile's tz is its rows per work item, default 4),
+ * the default for D2Q9 grids of at least 65,536 quads.  All compute Eqs.
+ * (4)-(5) with the same terms per node (the folded kernel sums them in
+ * another order; the segment and tiled kernels give identical bits). */
 #define MACLAB_KERNEL_AUTO 0
 #define MACLAB_KERNEL_REFERENCE 1
 #define MACLAB_KERNEL_TILED 2
 #define MACLAB_KERNEL_FOLDED 3
+#define MACLAB_KERNEL_SEGMENT 4
 
 /* Choose the step kernel.  MACLAB_ERR_UNSUPPORTED if the tiled kernel cannot
  * serve this domain (then the handle keeps its previous choice). */
@@ -150,7 +155,7 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel);
  * (the previous shape is kept). */
 maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz);
 
-/* Describe the kernel in use: out[0] = kernel id (REFERENCE, TILED or FOLDED),
+/* Describe the kernel in use: out[0] = kernel id (REFERENCE, TILED, FOLDED or SEGMENT),
  * out[1] = time steps advanced per launch, out[2] = kernel launches per
  * launch group, out[3] = threads per block (out[3] = 0 and out[1..2] = 1 for
  * the reference kernel's grid-stride launch of 256-thread blocks).  *name (may be NULL) receives a

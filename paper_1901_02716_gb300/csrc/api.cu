@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <iterator>
 #include <string>
 
 #include "common.cuh"
@@ -72,6 +73,8 @@ void free_ctx(maclab_ctx* h) {
   cudaFree(h->d_diag);
   cudaFree(h->d_adj_scratch);
   cudaFree(h->d_adj_red);
+  cudaFree(h->d_seg_inst);
+  cudaFree(h->d_seg_items);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->d_node_type);
@@ -419,7 +422,61 @@ static StepLaunch step_launch(const maclab_ctx* h, int from) {
   s.tz = h->tz;
   s.in = h->buf[from];
   s.out = h->buf[from ^ 1];
+  s.seg_inst = h->d_seg_inst;
+  s.seg_items = h->d_seg_items;
+  s.seg_n_items = h->seg_n_items;
+  s.seg_blocks = h->seg_blocks;
+  s.cur = from;
   return s;
+}
+
+static int device_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+  }
+  return sms;
+}
+
+// The segment kernel's descriptor of this domain and its work list for the
+// current rows per item (tz, default 4), built on first use and after a change
+// of tz; graphs captured with the old list are dropped.  Synchronises the
+// handle's stream when it uploads.
+static maclab_status segment_prepare(maclab_ctx* h) {
+  if (h->kernel != MACLAB_KERNEL_SEGMENT) return MACLAB_OK;
+  const int rows = h->tz > 0 ? h->tz : 4;
+  if (h->d_seg_inst && h->d_seg_items && h->seg_rows == rows) return MACLAB_OK;
+  if (!h->d_seg_inst) {
+    if (cudaMalloc(&h->d_seg_inst, batch_inst_bytes()) != cudaSuccess) {
+      cudaGetLastError();
+      h->d_seg_inst = nullptr;
+      return fail(MACLAB_ERR_OOM, "segment descriptor allocation failed");
+    }
+  }
+  std::vector<unsigned char> inst(batch_inst_bytes());
+  batch_fill_inst(inst.data(), h->g, h->buf[0], h->buf[1], h->force_lat);
+  std::vector<int> items;
+  batch_items(0, h->g, rows, 1, items);
+  void* d = nullptr;
+  if (cudaMalloc(&d, items.size() * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MACLAB_ERR_OOM, "segment work list allocation failed");
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->d_seg_inst, inst.data(), inst.size(), cudaMemcpyHostToDevice, h->stream),
+           "segment descriptor upload");
+  CUDA_TRY(cudaMemcpyAsync(d, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream),
+           "segment work list upload");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "segment upload sync");
+  cudaFree(h->d_seg_items);
+  h->d_seg_items = d;
+  h->seg_n_items = (int)(items.size() / 4);
+  h->seg_rows = rows;
+  const int want = (h->seg_n_items + 7) / 8;  // 256-thread blocks, two per SM
+  h->seg_blocks = want < 2 * device_sms() ? (want > 0 ? want : 1) : 2 * device_sms();
+  drop_graphs(h);
+  return MACLAB_OK;
 }
 
 // Capture graph_steps launches starting from buffer c (graph_steps is even, so
@@ -452,6 +509,8 @@ maclab_status maclab_step(maclab_handle h, int64_t n) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (n < 0) return fail(MACLAB_ERR_INVALID, "n must be >= 0");
   DeviceGuard dg(h->device);
+  maclab_status ps = segment_prepare(h);
+  if (ps != MACLAB_OK) return ps;
   while (h->graph_steps > 0 && n >= h->graph_steps) {
     if (!h->graph_exec[h->cur]) {
       maclab_status s = build_graph(h, h->cur);
@@ -619,7 +678,8 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
     h->kernel = pick_step_kernel(h->g, h->precision);
     return MACLAB_OK;
   }
-  if (kernel != MACLAB_KERNEL_REFERENCE && kernel != MACLAB_KERNEL_TILED && kernel != MACLAB_KERNEL_FOLDED)
+  if (kernel != MACLAB_KERNEL_REFERENCE && kernel != MACLAB_KERNEL_TILED && kernel != MACLAB_KERNEL_FOLDED &&
+      kernel != MACLAB_KERNEL_SEGMENT)
     return fail(MACLAB_ERR_INVALID, "unknown kernel id");
   if (!step_kernel_supported(h->g, h->precision, kernel))
     return fail(MACLAB_ERR_UNSUPPORTED, "kernel does not support this domain");
@@ -633,8 +693,9 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
 maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (ty < 0 || tz < 0 || tz > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad tile shape");
-  const bool ok = h->kernel == MACLAB_KERNEL_FOLDED ? fold_supported(h->g, h->precision, ty)
-                                                    : tiled_supported(h->g, h->precision, ty, tz);
+  const bool ok = h->kernel == MACLAB_KERNEL_FOLDED    ? fold_supported(h->g, h->precision, ty)
+                  : h->kernel == MACLAB_KERNEL_SEGMENT ? ty == 0  // tz: rows per work item
+                                                       : tiled_supported(h->g, h->precision, ty, tz);
   if (!ok) return fail(MACLAB_ERR_UNSUPPORTED, "no built tiled instance has this shape");
   drop_graphs(h);
   h->ty = ty;
@@ -964,6 +1025,8 @@ struct TuneChoice {
 std::map<std::string, TuneChoice> g_tune_cache;
 
 bool shape_supported(const maclab_ctx* h, int kernel, int ty, int tz) {
+  if (kernel == MACLAB_KERNEL_SEGMENT)
+    return ty == 0 && step_kernel_supported(h->g, h->precision, MACLAB_KERNEL_SEGMENT);
   return kernel == MACLAB_KERNEL_FOLDED ? fold_supported(h->g, h->precision, ty)
                                         : tiled_supported(h->g, h->precision, ty, tz);
 }
@@ -1042,18 +1105,43 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
   int bkernel = MACLAB_KERNEL_TILED, bty = 0, btz = 0;
   drop_graphs(h);
   const int n_ty = h->g.d == 3 ? 3 : 1;
-  for (int kernel : {MACLAB_KERNEL_TILED, MACLAB_KERNEL_FOLDED})
+  // each candidate timed on a captured graph of 8 steps (stepping runs in
+  // graphs, where the launch gaps that separate launches would add are absent)
+  if (!h->capture_stream && cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(saved);
+    return cuda_fail(cudaGetLastError(), "capture stream");
+  }
+  auto graph_ms = [&](int launches) -> float {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < launches && err == cudaSuccess; ++k)
+      err = launch_step(step_launch(h, h->cur ^ (k & 1)), h->capture_stream, h->kernel);
+    cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (err != cudaSuccess || e2 != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return 1e30f;
+    }
+    cudaGraphDestroy(graph);
+    const float ms = time_ms(h->stream, 1, [&]() { cudaGraphLaunch(exec, h->stream); });
+    cudaGraphExecDestroy(exec);
+    return ms;
+  };
+  const int seg_rows[] = {2, 4, 8};  // the segment kernel's tz: rows per work item
+  for (int kernel : {MACLAB_KERNEL_TILED, MACLAB_KERNEL_FOLDED, MACLAB_KERNEL_SEGMENT})
     for (int a = 0; a < n_ty; ++a)
-      for (int tz : tzs) {
+      for (int tz : (kernel == MACLAB_KERNEL_SEGMENT ? std::vector<int>(std::begin(seg_rows), std::end(seg_rows))
+                                                     : std::vector<int>(std::begin(tzs), std::end(tzs)))) {
         const int ty = h->g.d == 3 ? tys3[a] : 0;
         if (!shape_supported(h, kernel, ty, tz)) continue;
         h->kernel = kernel;
         h->ty = ty;
         h->tz = tz;
-        const float ms = time_ms(h->stream, 10, [&]() {
-          launch_step(step_launch(h, h->cur), h->stream, h->kernel);
-          h->cur ^= 1;
-        });
+        if (segment_prepare(h) != MACLAB_OK) continue;
+        const float ms = graph_ms(8) / 8;
         if (ms < best) {
           best = ms;
           bkernel = kernel;
@@ -1111,7 +1199,31 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
     }
     cudaMemcpyAsync(saved[i], m->buf[m->cur], state_bytes(m), cudaMemcpyDeviceToDevice, b->stream);
   }
-  // rows per work item x time steps per launch, compared per time step
+  // rows per work item x time steps per launch, compared per time step on a
+  // captured graph of 8 launches (stepping runs in graphs, where the launch
+  // gaps that separate launches would add are absent)
+  if (!b->capture_stream &&
+      cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "capture stream");
+  auto graph_ms = [&](int launches) -> float {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < launches && err == cudaSuccess; ++k)
+      err = batch_launch_one(b, b->cur ^ (k & 1), b->capture_stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &graph);
+    if (err != cudaSuccess || e2 != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return 1e30f;
+    }
+    cudaGraphDestroy(graph);
+    const float ms = time_ms(b->stream, 1, [&]() { cudaGraphLaunch(exec, b->stream); });
+    cudaGraphExecDestroy(exec);
+    return ms;
+  };
   const int candidates[] = {2, 4, 8, 16, 32, 64};
   float best = 1e30f;
   int best_rows = 16, best_depth = 1;
@@ -1119,10 +1231,7 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
   for (int depth = 1; depth <= max_depth; ++depth)
     for (int rows : candidates) {
       if (batch_build_items(b, rows, depth) != MACLAB_OK) continue;
-      const float ms = time_ms(b->stream, 20, [&]() {
-        batch_launch_one(b, b->cur, b->stream);
-        b->cur ^= 1;
-      }) / depth;
+      const float ms = graph_ms(8) / (8 * depth);
       if (ms < best) {
         best = ms;
         best_rows = rows;

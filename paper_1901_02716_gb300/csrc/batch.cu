@@ -218,33 +218,43 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
     load(y0, nxt);
     if (row_exists(y0 - 1))
       batch_row_update<C, kFirst>(st, R0, R2, R1);
-    for (int y = y0; y < y1; ++y) {
+    // source row y: sums A, B, N of destination rows y - 1, y, y + 1; then row
+    // y - 1 is complete
+    auto row = [&](int y, P(&A)[2][K], P(&B)[2][K], P(&N)[2][K]) {
 #pragma unroll
       for (int f = 0; f < K; ++f) {
         st[f][0] = nxt[f][0];
         st[f][1] = nxt[f][1];
       }
       load(y + 1, nxt);
-      batch_row_update<C, kMid>(st, R0, R1, R2);
-      if (y - 1 >= y0) store(y - 1, R0);
+      batch_row_update<C, kMid>(st, A, B, N);
+      if (y - 1 >= y0) store(y - 1, A);
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          R0[q][k] = R1[q][k];
-          R1[q][k] = R2[q][k];
-          R2[q][k] = O::splat(C(0));
-        }
-    }
-    if (row_exists(y1)) {
+        for (int k = 0; k < K; ++k) A[q][k] = O::splat(C(0));
+    };
+    // source row y1 (beyond the chunk): its contributions to row y1 - 1 (= B)
+    auto last = [&](P(&B)[2][K]) {
+      if (row_exists(y1)) {
 #pragma unroll
-      for (int f = 0; f < K; ++f) {
-        st[f][0] = nxt[f][0];
-        st[f][1] = nxt[f][1];
+        for (int f = 0; f < K; ++f) {
+          st[f][0] = nxt[f][0];
+          st[f][1] = nxt[f][1];
+        }
+        batch_row_update<C, kLast>(st, B, R0, R0);
       }
-      batch_row_update<C, kLast>(st, R0, R1, R2);
+      store(y1 - 1, B);
+    };
+    // the three row sums rotate with period 3
+    for (int y = y0;;) {
+      if (y >= y1) { last(R0); break; }
+      row(y++, R0, R1, R2);
+      if (y >= y1) { last(R1); break; }
+      row(y++, R1, R2, R0);
+      if (y >= y1) { last(R2); break; }
+      row(y++, R2, R0, R1);
     }
-    store(y1 - 1, R0);
   }
 }
 

@@ -103,11 +103,16 @@ struct StepLaunch {
   void* out;
   double force[3];  // lattice-unit increment added after the division of Eq. (5)
   int ty = 0, tz = 0;  // tile shape of the tiled kernel (0 = default)
+  // segment kernel: the domain's batch descriptor and work list on the device,
+  // and the buffer the step reads (in = buf[cur] of the descriptor)
+  const void* seg_inst = nullptr;
+  const void* seg_items = nullptr;
+  int seg_n_items = 0, seg_blocks = 0, cur = 0;
 };
 
 // Defined in step.cu.  Kernel ids follow MACLAB_KERNEL_* of maclab.h.
 struct KernelInfo {
-  int id;                // MACLAB_KERNEL_REFERENCE / _TILED / _FOLDED
+  int id;                // MACLAB_KERNEL_REFERENCE / _TILED / _FOLDED / _SEGMENT
   int steps_per_launch;  // time steps one launch group advances
   int launches;          // kernel launches in one group
   int threads;           // threads per block
@@ -218,6 +223,10 @@ struct maclab_ctx {
   int graph_steps = 32;
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
+  // segment kernel (a batch of this one domain): descriptor, work list
+  void* d_seg_inst = nullptr;
+  void* d_seg_items = nullptr;
+  int seg_n_items = 0, seg_blocks = 0, seg_rows = 0;
   void* d_adj_scratch = nullptr;   // reference adjoint: (L_r, L_m) at every node
   double* d_adj_red = nullptr;     // adjoint: reductions (1 + 4 * n_wall_ids doubles)
 };

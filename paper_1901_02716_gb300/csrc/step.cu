@@ -122,19 +122,29 @@ bool step_kernel_supported(const Geometry& g, int precision, int kernel) {
   if (kernel == MACLAB_KERNEL_REFERENCE) return true;
   if (kernel == MACLAB_KERNEL_TILED) return tiled_supported(g, precision, 0, 0);
   if (kernel == MACLAB_KERNEL_FOLDED) return fold_supported(g, precision, 0);
+  if (kernel == MACLAB_KERNEL_SEGMENT) return g.lattice == kD2Q9 && g.ilv == 1;
   return false;
 }
 
 // The folded kernel where it is built (D3Q19 FP32, ny a multiple of its tile
-// rows), else the tiled one, else the reference kernel.
+// rows); for D2Q9 grids of at least 65,536 quads the segment kernel (faster
+// there; on smaller grids its row chunks leave too few warps); else the tiled
+// one, else the reference kernel.
 int pick_step_kernel(const Geometry& g, int precision) {
   if (step_kernel_supported(g, precision, MACLAB_KERNEL_FOLDED)) return MACLAB_KERNEL_FOLDED;
+  if (step_kernel_supported(g, precision, MACLAB_KERNEL_SEGMENT) && (int64_t)(g.nx / 4) * g.ny >= 65536)
+    return MACLAB_KERNEL_SEGMENT;
   return step_kernel_supported(g, precision, MACLAB_KERNEL_TILED) ? MACLAB_KERNEL_TILED
                                                                  : MACLAB_KERNEL_REFERENCE;
 }
 
 static const char* kernel_name(const Geometry& g, int precision, int kernel) {
   if (kernel == MACLAB_KERNEL_FOLDED) return "step_fold<D3Q19,f32>";
+  if (kernel == MACLAB_KERNEL_SEGMENT) {
+    static const char* seg[4] = {"segment<D2Q9,f64>", "segment<D2Q9,f32>", "segment<D2Q9,bf16>",
+                                 "segment<D2Q9,f16>"};
+    return seg[precision & 3];
+  }
   static const char* names[2][2][4] = {
       {{"step_naive<D2Q9,f64>", "step_naive<D2Q9,f32>", "step_naive<D2Q9,bf16>",
         "step_naive<D2Q9,f16>"},
@@ -154,6 +164,8 @@ KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, in
   if (kernel == MACLAB_KERNEL_FOLDED)
     return KernelInfo{MACLAB_KERNEL_FOLDED, 1, 1, fold_threads(g, precision, ty),
                       kernel_name(g, precision, kernel)};
+  if (kernel == MACLAB_KERNEL_SEGMENT)
+    return KernelInfo{MACLAB_KERNEL_SEGMENT, 1, 1, 256, kernel_name(g, precision, kernel)};
   return KernelInfo{MACLAB_KERNEL_REFERENCE, 1, 1, 256, kernel_name(g, precision, kernel)};
 }
 
@@ -166,6 +178,10 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel) {
       return launch_tiled(s, stream, s.ty, s.tz);
     case MACLAB_KERNEL_FOLDED:
       return launch_fold(s, stream, s.ty, s.tz);
+    case MACLAB_KERNEL_SEGMENT:
+      if (!s.seg_inst || !s.seg_items) return cudaErrorInvalidValue;
+      return launch_batch_step(s.precision, s.seg_inst, s.seg_items, s.seg_n_items, s.cur, s.seg_blocks,
+                               kBatchSegW1, stream);
     default:
       return cudaErrorInvalidValue;
   }

@@ -113,7 +113,7 @@ def test_single_domain_tune(lat, dims, periodic, walls):
     ty, tz = s.tune()
     assert np.array_equal(s.get_lattice_state(), x)
     kernel = s.kernel_info()["kernel"]
-    assert kernel in (M.KERNEL_TILED, M.KERNEL_FOLDED)
+    assert kernel in (M.KERNEL_TILED, M.KERNEL_FOLDED, M.KERNEL_SEGMENT)
     s.step(3)
     r_g, u_g = s.get_state()
     r_o, u_o = orc.step(lat, case.rho, case.u, periodic, wall=case.wall_mask, nsteps=5)

@@ -194,6 +194,72 @@ def test_folded_rejects_unsupported(precision, dims):
     s.close()
 
 
+# The segment kernel (the batched D2Q9 kernel on one domain) for every width it
+# serves, tz = rows per work item.
+SEG_CASES = [
+    ((16, 13), 0b11, "none", 0),
+    ((64, 37), 0b00, "box", 2),
+    ((96, 41), 0b01, "mixed", 4),
+    ((4, 9), 0b11, "none", 16),
+    ((256, 70), 0b10, "box", 3),
+    ((248, 33), 0b11, "mixed", 0),
+]
+
+
+@pytest.mark.parametrize("dims,periodic,walls,rows", SEG_CASES)
+@pytest.mark.parametrize("precision", [M.F64, M.F32])
+def test_segment_kernel(dims, periodic, walls, rows, precision):
+    case = inputs.random_case(D2, dims, periodic, seed=44, u_amp=0.08, rho_amp=0.02, walls=walls,
+                              force=(1e-4, -2e-4))
+    s = M.Solver.from_case(case, precision)
+    s.set_kernel(M.KERNEL_SEGMENT)
+    s.set_tile(0, rows)
+    assert s.kernel_info()["kernel"] == M.KERNEL_SEGMENT
+    s.step(7)
+    r_g, u_g = s.get_state()
+    x = s.get_lattice_state().copy()
+    s.close()
+    r_o, u_o = orc.step(D2, case.rho, case.u, case.periodic, wall=case.wall_mask, force=case.force,
+                        nsteps=7)
+    assert_parity(r_g, u_g, r_o, u_o, precision)
+    # the same bits as the tiled kernel
+    t = M.Solver.from_case(case, precision)
+    t.set_kernel(M.KERNEL_TILED)
+    t.step(7)
+    assert np.array_equal(t.get_lattice_state(), x)
+    t.close()
+
+
+def test_segment_default_for_large_2d_and_graphs():
+    """1024^2 picks the segment kernel; 40 steps (a 32-step graph and 8
+    launches) equal the tiled kernel's bits; a change of rows per item
+    rebuilds the work list and keeps the result."""
+    case = inputs.random_case(D2, (1024, 1024), 0b00, seed=45, u_amp=0.05, walls="box")
+    s = M.Solver.from_case(case, M.F32)
+    assert s.kernel_info()["kernel"] == M.KERNEL_SEGMENT
+    s.step(20)
+    s.set_tile(0, 8)
+    s.step(20)
+    t = M.Solver.from_case(case, M.F32)
+    t.set_kernel(M.KERNEL_TILED)
+    t.step(40)
+    assert np.array_equal(s.get_lattice_state(), t.get_lattice_state())
+    s.close()
+    t.close()
+
+
+def test_segment_rejects_3d_and_odd_widths():
+    for case in (inputs.random_case(D3, (8, 8, 8), 0b111, seed=46),
+                 inputs.random_case(D2, (17, 13), 0b11, seed=47)):
+        s = M.Solver.from_case(case, M.F32)
+        before = s.kernel_info()["kernel"]
+        with pytest.raises(M.MacLABError) as ei:
+            s.set_kernel(M.KERNEL_SEGMENT)
+        assert ei.value.status == M.ERR_UNSUPPORTED
+        assert s.kernel_info()["kernel"] == before
+        s.close()
+
+
 def test_tiled_rejects_unsupported_shape():
     case = inputs.random_case(D2, (17, 13), 0b11, seed=39)
     s = M.Solver.from_case(case, M.F32)
