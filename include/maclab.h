@@ -135,7 +135,8 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * tile's edge rows fold their halo rows in; needs ny divisible by the tile's
  * rows); MACLAB_KERNEL_SEGMENT is the batched D2Q9 kernel run on one domain
  * (a warp per 30-quad row segment, x exchange by warp shuffles, no shared
- * memory; nx % 4 == 0; the tile's tz is its rows per work item, default 4),
+ * memory; nx % 4 == 0; the tile's tz is its rows per work item, default 4,
+ * and ty = 2 asks for two time steps per launch, see maclab_batch_set_depth),
  * the default for D2Q9 grids of at least 65,536 quads.  All compute Eqs.
  * (4)-(5) with the same terms per node (the folded kernel sums them in
  * another order; the segment and tiled kernels give identical bits). */
@@ -149,10 +150,13 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * serve this domain (then the handle keeps its previous choice). */
 maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel);
 
-/* Tile shape of the tiled (or folded) kernel in use: ty rows of y per block (3D only) and tz
- * planes of the slowest axis per block; 0 keeps the library's default.
- * MACLAB_ERR_UNSUPPORTED if no built instance has that shape for this domain
- * (the previous shape is kept). */
+/* Tile shape of the kernel in use.  Tiled and folded kernels: ty rows of y per
+ * block (3D only) and tz planes of the slowest axis per block.  Segment kernel:
+ * ty time steps per launch (1 or 2; 2 needs FP32 or FP64 storage and nx >= 8,
+ * and a run of n steps then ends with a one-step launch so that the previous
+ * state is step n - 1) and tz rows per work item.  0 keeps the library's
+ * default.  MACLAB_ERR_UNSUPPORTED if no built instance has that shape for this
+ * domain (the previous shape is kept). */
 maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz);
 
 /* Describe the kernel in use: out[0] = kernel id (REFERENCE, TILED, FOLDED or SEGMENT),

@@ -427,7 +427,14 @@ static StepLaunch step_launch(const maclab_ctx* h, int from) {
   s.seg_n_items = h->seg_n_items;
   s.seg_blocks = h->seg_blocks;
   s.cur = from;
+  s.seg_depth = h->seg_depth;
+  s.seg_steps = h->kernel == MACLAB_KERNEL_SEGMENT ? h->seg_depth : 1;
   return s;
+}
+
+// Time steps one launch of the handle's kernel advances.
+static int launch_depth(const maclab_ctx* h) {
+  return h->kernel == MACLAB_KERNEL_SEGMENT ? h->seg_depth : 1;
 }
 
 static int device_sms() {
@@ -441,13 +448,15 @@ static int device_sms() {
 }
 
 // The segment kernel's descriptor of this domain and its work list for the
-// current rows per item (tz, default 4), built on first use and after a change
-// of tz; graphs captured with the old list are dropped.  Synchronises the
-// handle's stream when it uploads.
+// current rows per item (tz, default 4) and steps per launch (ty: 2 for two,
+// else one), built on first use and after a change of either; graphs captured
+// with the old list are dropped.  Synchronises the handle's stream when it
+// uploads.
 static maclab_status segment_prepare(maclab_ctx* h) {
   if (h->kernel != MACLAB_KERNEL_SEGMENT) return MACLAB_OK;
   const int rows = h->tz > 0 ? h->tz : 4;
-  if (h->d_seg_inst && h->d_seg_items && h->seg_rows == rows) return MACLAB_OK;
+  const int depth = segment_depth(h->g, h->precision, h->ty);
+  if (h->d_seg_inst && h->d_seg_items && h->seg_rows == rows && h->seg_depth == depth) return MACLAB_OK;
   if (!h->d_seg_inst) {
     if (cudaMalloc(&h->d_seg_inst, batch_inst_bytes()) != cudaSuccess) {
       cudaGetLastError();
@@ -458,7 +467,7 @@ static maclab_status segment_prepare(maclab_ctx* h) {
   std::vector<unsigned char> inst(batch_inst_bytes());
   batch_fill_inst(inst.data(), h->g, h->buf[0], h->buf[1], h->force_lat);
   std::vector<int> items;
-  batch_items(0, h->g, rows, 1, items);
+  batch_items(0, h->g, rows, depth, items);
   void* d = nullptr;
   if (cudaMalloc(&d, items.size() * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -473,14 +482,17 @@ static maclab_status segment_prepare(maclab_ctx* h) {
   h->d_seg_items = d;
   h->seg_n_items = (int)(items.size() / 4);
   h->seg_rows = rows;
-  const int want = (h->seg_n_items + 7) / 8;  // 256-thread blocks, two per SM
-  h->seg_blocks = want < 2 * device_sms() ? (want > 0 ? want : 1) : 2 * device_sms();
+  h->seg_depth = depth;
+  // one step per launch: 256-thread blocks, two per SM; two: 128-thread blocks, three per SM
+  const int warps = depth == 2 ? 4 : 8, per_sm = depth == 2 ? 3 : 2;
+  const int want = (h->seg_n_items + warps - 1) / warps;
+  h->seg_blocks = want < per_sm * device_sms() ? (want > 0 ? want : 1) : per_sm * device_sms();
   drop_graphs(h);
   return MACLAB_OK;
 }
 
-// Capture graph_steps launches starting from buffer c (graph_steps is even, so
-// the graph ends on buffer c again).
+// Capture graph_steps / depth launches (graph_steps steps) starting from
+// buffer c; with an odd number of launches the graph ends on buffer c ^ 1.
 static maclab_status build_graph(maclab_ctx* h, int c) {
   if (!h->capture_stream) {
     if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -489,7 +501,8 @@ static maclab_status build_graph(maclab_ctx* h, int c) {
   cudaGraph_t graph = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeRelaxed), "begin capture");
   cudaError_t err = cudaSuccess;
-  for (int k = 0; k < h->graph_steps && err == cudaSuccess; ++k)
+  const int launches = h->graph_steps / launch_depth(h);
+  for (int k = 0; k < launches && err == cudaSuccess; ++k)
     err = launch_step(step_launch(h, c ^ (k & 1)), h->capture_stream, h->kernel);
   cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &graph);
   if (err != cudaSuccess || e2 != cudaSuccess) {
@@ -511,22 +524,34 @@ maclab_status maclab_step(maclab_handle h, int64_t n) {
   DeviceGuard dg(h->device);
   maclab_status ps = segment_prepare(h);
   if (ps != MACLAB_OK) return ps;
-  while (h->graph_steps > 0 && n >= h->graph_steps) {
+  // With two steps per launch the last step is a one-step launch, so that the
+  // other buffer holds step n - 1 (the steady residual reads it).
+  const int k = launch_depth(h);
+  const int64_t bulk = k > 1 && n > 0 ? n - 1 : n;
+  const int launches = h->graph_steps / k;
+  const int64_t gsteps = (int64_t)launches * k;
+  int64_t done = 0;
+  while (gsteps > 0 && bulk - done >= gsteps) {
     if (!h->graph_exec[h->cur]) {
       maclab_status s = build_graph(h, h->cur);
       if (s != MACLAB_OK) return s;
     }
     CUDA_TRY(cudaGraphLaunch(h->graph_exec[h->cur], h->stream), "graph launch");
-    h->steps += h->graph_steps;
-    n -= h->graph_steps;
-    h->prev_valid = true;
+    if (launches & 1) h->cur ^= 1;
+    done += gsteps;
   }
-  for (int64_t k = 0; k < n; ++k) {
+  for (; bulk - done >= k; done += k) {
     CUDA_TRY(launch_step(step_launch(h, h->cur), h->stream, h->kernel), "step launch");
     h->cur ^= 1;
-    h->steps += 1;
-    h->prev_valid = true;
   }
+  for (; done < n; ++done) {
+    StepLaunch sl = step_launch(h, h->cur);
+    sl.seg_steps = 1;
+    CUDA_TRY(launch_step(sl, h->stream, h->kernel), "step launch");
+    h->cur ^= 1;
+  }
+  h->steps += n;
+  if (n > 0) h->prev_valid = true;
   return MACLAB_OK;
 }
 
@@ -694,7 +719,8 @@ maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (ty < 0 || tz < 0 || tz > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad tile shape");
   const bool ok = h->kernel == MACLAB_KERNEL_FOLDED    ? fold_supported(h->g, h->precision, ty)
-                  : h->kernel == MACLAB_KERNEL_SEGMENT ? ty == 0  // tz: rows per work item
+                  : h->kernel == MACLAB_KERNEL_SEGMENT
+                      ? (ty <= 1 || segment_depth(h->g, h->precision, ty) == 2)  // ty: steps per launch, tz: rows
                                                        : tiled_supported(h->g, h->precision, ty, tz);
   if (!ok) return fail(MACLAB_ERR_UNSUPPORTED, "no built tiled instance has this shape");
   drop_graphs(h);
@@ -1026,7 +1052,8 @@ std::map<std::string, TuneChoice> g_tune_cache;
 
 bool shape_supported(const maclab_ctx* h, int kernel, int ty, int tz) {
   if (kernel == MACLAB_KERNEL_SEGMENT)
-    return ty == 0 && step_kernel_supported(h->g, h->precision, MACLAB_KERNEL_SEGMENT);
+    return step_kernel_supported(h->g, h->precision, MACLAB_KERNEL_SEGMENT) &&
+           (ty <= 1 || segment_depth(h->g, h->precision, ty) == 2);
   return kernel == MACLAB_KERNEL_FOLDED ? fold_supported(h->g, h->precision, ty)
                                         : tiled_supported(h->g, h->precision, ty, tz);
 }
@@ -1130,25 +1157,31 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
     cudaGraphExecDestroy(exec);
     return ms;
   };
-  const int seg_rows[] = {2, 4, 8};  // the segment kernel's tz: rows per work item
-  for (int kernel : {MACLAB_KERNEL_TILED, MACLAB_KERNEL_FOLDED, MACLAB_KERNEL_SEGMENT})
+  // candidates (kernel, ty, tz): tiled and folded shapes; the segment kernel
+  // with one or two steps per launch (ty) and 2, 4 or 8 rows per work item (tz)
+  struct Cand {
+    int kernel, ty, tz;
+  };
+  std::vector<Cand> cands;
+  for (int kernel : {MACLAB_KERNEL_TILED, MACLAB_KERNEL_FOLDED})
     for (int a = 0; a < n_ty; ++a)
-      for (int tz : (kernel == MACLAB_KERNEL_SEGMENT ? std::vector<int>(std::begin(seg_rows), std::end(seg_rows))
-                                                     : std::vector<int>(std::begin(tzs), std::end(tzs)))) {
-        const int ty = h->g.d == 3 ? tys3[a] : 0;
-        if (!shape_supported(h, kernel, ty, tz)) continue;
-        h->kernel = kernel;
-        h->ty = ty;
-        h->tz = tz;
-        if (segment_prepare(h) != MACLAB_OK) continue;
-        const float ms = graph_ms(8) / 8;
-        if (ms < best) {
-          best = ms;
-          bkernel = kernel;
-          bty = ty;
-          btz = tz;
-        }
-      }
+      for (int tz : tzs) cands.push_back(Cand{kernel, h->g.d == 3 ? tys3[a] : 0, tz});
+  for (int ty : {0, 2})
+    for (int tz : {2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_SEGMENT, ty, tz});
+  for (const Cand& c : cands) {
+    if (!shape_supported(h, c.kernel, c.ty, c.tz)) continue;
+    h->kernel = c.kernel;
+    h->ty = c.ty;
+    h->tz = c.tz;
+    if (segment_prepare(h) != MACLAB_OK) continue;
+    const float ms = graph_ms(8) / (8 * launch_depth(h));  // per time step
+    if (ms < best) {
+      best = ms;
+      bkernel = c.kernel;
+      bty = c.ty;
+      btz = c.tz;
+    }
+  }
   cudaError_t e = cudaGetLastError();
   // restore
   h->cur = 0;

@@ -108,6 +108,8 @@ struct StepLaunch {
   const void* seg_inst = nullptr;
   const void* seg_items = nullptr;
   int seg_n_items = 0, seg_blocks = 0, cur = 0;
+  int seg_depth = 1;  // steps per launch the work list was cut for (1 or 2)
+  int seg_steps = 1;  // steps this launch advances (1, or 2 with seg_depth 2)
 };
 
 // Defined in step.cu.  Kernel ids follow MACLAB_KERNEL_* of maclab.h.
@@ -119,6 +121,7 @@ struct KernelInfo {
   const char* name;      // static name of the instance
 };
 bool step_kernel_supported(const Geometry& g, int precision, int kernel);
+int segment_depth(const Geometry& g, int precision, int ty);
 int pick_step_kernel(const Geometry& g, int precision);
 KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, int ty, int tz);
 // Queue one launch group of `kernel` (advances steps_per_launch steps).
@@ -226,7 +229,7 @@ struct maclab_ctx {
   // segment kernel (a batch of this one domain): descriptor, work list
   void* d_seg_inst = nullptr;
   void* d_seg_items = nullptr;
-  int seg_n_items = 0, seg_blocks = 0, seg_rows = 0;
+  int seg_n_items = 0, seg_blocks = 0, seg_rows = 0, seg_depth = 1;
   void* d_adj_scratch = nullptr;   // reference adjoint: (L_r, L_m) at every node
   double* d_adj_red = nullptr;     // adjoint: reductions (1 + 4 * n_wall_ids doubles)
 };

@@ -118,6 +118,12 @@ static cudaError_t launch_naive_lat(const StepLaunch& s, cudaStream_t stream) {
   }
 }
 
+// Time steps per launch of the segment kernel for the tile setting ty (2 asks
+// for two steps per launch: FP32 or FP64 storage and nx >= 8; otherwise 1).
+int segment_depth(const Geometry& g, int precision, int ty) {
+  return ty == 2 && (precision == MACLAB_F32 || precision == MACLAB_F64) && g.nx >= 8 ? 2 : 1;
+}
+
 bool step_kernel_supported(const Geometry& g, int precision, int kernel) {
   if (kernel == MACLAB_KERNEL_REFERENCE) return true;
   if (kernel == MACLAB_KERNEL_TILED) return tiled_supported(g, precision, 0, 0);
@@ -164,8 +170,10 @@ KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, in
   if (kernel == MACLAB_KERNEL_FOLDED)
     return KernelInfo{MACLAB_KERNEL_FOLDED, 1, 1, fold_threads(g, precision, ty),
                       kernel_name(g, precision, kernel)};
-  if (kernel == MACLAB_KERNEL_SEGMENT)
-    return KernelInfo{MACLAB_KERNEL_SEGMENT, 1, 1, 256, kernel_name(g, precision, kernel)};
+  if (kernel == MACLAB_KERNEL_SEGMENT) {
+    const int depth = segment_depth(g, precision, ty);
+    return KernelInfo{MACLAB_KERNEL_SEGMENT, depth, 1, depth == 2 ? 128 : 256, kernel_name(g, precision, kernel)};
+  }
   return KernelInfo{MACLAB_KERNEL_REFERENCE, 1, 1, 256, kernel_name(g, precision, kernel)};
 }
 
@@ -180,8 +188,11 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel) {
       return launch_fold(s, stream, s.ty, s.tz);
     case MACLAB_KERNEL_SEGMENT:
       if (!s.seg_inst || !s.seg_items) return cudaErrorInvalidValue;
+      if (s.seg_steps == 2)
+        return launch_batch_step2(s.precision, s.seg_inst, s.seg_items, s.seg_n_items, s.cur, s.seg_blocks,
+                                  stream);
       return launch_batch_step(s.precision, s.seg_inst, s.seg_items, s.seg_n_items, s.cur, s.seg_blocks,
-                               kBatchSegW1, stream);
+                               s.seg_depth == 2 ? kBatchSegW2 : kBatchSegW1, stream);
     default:
       return cudaErrorInvalidValue;
   }

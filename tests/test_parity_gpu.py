@@ -230,6 +230,27 @@ def test_segment_kernel(dims, periodic, walls, rows, precision):
     t.close()
 
 
+@pytest.mark.parametrize("precision", [M.F64, M.F32])
+@pytest.mark.parametrize("steps", [1, 2, 9, 40, 67])
+def test_segment_two_steps_per_launch(precision, steps):
+    """ty = 2: two updates per launch on one domain, runs of n steps ending in a
+    one-step launch; the same bits and the same residual as the tiled kernel."""
+    case = inputs.random_case(D2, (136, 45), 0b01, seed=48, u_amp=0.05, walls="mixed", force=(1e-4, 0.0))
+    s = M.Solver.from_case(case, precision)
+    s.set_kernel(M.KERNEL_SEGMENT)
+    s.set_tile(2, 4)
+    assert s.kernel_info()["steps_per_launch"] == 2
+    s.step(steps)
+    t = M.Solver.from_case(case, precision)
+    t.set_kernel(M.KERNEL_TILED)
+    t.step(steps)
+    assert np.array_equal(s.get_lattice_state(), t.get_lattice_state())
+    assert s.diagnostics()["residual"] == t.diagnostics()["residual"]
+    assert s.params["steps"] == steps
+    s.close()
+    t.close()
+
+
 def test_segment_default_for_large_2d_and_graphs():
     """1024^2 picks the segment kernel; 40 steps (a 32-step graph and 8
     launches) equal the tiled kernel's bits; a change of rows per item
