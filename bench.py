@@ -400,15 +400,16 @@ def suite_leg(M, stream):
                                 "steps_per_launch": info["steps_per_launch"],
                                 "work_items": info["items"]}
     b.close()
-    for name, case, steps in (
-            ("cavity2d_1024", inputs.cavity2d(1024, lid=inputs.lid_speed(1000.0, 1024)), 200),
-            ("cavity2d_256", inputs.cavity2d(256, lid=inputs.lid_speed(100.0, 256)), 400),
-            ("tgv3d_96", inputs.tgv3d(96, 0.02), 100),
-            ("cavity3d_512_hbm", inputs.cavity3d(512, lid=inputs.lid_speed(100.0, 512)), 10)):
-        s = M.Solver.from_case(case, M.F32, stream=ctypes_stream(stream))
+    for name, case, steps, prec in (
+            ("cavity2d_1024", inputs.cavity2d(1024, lid=inputs.lid_speed(1000.0, 1024)), 200, M.F32),
+            ("cavity2d_256", inputs.cavity2d(256, lid=inputs.lid_speed(100.0, 256)), 400, M.F32),
+            ("cavity3d_128_bf16", cavity_case(128, 100.0), 100, M.BF16_STORE),
+            ("tgv3d_96", inputs.tgv3d(96, 0.02), 100, M.F32),
+            ("cavity3d_512_hbm", inputs.cavity3d(512, lid=inputs.lid_speed(100.0, 512)), 10, M.F32)):
+        s = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
         s.tune()
         ms = _timed_steps(torch, stream, s.step, steps)
-        bpl = 8 * (case.d + 1)
+        bpl = (4 if prec == M.BF16_STORE else 8) * (case.d + 1)
         mlups = case.n_fluid * steps / (ms * 1e-3) / 1e6
         out[name] = {"mlups": mlups, "fluid_nodes": case.n_fluid, "kernel": s.kernel_tag(),
                      "hbm_frac_algorithmic": mlups * 1e6 * bpl / (peaks()[0] * 1e9)}

@@ -134,7 +134,8 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * MACLAB_KERNEL_FOLDED is its D3Q19 FP32 form without halo-row threads (the
  * tile's edge rows fold their halo rows in; needs ny divisible by the tile's
  * rows); MACLAB_KERNEL_SEGMENT is the batched D2Q9 kernel run on one domain
- * (a warp per 30-quad row segment, x exchange by warp shuffles, no shared
+ * (a warp per 30-quad row segment, x exchange by warp shuffles; with two
+ * steps per launch the rows are staged four ahead in the warp's own shared
  * memory; nx % 4 == 0; the tile's tz is its rows per work item, default 4,
  * and ty = 2 asks for two time steps per launch, see maclab_batch_set_depth),
  * the default for D2Q9 grids of at least 65,536 quads.  All compute Eqs.

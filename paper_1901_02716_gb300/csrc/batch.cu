@@ -15,8 +15,10 @@
 //    around the row end is lane-swapped on load, which is what the seam
 //    between the half rows needs.
 //  * Equilibria moving +x leave pair b for the next lane's pair a, those moving
-//    -x leave pair a for the previous lane's pair b: warp shuffles, no shared
-//    memory, no block barrier.  The halo lanes' own sums are discarded.
+//    -x leave pair a for the previous lane's pair b: warp shuffles, no block
+//    barrier.  The halo lanes' own sums are discarded.
+//  * Input rows are prefetched one row ahead in registers (the two-step
+//    kernel below stages them four rows ahead through shared memory).
 //  * The three destination rows of momentum sums live in registers, as in
 //    step_tiled.
 
@@ -113,6 +115,7 @@ __device__ __forceinline__ void batch_row_update(const typename Pair<C>::P (&st)
     }
   });
 }
+
 
 // segw: quads per work item's segment (30, or fewer when the work list was cut
 // for two steps per launch)
@@ -275,6 +278,28 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
 
 constexpr int kSegW2 = kBatchSegW2;  // output quads per warp at depth 2
 
+// Per-warp ring of kRowRing staged input rows in shared memory: each lane's
+// quad of every field, copied with cp.async kRowRing rows ahead of its use.  A
+// lane reads back only what it copied itself, so the ring needs no barrier.
+constexpr int kRowRing = 4;
+template <typename S, int K>
+struct RowRing {
+  static constexpr int QW = Quad<S>::BYTES;
+  static constexpr size_t warp_bytes = (size_t)kRowRing * K * 32 * QW;
+  unsigned char* base;  // this lane's quad of slot 0, field 0
+  uint32_t sh;          // its shared-space address
+  __device__ __forceinline__ RowRing(unsigned char* smem, int warp_in_block, int lane) {
+    base = smem + (size_t)warp_in_block * warp_bytes + (size_t)lane * QW;
+    sh = (uint32_t)__cvta_generic_to_shared(base);
+  }
+  __device__ __forceinline__ uint32_t slot_sh(int slot, int f) const {
+    return sh + (uint32_t)((slot * K + f) * 32 * QW);
+  }
+  __device__ __forceinline__ const S* slot_ptr(int slot, int f) const {
+    return reinterpret_cast<const S*>(base + (size_t)(slot * K + f) * 32 * QW);
+  }
+};
+
 // Intermediate state of one row from its sums (the arithmetic of the store of
 // batch_step_d2q9), with wall lanes (bits a.x, a.y, b.x, b.y) keeping the
 // row's input state `in`; zero for a row that does not exist.
@@ -323,9 +348,11 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
   using O = Pair<C>;
   using P = typename O::P;
   constexpr int K = 3;
+  extern __shared__ __align__(16) unsigned char batch_smem[];
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const RowRing<S, K> ring(batch_smem, threadIdx.x >> 5, lane);
 
   for (int it = warp; it < n_items; it += nwarps) {
     const BatchItem item = items[it];
@@ -360,8 +387,23 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
 
     auto row_exists = [&](int y) { return (y >= 0 && y < I.ny) || I.py; };
     auto row_mem = [&](int y) { return y < 0 ? y + I.ny : (y >= I.ny ? y - I.ny : y); };
-    // a row of the input (zeros where absent) and the wall lanes of this quad in it
+    // input rows y0 - 2 .. y1 + 1 (index i = y - y0 + 2) through the ring:
+    // issue(i) starts copying row i, load(y) waits for row y and reads it
+    // (zeros where absent) with the wall lanes of this quad in it
+    const int y0 = item.y0, y1 = item.y1;
+    const int nr = y1 - y0 + 4;
+    auto issue = [&](int i) {
+      const int y = y0 - 2 + i;
+      if (i < nr && active && row_exists(y)) {
+        const int64_t off = (int64_t)row_mem(y) * I.nx + 4 * t;
+#pragma unroll
+        for (int f = 0; f < K; ++f) Quad<S>::copy(ring.slot_sh(i % kRowRing, f), in + f * n + off);
+      }
+      cp_async_commit();
+    };
     auto load = [&](int y, P (&st)[K][2], uint32_t& wall) {
+      const int i = y - y0 + 2;
+      cp_async_wait<kRowRing - 1>();
       const bool ok = active && row_exists(y);
       const int ym = row_mem(y);
       const int64_t off = (int64_t)ym * I.nx + 4 * t;
@@ -369,7 +411,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
 #pragma unroll
       for (int f = 0; f < K; ++f) {
         if (ok) {
-          Quad<S>::ld(in + f * n + off, st[f][0], st[f][1]);
+          Quad<S>::lds(ring.slot_ptr(i % kRowRing, f), st[f][0], st[f][1]);
           if (swapped) {
             st[f][0] = O::swap(st[f][0]);
             st[f][1] = O::swap(st[f][1]);
@@ -424,20 +466,14 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     };
 
     // sums of the first update for row d in A[(d - y0 + 3) % 3], of the second in B[...]
-    const int y0 = item.y0, y1 = item.y1;
     P A0[2][K], A1[2][K], A2[2][K], B0[2][K], B1[2][K], B2[2][K];
     zero_sums(A0); zero_sums(A1); zero_sums(A2);
     zero_sums(B0); zero_sums(B1); zero_sums(B2);
-    P st[K][2], nxt[K][2], prev[K][2], mid[K][2];
-    uint32_t w_st = 0, w_nxt = 0, w_prev = 0;
-    auto advance = [&](int y_next) {  // st <- the prefetched row, prefetch row y_next
-#pragma unroll
-      for (int f = 0; f < K; ++f) {
-        st[f][0] = nxt[f][0];
-        st[f][1] = nxt[f][1];
-      }
-      w_st = w_nxt;
-      load(y_next, nxt, w_nxt);
+    P st[K][2], prev[K][2], mid[K][2];
+    uint32_t w_st = 0, w_prev = 0;
+    auto advance = [&](int y) {  // st <- input row y; start copying row y + kRowRing
+      load(y, st, w_st);
+      issue(y - y0 + 2 + kRowRing);
     };
     auto keep = [&]() {  // prev <- st: the input of the row the next emission completes
 #pragma unroll
@@ -449,16 +485,17 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     };
 
     // input row y0 - 2: only its sums into row y0 - 1
-    load(y0 - 2, st, w_st);
-    load(y0 - 1, nxt, w_nxt);
+#pragma unroll
+    for (int i = 0; i < kRowRing; ++i) issue(i);
+    advance(y0 - 2);
     if (row_exists(y0 - 2)) batch_row_update<C, kFirst>(st, A0, A1, A2);
     // input row y0 - 1 (row y0 - 2 of the first update is not needed)
-    advance(y0);
+    advance(y0 - 1);
     batch_row_update<C, kMid>(st, A1, A2, A0);
     zero_sums(A1);
     keep();
     // input row y0 completes intermediate row y0 - 1, the second update's first source
-    advance(y0 + 1);
+    advance(y0);
     batch_row_update<C, kMid>(st, A2, A0, A1);
     batch_emit<C>(A2, prev, w_prev, row_exists(y0 - 1), force, mid);
     zero_sums(A2);
@@ -470,7 +507,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     // ys - 1, ys, ys + 1; Bp/Bc/Bn: second-update sums of rows ys - 2, ys - 1, ys.
     auto body = [&](int ys, P(&Ap)[2][K], P(&Ac)[2][K], P(&An)[2][K], P(&Bp)[2][K], P(&Bc)[2][K],
                     P(&Bn)[2][K]) {
-      advance(ys + 1);
+      advance(ys);
       batch_row_update<C, kMid>(st, Ap, Ac, An);
       batch_emit<C>(Ap, prev, w_prev, row_exists(ys - 1), force, mid);
       zero_sums(Ap);
@@ -482,12 +519,10 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     // input row y1 + 1: completes intermediate row y1 and final row y1 - 1
     auto last = [&](P(&Ap)[2][K], P(&Ac)[2][K], P(&An)[2][K], P(&Bp)[2][K], P(&Bc)[2][K],
                     P(&Bn)[2][K]) {
-#pragma unroll
-      for (int f = 0; f < K; ++f) {
-        st[f][0] = nxt[f][0];
-        st[f][1] = nxt[f][1];
+      if (row_exists(y1 + 1)) {
+        advance(y1 + 1);
+        batch_row_update<C, kLast>(st, Ap, Ac, An);
       }
-      if (row_exists(y1 + 1)) batch_row_update<C, kLast>(st, Ap, Ac, An);
       batch_emit<C>(Ap, prev, w_prev, row_exists(y1), force, mid);
       if (row_exists(y1)) batch_row_update<C, kLast>(mid, Bp, Bc, Bn);
       store(y1 - 1, Bp);
@@ -507,7 +542,8 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
 template <typename S>
 static cudaError_t launch_batch2_t(const BatchInst* insts, const BatchItem* items, int n_items,
                                    int cur, int blocks, cudaStream_t st) {
-  batch_step2_d2q9<S><<<blocks, 128, 0, st>>>(insts, items, n_items, cur);
+  constexpr size_t smem = 4 * RowRing<S, 3>::warp_bytes;  // 4 warps
+  batch_step2_d2q9<S><<<blocks, 128, smem, st>>>(insts, items, n_items, cur);
   return cudaGetLastError();
 }
 
