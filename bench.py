@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--side", type=int, default=128, help="cavity side (nodes, walls included)")
+    p.add_argument("--lattice", default="d3q19", choices=["d3q19", "d2q9"],
+                   help="d2q9: the 2D lid-driven cavity of the same side instead (diagnostic runs)")
     p.add_argument("--re", type=float, default=100.0)
     p.add_argument("--inner", type=int, default=100, help="MacLAB steps per benchmark step")
     p.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "f16"])
@@ -210,7 +212,11 @@ def run_ours(args, rank, world, local_rank):
     if not os.path.exists(M.library_path()):
         _build.build()
     prec = M.PRECISION_NAMES[args.precision]
-    case = cavity_case(args.side, args.re)
+    if args.lattice == "d2q9":
+        from paper_1901_02716_gb300 import inputs
+        case = inputs.cavity2d(args.side, lid=inputs.lid_speed(args.re, args.side))
+    else:
+        case = cavity_case(args.side, args.re)
     stream = torch.cuda.current_stream()
     solver = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
     solver.set_kernel({"auto": M.KERNEL_AUTO, "reference": M.KERNEL_REFERENCE,
@@ -253,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
         solver.close()
         return
 
-    d = 3
+    d = case.d
     bytes_per_lup = (d + 1) * 2 * {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[args.precision]
     steps_per_launch = solver.steps_per_launch()
     algo_bytes = bytes_per_lup * case.n_fluid * steps_per_launch
@@ -267,8 +273,9 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": f"3D lid-driven cavity D3Q19 {args.side}^3 (walls included), "
-                               f"Re={args.re:g}, {args.precision} storage",
+        "config": {"workload": (f"3D lid-driven cavity D3Q19 {args.side}^3" if d == 3 else
+                                f"2D lid-driven cavity D2Q9 {args.side}^2") +
+                               f" (walls included), Re={args.re:g}, {args.precision} storage",
                    "inner_steps": args.inner, "fluid_nodes": case.n_fluid,
                    "l2": "flushed (256 MiB write) before each timed step",
                    "parallelism": f"replicas x{world}"},
@@ -280,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
     }
 
-    if not args.no_extras:
+    if not args.no_extras and d == 3:  # the 2D cavity line is a diagnostic run without the extra legs
         line["e2e"] = e2e_leg(M, case, prec, args, stream)
         line["adjoint_forward"] = adjoint_leg(M, case, prec, args, stream)
         line["suite"] = suite_leg(M, stream)
