@@ -145,7 +145,11 @@ int pick_step_kernel(const Geometry& g, int precision) {
 }
 
 static const char* kernel_name(const Geometry& g, int precision, int kernel) {
-  if (kernel == MACLAB_KERNEL_FOLDED) return "step_fold<D3Q19,f32>";
+  if (kernel == MACLAB_KERNEL_FOLDED) {
+    static const char* fold[4] = {"step_fold<D3Q19,f64>", "step_fold<D3Q19,f32>", "step_fold<D3Q19,bf16>",
+                                  "step_fold<D3Q19,f16>"};
+    return fold[precision & 3];
+  }
   if (kernel == MACLAB_KERNEL_SEGMENT) {
     static const char* seg[4] = {"segment<D2Q9,f64>", "segment<D2Q9,f32>", "segment<D2Q9,bf16>",
                                  "segment<D2Q9,f16>"};

@@ -7,22 +7,27 @@ namespace maclab {
 
 namespace {
 
-// Instantiated (BXC, TY) for FP32 storage, in order of preference for each
-// width (the first whose TY divides ny is the default).
-struct FoldShape {
-  int bxc, ty;
-};
+// Instantiated (BXC, TY) in order of preference for each width (the first whose
+// TY divides ny is the default): FP32 all of them, 16-bit storage the three
+// middle widths' shapes.
 constexpr FoldShape kFoldShapes[] = {{16, 8}, {32, 8}, {32, 4}, {64, 4}, {64, 8}, {128, 4}};
 
+bool fold_shape_built(const FoldShape& s, int precision) {
+  if (precision == MACLAB_F32) return true;
+  if (precision == MACLAB_BF16_STORE || precision == MACLAB_F16_STORE)
+    return (s.bxc == 32 && (s.ty == 8 || s.ty == 4)) || (s.bxc == 64 && s.ty == 4);
+  return false;
+}
+
 bool fold_shape(const Geometry& g, int precision, int ty_req, FoldShape* out) {
-  if (g.d != 3 || g.lattice != kD3Q19 || !g.ilv || precision != MACLAB_F32) return false;
+  if (g.d != 3 || g.lattice != kD3Q19 || !g.ilv || precision == MACLAB_F64) return false;
   const int bx = g.nx / 4;
   int bxc = 0;
   for (int c : {16, 32, 64, 128})
     if (bx <= c) { bxc = c; break; }
   if (!bxc) return false;
   for (const FoldShape& s : kFoldShapes) {
-    if (s.bxc != bxc || (ty_req > 0 && s.ty != ty_req)) continue;
+    if (s.bxc != bxc || (ty_req > 0 && s.ty != ty_req) || !fold_shape_built(s, precision)) continue;
     if (g.ny % s.ty != 0) continue;  // every row of a tile exists
     *out = s;
     return true;
@@ -97,8 +102,12 @@ cudaError_t launch_fold(const StepLaunch& sl, cudaStream_t stream, int ty, int t
   ta.plane_stride = (int64_t)g.nx * g.ny;
   ta.ty = s.ty;
   const int ytiles = g.ny / s.ty;
+  auto dispatch = [&](const void* in, void* out, dim3 grid, int* resident) {
+    return sl.precision == MACLAB_F32 ? fold_dispatch<float>(s, ta, in, out, stream, grid, resident)
+                                      : fold_dispatch_s16(sl.precision, s, ta, in, out, stream, grid, resident);
+  };
   int resident = 0;
-  cudaError_t e = fold_dispatch<float>(s, ta, nullptr, nullptr, stream, dim3(), &resident);
+  cudaError_t e = dispatch(nullptr, nullptr, dim3(), &resident);
   if (e != cudaSuccess) return e;
   ta.nzc = fold_chunks(ta.nplanes, ytiles, tz, resident);
   ta.px = (g.periodic & 1u) ? 1 : 0;
@@ -107,7 +116,7 @@ cudaError_t launch_fold(const StepLaunch& sl, cudaStream_t stream, int ty, int t
   ta.wall_mode = g.wall_mode;
   ta.mask = g.mask;
   for (int i = 0; i < 3; ++i) ta.force[i] = sl.force[i];
-  return fold_dispatch<float>(s, ta, sl.in, sl.out, stream, dim3(ta.nzc, ytiles), nullptr);
+  return dispatch(sl.in, sl.out, dim3(ta.nzc, ytiles), nullptr);
 }
 
 }  // namespace maclab

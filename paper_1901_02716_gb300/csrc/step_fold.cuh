@@ -20,6 +20,16 @@
 
 namespace maclab {
 
+// A block shape: BXC quads of a row by TY rows.
+struct FoldShape {
+  int bxc, ty;
+};
+
+// Launch dispatch for 16-bit storage (step_fold_s16.cu): shapes (32, 8),
+// (32, 4) and (64, 4); with resident set, only the blocks one SM holds.
+cudaError_t fold_dispatch_s16(int precision, const FoldShape& s, const TiledArgs& ta, const void* in,
+                              void* out, cudaStream_t st, dim3 grid, int* resident);
+
 template <typename S, int BXC, int TY>
 struct FoldLayout {
   using C = typename Store<S>::C;

@@ -181,8 +181,37 @@ def test_folded_matches_tiled_kernel(dims, periodic, walls, ty):
     assert np.abs(u1 - u2).max() < 2e-6 * np.abs(u1).max()
 
 
+@pytest.mark.parametrize("precision", [M.BF16_STORE, M.F16_STORE])
+@pytest.mark.parametrize("dims,periodic,walls,ty", [((128, 8, 6), 0b000, "box", 0),
+                                                    ((96, 12, 10), 0b010, "mixed", 0),
+                                                    ((128, 16, 11), 0b000, "box", 8),
+                                                    ((256, 8, 5), 0b111, "none", 0)])
+def test_folded_kernel_16bit_storage(precision, dims, periodic, walls, ty):
+    """16-bit storage, FP32 arithmetic: the oracle within the stated storage
+    error, and the tiled kernel within one rounding of the stored value."""
+    case = inputs.random_case(D3, dims, periodic, seed=49, u_amp=0.08, rho_amp=0.02, walls=walls,
+                              force=(1e-4, -2e-4, 3e-4))
+    out = []
+    for kern in (M.KERNEL_FOLDED, M.KERNEL_TILED):
+        s = M.Solver.from_case(case, precision)
+        s.set_kernel(kern)
+        if ty and kern == M.KERNEL_FOLDED:
+            s.set_tile(ty, 0)
+        assert s.kernel_info()["kernel"] == kern
+        s.step(7)
+        out.append(s.get_state())
+        s.close()
+    (r_f, u_f), (r_t, u_t) = out
+    r_o, u_o = orc.step(D3, case.rho, case.u, case.periodic, wall=case.wall_mask, force=case.force,
+                        nsteps=7)
+    assert_parity(r_f, u_f, r_o, u_o, precision)
+    ulp = 2.0 ** -8 if precision == M.BF16_STORE else 2.0 ** -11
+    assert np.abs(u_f - u_t).max() <= 4 * ulp * np.abs(u_t).max()
+    assert np.abs(r_f - r_t).max() <= 4 * ulp * 0.05
+
+
 @pytest.mark.parametrize("precision,dims", [(M.F64, (32, 8, 5)), (M.F32, (32, 6, 5)),
-                                            (M.F32, (16, 12, 5))])
+                                            (M.F32, (16, 12, 5)), (M.BF16_STORE, (16, 8, 5))])
 def test_folded_rejects_unsupported(precision, dims):
     case = inputs.random_case(D3, dims, 0b111, seed=43)
     s = M.Solver.from_case(case, precision)
