@@ -60,3 +60,41 @@ def step(lattice_d, dims, periodic, rho, u, wall=None, force=None):
         rho_n[x] = r
         u_n[x] = tuple(m[i] / r + force[i] for i in range(lattice_d))
     return rho_n, u_n
+
+
+def bgk_run(dims, rho, u, nsteps, tau):
+    """Exact rational single-relaxation-time LBM (Eq. (1) with a BGK
+    collision of relaxation time tau) on a fully periodic D2Q9 grid, started
+    from f = f^eq(rho, u) (Eq. (2)).  Each step: moments (Eq. (3)), collide
+    f <- f + (f^eq - f) / tau, then stream f_a(x + c_a) <- f_a(x).  Returns the
+    moments (rho, u) after nsteps; tau is a Fraction."""
+    def feq(r, v):
+        uu = sum(vi * vi for vi in v)
+        out = []
+        for c, w in D2Q9:
+            cu = c[0] * v[0] + c[1] * v[1]
+            out.append(w * r * (1 + 3 * cu + Fr(9, 2) * cu * cu - Fr(3, 2) * uu))
+        return out
+
+    def mom(fx):
+        r = sum(fx)
+        m = [sum(c[i] * fa for (c, _), fa in zip(D2Q9, fx)) for i in range(2)]
+        return r, (m[0] / r, m[1] / r)
+
+    nodes = list(product(range(dims[0]), range(dims[1])))
+    f = {x: feq(rho[x], u[x]) for x in nodes}
+    for _ in range(nsteps):
+        post = {}
+        for x in nodes:
+            r, v = mom(f[x])
+            e = feq(r, v)
+            post[x] = [fa + (ea - fa) / tau for fa, ea in zip(f[x], e)]
+        f = {x: [None] * 9 for x in nodes}
+        for x in nodes:
+            for a, (c, _) in enumerate(D2Q9):
+                y = ((x[0] + c[0]) % dims[0], (x[1] + c[1]) % dims[1])
+                f[y][a] = post[x][a]
+    rho_n, u_n = {}, {}
+    for x in nodes:
+        rho_n[x], u_n[x] = mom(f[x])
+    return rho_n, u_n

@@ -1,6 +1,7 @@
 """Standard single-relaxation-time LBM, Eq. (1), that stores the distributions f.
 
-TEST INFRASTRUCTURE ONLY (used by ``tests/`` to pin the oracle).  It is written
+TEST INFRASTRUCTURE ONLY (used by ``tests/`` to pin the oracle, and as the
+oracle of the GPU stream-and-collide comparator at any tau).  It is written
 independently of ``maclab_oracle.c``: numpy, its own velocity tables, and the
 two-step stream-and-collide form of Eq. (1) instead of the macroscopic update.
 

@@ -8,7 +8,9 @@ transposed component):
 * the moment identities of Eq. (14) and isotropy of the weights;
 * exact rational brute force on 4x4 and 4x4x4 grids (walls, wrap, force);
 * the tau = 1 reduction of Eq. (1) (Methods): an independent stream-and-collide
-  LBM that stores f gives the same (rho, u) on periodic grids;
+  LBM that stores f gives the same (rho, u) on periodic grids; at other tau the
+  same comparator (the oracle of the GPU LBM) against an exact rational BGK,
+  and its mass and momentum conservation;
 * closed forms: Couette Eq. (7) and Couette-Poiseuille Eq. (8) steady states
   (exact at the nodes), the shear-wave and Taylor-Green decay factors, and the
   continuum decay exp(-2 nu k^2 t) of Test 4;
@@ -148,6 +150,36 @@ def test_tau1_comparator_differs_at_other_tau():
     r1, u1 = lbm_tau1.run(case.rho, case.u, 3, tau=1.0)
     r2, u2 = lbm_tau1.run(case.rho, case.u, 3, tau=0.8)
     assert np.abs(u1 - u2).max() > 1e-4
+
+
+@pytest.mark.parametrize("tau", [Fr(3, 5), Fr(7, 4)])
+def test_bgk_comparator_exact_rational(tau):
+    """The general-tau stream-and-collide comparator (the oracle of the GPU
+    LBM) against an exact rational BGK on a 4 x 3 periodic grid: a dropped
+    term, a wrong sign or a wrong relaxation in the collision would show."""
+    rng = np.random.default_rng(7)
+    nx, ny = 4, 3
+    rho_q = {(x, y): Fr(int(rng.integers(90, 110)), 100) for x in range(nx) for y in range(ny)}
+    u_q = {k: (Fr(int(rng.integers(-8, 9)), 100), Fr(int(rng.integers(-8, 9)), 100))
+           for k in rho_q}
+    rho = np.array([[float(rho_q[(x, y)]) for x in range(nx)] for y in range(ny)])
+    u = np.array([[[float(u_q[(x, y)][i]) for x in range(nx)] for y in range(ny)] for i in range(2)])
+    r_q, v_q = exact_rational.bgk_run((nx, ny), rho_q, u_q, 3, tau)
+    r_f, u_f = lbm_tau1.run(rho, u, 3, tau=float(tau))
+    for x in range(nx):
+        for y in range(ny):
+            assert abs(r_f[y, x] - float(r_q[(x, y)])) < 1e-14
+            for i in range(2):
+                assert abs(u_f[i, y, x] - float(v_q[(x, y)][i])) < 1e-14
+
+
+@pytest.mark.parametrize("tau", [0.55, 0.8, 1.6])
+def test_bgk_comparator_conserves_mass_and_momentum(tau):
+    case = inputs.random_case(D2, (12, 10), 0b11, seed=8, u_amp=0.08, rho_amp=0.03)
+    r, u = lbm_tau1.run(case.rho, case.u, 20, tau=tau)
+    assert abs(r.sum() - case.rho.sum()) < 1e-11 * case.rho.sum()
+    for i in range(2):
+        assert abs((r * u[i]).sum() - (case.rho * case.u[i]).sum()) < 1e-12 * case.rho.sum()
 
 
 # ---------------------------------------------------------------- closed forms
