@@ -407,6 +407,28 @@ def suite_leg(M, stream):
                                 "steps_per_launch": info["steps_per_launch"],
                                 "work_items": info["items"]}
     b.close()
+    # the stream-and-collide comparator (SRT-BGK D2Q9, tau = 0.8) beside MacLAB on
+    # the same periodic 1024^2 Taylor-Green field: traffic and state per update
+    tg = inputs.tgv2d(1024, 0.02)
+    lb = M.Lbm(1024, 1024, 0.8, M.F32, stream=ctypes_stream(stream))
+    lb.set_state(tg.rho, tg.u)
+    n = 200
+    ms = _timed_steps(torch, stream, lb.step, n)
+    li = lb.info()
+    lb.close()
+    s = M.Solver.from_case(tg, M.F32, stream=ctypes_stream(stream))
+    s.tune()
+    ms_m = _timed_steps(torch, stream, s.step, n)
+    mi = s.kernel_tag()
+    s.close()
+    lb_mlups = li["nodes"] * n / (ms * 1e-3) / 1e6
+    mac_mlups = tg.n_fluid * n / (ms_m * 1e-3) / 1e6
+    out["srt_lbm_vs_maclab_2d_1024"] = {
+        "lbm_mlups": lb_mlups, "lbm_bytes_per_update": li["bytes_per_update"],
+        "lbm_state_bytes": li["state_bytes"],
+        "lbm_hbm_frac_algorithmic": lb_mlups * 1e6 * li["bytes_per_update"] / (peaks()[0] * 1e9),
+        "maclab_mlups": mac_mlups, "maclab_bytes_per_update": 24, "maclab_kernel": mi,
+        "maclab_state_bytes": 2 * 3 * 4 * tg.n_fluid, "speedup": mac_mlups / lb_mlups}
     for name, case, steps, prec in (
             ("cavity2d_1024", inputs.cavity2d(1024, lid=inputs.lid_speed(1000.0, 1024)), 200, M.F32),
             ("cavity2d_256", inputs.cavity2d(256, lid=inputs.lid_speed(100.0, 256)), 400, M.F32),

@@ -339,6 +339,45 @@ const char *maclab_version(void);
 /* Message of the last failing call on this host thread (empty if none). */
 const char *maclab_last_error(void);
 
+/* ---------------------------------------------------------------- comparator
+ * The scheme MacLAB replaces: the single-relaxation-time lattice Boltzmann
+ * method of Eq. (1) (BGK collision, relaxation time tau), which stores the
+ * distributions f and streams and collides them every step.  Fully periodic
+ * D2Q9 grids in lattice units (lattice viscosity (tau - 1/2) / 3); no walls,
+ * force or adjoint.  It holds 2 x 9 values per node and moves 9 + 9 per update
+ * (72 B in FP32, against MacLAB's 2 x 3 held and 24 B moved), which is the
+ * memory and traffic claim of the paper's introduction and discussion; at
+ * tau = 1 it gives MacLAB's (rho, u) (Methods, Eqs. (9)-(13)).  One kernel per
+ * step: every node gathers the streamed post-collision distributions of its
+ * upstream neighbours, forms (rho, u) (Eq. (3)) and the equilibria (Eq. (2)),
+ * relaxes and stores the nine post-collision values.  Velocity order and
+ * weights as the paper lists them with Eq. (1). */
+typedef struct maclab_lbm_ctx *maclab_lbm;
+
+/* nx, ny >= 1 nodes; tau > 1/2; precision MACLAB_F32 or MACLAB_F64 (values
+ * stored and computed in that type); stream: a cudaStream_t or NULL for the
+ * default stream.  Allocates the two distribution buffers and a staging
+ * buffer on the current device.  Errors: MACLAB_ERR_INVALID, MACLAB_ERR_OOM,
+ * MACLAB_ERR_CUDA. */
+maclab_status maclab_lbm_create(int32_t nx, int32_t ny, double tau, int32_t precision, void *stream,
+                                maclab_lbm *out);
+maclab_status maclab_lbm_destroy(maclab_lbm h);
+
+/* Start from f = f^eq(rho, u) (Eq. (2)).  Host arrays, x fastest: rho[ny][nx],
+ * u[2][ny][nx] (lattice units, u / e).  Synchronises the stream. */
+maclab_status maclab_lbm_set_state(maclab_lbm h, const double *rho, const double *u);
+
+/* n steps, queued on the stream. */
+maclab_status maclab_lbm_step(maclab_lbm h, int64_t n);
+
+/* The moments (rho, u) of the current distributions (Eq. (3)) into host
+ * arrays shaped as in maclab_lbm_set_state.  Synchronises the stream. */
+maclab_status maclab_lbm_get_state(maclab_lbm h, double *rho, double *u);
+
+/* out[0] nodes, out[1] bytes of device state (both distribution buffers),
+ * out[2] bytes read and written per node update, out[3] steps taken. */
+maclab_status maclab_lbm_info(maclab_lbm h, int64_t out[4]);
+
 #ifdef __cplusplus
 }
 #endif

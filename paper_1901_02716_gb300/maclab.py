@@ -96,6 +96,13 @@ SIGNATURES = {
     "maclab_version": (ctypes.c_char_p, []),
     "maclab_check_reciprocal": (_S, [ctypes.c_float, ctypes.c_float, ctypes.c_int32,
                                      ctypes.POINTER(ctypes.c_double)]),
+    "maclab_lbm_create": (_S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                               ctypes.c_void_p, ctypes.POINTER(_H)]),
+    "maclab_lbm_destroy": (_S, [_H]),
+    "maclab_lbm_set_state": (_S, [_H, ctypes.c_void_p, ctypes.c_void_p]),
+    "maclab_lbm_step": (_S, [_H, ctypes.c_int64]),
+    "maclab_lbm_get_state": (_S, [_H, ctypes.c_void_p, ctypes.c_void_p]),
+    "maclab_lbm_info": (_S, [_H, ctypes.POINTER(ctypes.c_int64)]),
     "maclab_last_error": (ctypes.c_char_p, []),
 }
 
@@ -507,6 +514,51 @@ class _Member(Solver):
 
     def close(self):
         self.handle = None
+
+
+class Lbm:
+    """The stream-and-collide comparator (maclab_lbm_*): single-relaxation-time
+    D2Q9 LBM of relaxation time tau on a periodic nx x ny grid, lattice units."""
+
+    def __init__(self, nx, ny, tau, precision=F32, stream=None):
+        self.nx, self.ny = int(nx), int(ny)
+        self.handle = _H()
+        _check(lib().maclab_lbm_create(self.nx, self.ny, float(tau), int(precision),
+                                       stream, ctypes.byref(self.handle)),
+               "maclab_lbm_create")
+
+    def set_state(self, rho, u):
+        """rho [ny, nx], u [2, ny, nx] (lattice units); f = f^eq."""
+        r = np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ny, self.nx)
+        v = np.ascontiguousarray(u, dtype=np.float64).reshape(2, self.ny, self.nx)
+        _check(lib().maclab_lbm_set_state(self.handle, r.ctypes.data, v.ctypes.data),
+               "maclab_lbm_set_state")
+
+    def step(self, n=1):
+        _check(lib().maclab_lbm_step(self.handle, int(n)), "maclab_lbm_step")
+
+    def get_state(self):
+        r = np.empty((self.ny, self.nx))
+        v = np.empty((2, self.ny, self.nx))
+        _check(lib().maclab_lbm_get_state(self.handle, r.ctypes.data, v.ctypes.data),
+               "maclab_lbm_get_state")
+        return r, v
+
+    def info(self):
+        out = (ctypes.c_int64 * 4)()
+        _check(lib().maclab_lbm_info(self.handle, out), "maclab_lbm_info")
+        return {"nodes": out[0], "state_bytes": out[1], "bytes_per_update": out[2], "steps": out[3]}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().maclab_lbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
