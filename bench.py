@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--kernel", default="auto", choices=["auto", "reference", "tiled", "folded", "segment"])
     p.add_argument("--ty", type=int, default=0, help="tiled kernel: rows per tile (0 = default)")
     p.add_argument("--tz", type=int, default=0, help="tiled kernel: planes per block (0 = default)")
+    p.add_argument("--leg", default="main", choices=["main", "adjoint", "batch"],
+                   help="adjoint / batch: run only that leg and print its JSON (for profiling)")
     return p.parse_args()
 
 
@@ -499,8 +501,37 @@ def dist_max(x, world):
     return float(t.item())
 
 
+def run_leg(args):
+    """One leg alone, on one GPU: the reverse step on the configured cavity, or
+    the 64 batched cavities; prints the leg's JSON."""
+    import torch
+    from paper_1901_02716_gb300 import _build
+    from paper_1901_02716_gb300 import maclab as M
+    torch.cuda.set_device(0)
+    if not os.path.exists(M.library_path()):
+        _build.build()
+    stream = torch.cuda.current_stream()
+    if args.leg == "adjoint":
+        out = adjoint_leg(M, cavity_case(args.side, args.re), M.PRECISION_NAMES[args.precision], args, stream)
+    else:
+        from paper_1901_02716_gb300 import inputs
+        sides, res, lids = inputs.batch_cavity_sides(64, seed=4)
+        b = M.Batch.from_cases([inputs.cavity2d(n, lid=v) for n, v in zip(sides, lids)], M.F32,
+                               stream=ctypes_stream(stream))
+        rows = b.tune()
+        info = b.info()
+        ms = _timed_steps(torch, stream, b.step, 200)
+        out = {"mlups": info["fluid_nodes"] * 200 / (ms * 1e-3) / 1e6, "rows_per_item": rows,
+               "steps_per_launch": info["steps_per_launch"], "work_items": info["items"]}
+        b.close()
+    print(json.dumps({"leg": args.leg, **out}))
+
+
 def main():
     args = parse()
+    if args.leg != "main":
+        run_leg(args)
+        return
     rank, world, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
