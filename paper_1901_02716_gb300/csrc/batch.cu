@@ -138,7 +138,10 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
     const BatchInst& I = insts[item.inst];
     const S* in = static_cast<const S*>(I.buf[cur]);
     S* out = const_cast<S*>(static_cast<const S*>(I.buf[cur ^ 1]));
-    const int nq = I.nx >> 2;
+    // the descriptor's fields, read once per work item
+    const int d_nx = I.nx, d_ny = I.ny, d_px = I.px, d_py = I.py, d_wall = I.wall_mode;
+    const uint8_t* const d_mask = I.mask;
+    const int nq = d_nx >> 2;
     const int n_int = min(segw, nq - segw * item.seg);
     int t = segw * item.seg - 1 + lane;            // quad of this lane
     const bool interior = lane >= 1 && lane <= n_int;
@@ -155,14 +158,14 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
       force[0] = O::splat(C(I.force[0]));
       force[1] = O::splat(C(I.force[1]));
     }
-    const bool x_lo_wall = I.wall_mode == kWallBox && !I.px && t == 0 && interior;
-    const bool x_hi_wall = I.wall_mode == kWallBox && !I.px && t == nq - 1 && interior;
+    const bool x_lo_wall = d_wall == kWallBox && !d_px && t == 0 && interior;
+    const bool x_hi_wall = d_wall == kWallBox && !d_px && t == nq - 1 && interior;
 
-    auto row_exists = [&](int y) { return (y >= 0 && y < I.ny) || I.py; };
-    auto row_mem = [&](int y) { return y < 0 ? y + I.ny : (y >= I.ny ? y - I.ny : y); };
+    auto row_exists = [&](int y) { return (y >= 0 && y < d_ny) || d_py; };
+    auto row_mem = [&](int y) { return y < 0 ? y + d_ny : (y >= d_ny ? y - d_ny : y); };
     auto load = [&](int y, P (&st)[K][2]) {
       const bool ok = active && row_exists(y);
-      const int64_t off = (int64_t)row_mem(y) * I.nx + 4 * t;
+      const int64_t off = (int64_t)row_mem(y) * d_nx + 4 * t;
 #pragma unroll
       for (int f = 0; f < K; ++f) {
         if (ok) {
@@ -179,12 +182,12 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
     };
     auto store = [&](int y, P (&acc)[2][K]) {
       if (!interior) return;
-      if (!I.py && (y == 0 || y == I.ny - 1)) return;
-      const int64_t off = (int64_t)y * I.nx + 4 * t;
+      if (!d_py && (y == 0 || y == d_ny - 1)) return;
+      const int64_t off = (int64_t)y * d_nx + 4 * t;
       bool wall[4] = {x_lo_wall, false, false, x_hi_wall};
       bool any = x_lo_wall || x_hi_wall;
-      if (I.wall_mode == kWallMask) {
-        const uchar4 m = *reinterpret_cast<const uchar4*>(I.mask + off);
+      if (d_wall == kWallMask) {
+        const uchar4 m = *reinterpret_cast<const uchar4*>(d_mask + off);
         wall[0] = m.x != 0; wall[1] = m.y != 0; wall[2] = m.z != 0; wall[3] = m.w != 0;
         any = wall[0] || wall[1] || wall[2] || wall[3];
       }
@@ -359,7 +362,10 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     const BatchInst& I = insts[item.inst];
     const S* in = static_cast<const S*>(I.buf[cur]);
     S* out = const_cast<S*>(static_cast<const S*>(I.buf[cur ^ 1]));
-    const int nq = I.nx >> 2;                        // >= 2 (checked by the host)
+    // the descriptor's fields, read once per work item
+    const int d_nx = I.nx, d_ny = I.ny, d_px = I.px, d_py = I.py, d_wall = I.wall_mode;
+    const uint8_t* const d_mask = I.mask;
+    const int nq = d_nx >> 2;                        // >= 2 (checked by the host)
     const int n_int = min(kSegW2, nq - kSegW2 * item.seg);
     int t = kSegW2 * item.seg - 2 + lane;            // quad of this lane
     const bool interior = lane >= 2 && lane <= n_int + 1;
@@ -378,15 +384,15 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     }
     // box walls at x = 0 and x = nx - 1 in lane order (a wrapped quad is lane-swapped)
     uint32_t xwall = 0;
-    if (I.wall_mode == kWallBox && !I.px) {
+    if (d_wall == kWallBox && !d_px) {
       if (t == 0) xwall |= swapped ? 2u : 1u;
       if (t == nq - 1) xwall |= swapped ? 4u : 8u;
     }
-    const bool x_lo_wall = I.wall_mode == kWallBox && !I.px && t == 0 && interior;
-    const bool x_hi_wall = I.wall_mode == kWallBox && !I.px && t == nq - 1 && interior;
+    const bool x_lo_wall = d_wall == kWallBox && !d_px && t == 0 && interior;
+    const bool x_hi_wall = d_wall == kWallBox && !d_px && t == nq - 1 && interior;
 
-    auto row_exists = [&](int y) { return (y >= 0 && y < I.ny) || I.py; };
-    auto row_mem = [&](int y) { return y < 0 ? y + I.ny : (y >= I.ny ? y - I.ny : y); };
+    auto row_exists = [&](int y) { return (y >= 0 && y < d_ny) || d_py; };
+    auto row_mem = [&](int y) { return y < 0 ? y + d_ny : (y >= d_ny ? y - d_ny : y); };
     // input rows y0 - 2 .. y1 + 1 (index i = y - y0 + 2) through the ring:
     // issue(i) starts copying row i, load(y) waits for row y and reads it
     // (zeros where absent) with the wall lanes of this quad in it
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     auto issue = [&](int i) {
       const int y = y0 - 2 + i;
       if (i < nr && active && row_exists(y)) {
-        const int64_t off = (int64_t)row_mem(y) * I.nx + 4 * t;
+        const int64_t off = (int64_t)row_mem(y) * d_nx + 4 * t;
 #pragma unroll
         for (int f = 0; f < K; ++f) Quad<S>::copy(ring.slot_sh(i % kRowRing, f), in + f * n + off);
       }
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
       cp_async_wait<kRowRing - 1>();
       const bool ok = active && row_exists(y);
       const int ym = row_mem(y);
-      const int64_t off = (int64_t)ym * I.nx + 4 * t;
+      const int64_t off = (int64_t)ym * d_nx + 4 * t;
       wall = 0;
 #pragma unroll
       for (int f = 0; f < K; ++f) {
@@ -422,24 +428,24 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
         }
       }
       if (ok) {
-        if (I.wall_mode == kWallMask) {
-          const uchar4 m = *reinterpret_cast<const uchar4*>(I.mask + off);
+        if (d_wall == kWallMask) {
+          const uchar4 m = *reinterpret_cast<const uchar4*>(d_mask + off);
           wall = swapped ? ((m.y ? 1u : 0u) | (m.x ? 2u : 0u) | (m.w ? 4u : 0u) | (m.z ? 8u : 0u))
                          : ((m.x ? 1u : 0u) | (m.y ? 2u : 0u) | (m.z ? 4u : 0u) | (m.w ? 8u : 0u));
-        } else if (I.wall_mode == kWallBox) {
-          wall = (!I.py && (ym == 0 || ym == I.ny - 1)) ? 15u : xwall;
+        } else if (d_wall == kWallBox) {
+          wall = (!d_py && (ym == 0 || ym == d_ny - 1)) ? 15u : xwall;
         }
       }
     };
     // final rows: the store of batch_step_d2q9
     auto store = [&](int y, P (&acc)[2][K]) {
       if (!interior) return;
-      if (!I.py && (y == 0 || y == I.ny - 1)) return;
-      const int64_t off = (int64_t)y * I.nx + 4 * t;
+      if (!d_py && (y == 0 || y == d_ny - 1)) return;
+      const int64_t off = (int64_t)y * d_nx + 4 * t;
       bool wall[4] = {x_lo_wall, false, false, x_hi_wall};
       bool any = x_lo_wall || x_hi_wall;
-      if (I.wall_mode == kWallMask) {
-        const uchar4 m = *reinterpret_cast<const uchar4*>(I.mask + off);
+      if (d_wall == kWallMask) {
+        const uchar4 m = *reinterpret_cast<const uchar4*>(d_mask + off);
         wall[0] = m.x != 0; wall[1] = m.y != 0; wall[2] = m.z != 0; wall[3] = m.w != 0;
         any = wall[0] || wall[1] || wall[2] || wall[3];
       }
