@@ -436,6 +436,7 @@ def suite_leg(M, stream):
             ("cavity2d_256", inputs.cavity2d(256, lid=inputs.lid_speed(100.0, 256)), 400, M.F32),
             ("cavity3d_128_bf16", cavity_case(128, 100.0), 100, M.BF16_STORE),
             ("tgv3d_96", inputs.tgv3d(96, 0.02), 100, M.F32),
+            ("cavity2d_8192_hbm", inputs.cavity2d(8192, lid=inputs.lid_speed(1000.0, 8192)), 20, M.F32),
             ("cavity3d_512_hbm", inputs.cavity3d(512, lid=inputs.lid_speed(100.0, 512)), 10, M.F32)):
         s = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
         s.tune()

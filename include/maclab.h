@@ -151,6 +151,16 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * serve this domain (then the handle keeps its previous choice). */
 maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel);
 
+/* Programmatic dependent launch of the tiled, folded and segment step kernels
+ * (on = 1, the default): a launch may be scheduled onto the GPU while the
+ * previous step's kernel is still running; on the device it waits for that
+ * kernel to complete, and for its writes to be visible, before reading or
+ * writing any state, so the results are bit-identical with on = 0 (plain
+ * stream-ordered launches).  It shortens the gap between consecutive steps.
+ * The reference kernel is always launched plainly.  MACLAB_ERR_INVALID unless
+ * on is 0 or 1. */
+maclab_status maclab_set_launch_overlap(maclab_handle h, int32_t on);
+
 /* Tile shape of the kernel in use.  Tiled and folded kernels: ty rows of y per
  * block (3D only) and tz planes of the slowest axis per block.  Segment kernel:
  * ty time steps per launch (1 or 2; 2 needs FP32 or FP64 storage and nx >= 8,
@@ -219,6 +229,9 @@ maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows);
  * single steps.  MACLAB_ERR_UNSUPPORTED unless the batch uses one launch per
  * step, stores FP32 or FP64 and every nx >= 8.  Rebuilds the work list. */
 maclab_status maclab_batch_set_depth(maclab_batch b, int32_t depth);
+
+/* maclab_set_launch_overlap for the batch's launches and its members. */
+maclab_status maclab_batch_set_launch_overlap(maclab_batch b, int32_t on);
 
 /* out[0] members, out[1] total nodes, out[2] fluid nodes, out[3] work items
  * per launch (0 when one launch per member is used), out[4] rows per item,

@@ -429,6 +429,7 @@ static StepLaunch step_launch(const maclab_ctx* h, int from) {
   s.cur = from;
   s.seg_depth = h->seg_depth;
   s.seg_steps = h->kernel == MACLAB_KERNEL_SEGMENT ? h->seg_depth : 1;
+  s.overlap = h->overlap;
   return s;
 }
 
@@ -715,6 +716,14 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
   return MACLAB_OK;
 }
 
+maclab_status maclab_set_launch_overlap(maclab_handle h, int32_t on) {
+  if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  if (on != 0 && on != 1) return fail(MACLAB_ERR_INVALID, "on must be 0 or 1");
+  drop_graphs(h);
+  h->overlap = on;
+  return MACLAB_OK;
+}
+
 maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (ty < 0 || tz < 0 || tz > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad tile shape");
@@ -761,6 +770,7 @@ struct maclab_batch_ctx {
   int rows = 0;                // rows per work item
   int depth = 1;               // time steps per launch (1 or 2)
   int blocks = 0;
+  int overlap = 1;             // programmatic dependent launch
   int cur = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -844,10 +854,11 @@ maclab_status batch_build_items(maclab_batch_ctx* b, int rows, int depth) {
 // One launch of `steps` time steps (1, or b->depth) from buffer c.
 cudaError_t batch_launch_steps(maclab_batch_ctx* b, int c, int steps, cudaStream_t st) {
   if (b->one_launch && steps == 2)
-    return launch_batch_step2(b->precision, b->d_insts, b->d_items, b->n_items, c, b->blocks, st);
+    return launch_batch_step2(b->precision, b->d_insts, b->d_items, b->n_items, c, b->blocks, st,
+                              b->overlap);
   if (b->one_launch)
     return launch_batch_step(b->precision, b->d_insts, b->d_items, b->n_items, c, b->blocks,
-                             b->depth == 2 ? kBatchSegW2 : kBatchSegW1, st);
+                             b->depth == 2 ? kBatchSegW2 : kBatchSegW1, st, b->overlap);
   for (maclab_ctx* m : b->members) {
     cudaError_t e = launch_step(step_launch(m, c), st, m->kernel);
     if (e != cudaSuccess) return e;
@@ -1019,6 +1030,18 @@ maclab_status maclab_batch_set_depth(maclab_batch b, int32_t depth) {
                 "two steps per launch need one launch per step, FP32 or FP64 storage and nx >= 8");
   DeviceGuard dg(b->device);
   return batch_build_items(b, b->rows ? b->rows : 16, depth);
+}
+
+maclab_status maclab_batch_set_launch_overlap(maclab_batch b, int32_t on) {
+  if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
+  if (on != 0 && on != 1) return fail(MACLAB_ERR_INVALID, "on must be 0 or 1");
+  batch_drop_graphs(b);
+  b->overlap = on;
+  for (maclab_ctx* m : b->members) {
+    drop_graphs(m);
+    m->overlap = on;
+  }
+  return MACLAB_OK;
 }
 
 maclab_status maclab_batch_info(maclab_batch b, int64_t out[7]) {

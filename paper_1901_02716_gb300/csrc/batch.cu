@@ -132,6 +132,8 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  pdl_wait();  // the previous step's writes are visible from here on
+  pdl_launch_next();
 
   for (int it = warp; it < n_items; it += nwarps) {
     const BatchItem item = items[it];
@@ -356,6 +358,8 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const RowRing<S, K> ring(batch_smem, threadIdx.x >> 5, lane);
+  pdl_wait();  // the previous step's writes are visible from here on
+  pdl_launch_next();
 
   for (int it = warp; it < n_items; it += nwarps) {
     const BatchItem item = items[it];
@@ -547,41 +551,41 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
 
 template <typename S>
 static cudaError_t launch_batch2_t(const BatchInst* insts, const BatchItem* items, int n_items,
-                                   int cur, int blocks, cudaStream_t st) {
+                                   int cur, int blocks, cudaStream_t st, int overlap) {
   constexpr size_t smem = 4 * RowRing<S, 3>::warp_bytes;  // 4 warps
-  batch_step2_d2q9<S><<<blocks, 128, smem, st>>>(insts, items, n_items, cur);
-  return cudaGetLastError();
+  return launch_kernel(batch_step2_d2q9<S>, dim3(blocks), dim3(128), smem, st, overlap, insts, items,
+                       n_items, cur);
 }
 
 template <typename S>
 static cudaError_t launch_batch_t(const BatchInst* insts, const BatchItem* items, int n_items,
-                                  int cur, int blocks, int segw, cudaStream_t st) {
-  batch_step_d2q9<S><<<blocks, 256, 0, st>>>(insts, items, n_items, cur, segw);
-  return cudaGetLastError();
+                                  int cur, int blocks, int segw, cudaStream_t st, int overlap) {
+  return launch_kernel(batch_step_d2q9<S>, dim3(blocks), dim3(256), 0, st, overlap, insts, items, n_items,
+                       cur, segw);
 }
 
 cudaError_t launch_batch_step(int precision, const void* insts, const void* items, int n_items,
-                              int cur, int blocks, int segw, cudaStream_t st) {
+                              int cur, int blocks, int segw, cudaStream_t st, int overlap) {
   const BatchInst* I = static_cast<const BatchInst*>(insts);
   const BatchItem* T = static_cast<const BatchItem*>(items);
   if (segw < 1 || segw > 30) return cudaErrorInvalidValue;
   switch (precision) {
-    case MACLAB_F64: return launch_batch_t<double>(I, T, n_items, cur, blocks, segw, st);
-    case MACLAB_F32: return launch_batch_t<float>(I, T, n_items, cur, blocks, segw, st);
-    case MACLAB_BF16_STORE: return launch_batch_t<__nv_bfloat16>(I, T, n_items, cur, blocks, segw, st);
-    case MACLAB_F16_STORE: return launch_batch_t<__half>(I, T, n_items, cur, blocks, segw, st);
+    case MACLAB_F64: return launch_batch_t<double>(I, T, n_items, cur, blocks, segw, st, overlap);
+    case MACLAB_F32: return launch_batch_t<float>(I, T, n_items, cur, blocks, segw, st, overlap);
+    case MACLAB_BF16_STORE: return launch_batch_t<__nv_bfloat16>(I, T, n_items, cur, blocks, segw, st, overlap);
+    case MACLAB_F16_STORE: return launch_batch_t<__half>(I, T, n_items, cur, blocks, segw, st, overlap);
   }
   return cudaErrorInvalidValue;
 }
 
 // Two steps per launch: FP32 and FP64 storage only.
 cudaError_t launch_batch_step2(int precision, const void* insts, const void* items, int n_items,
-                               int cur, int blocks, cudaStream_t st) {
+                               int cur, int blocks, cudaStream_t st, int overlap) {
   const BatchInst* I = static_cast<const BatchInst*>(insts);
   const BatchItem* T = static_cast<const BatchItem*>(items);
   switch (precision) {
-    case MACLAB_F64: return launch_batch2_t<double>(I, T, n_items, cur, blocks, st);
-    case MACLAB_F32: return launch_batch2_t<float>(I, T, n_items, cur, blocks, st);
+    case MACLAB_F64: return launch_batch2_t<double>(I, T, n_items, cur, blocks, st, overlap);
+    case MACLAB_F32: return launch_batch2_t<float>(I, T, n_items, cur, blocks, st, overlap);
   }
   return cudaErrorInvalidValue;
 }

@@ -7,11 +7,40 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
 #include <vector>
 
 #include "maclab.h"
 
 namespace maclab {
+
+// ------------------------------------------------------------------ launch overlap
+// Programmatic dependent launch.  A kernel queued by launch_kernel with
+// overlap set may be scheduled onto the SMs while the kernel before it in the
+// stream is still running.  Every such kernel calls pdl_wait() before it
+// touches global memory: it returns once the previous kernel has completed
+// and its writes are visible, so results do not depend on the overlap.
+// pdl_launch_next() then lets the following kernel be scheduled.  Launched
+// without the attribute (overlap 0), both are no-ops and the stream
+// serialises the kernels as usual.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          int overlap, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ------------------------------------------------------------------ storage
 
@@ -110,6 +139,7 @@ struct StepLaunch {
   int seg_n_items = 0, seg_blocks = 0, cur = 0;
   int seg_depth = 1;  // steps per launch the work list was cut for (1 or 2)
   int seg_steps = 1;  // steps this launch advances (1, or 2 with seg_depth 2)
+  int overlap = 0;    // programmatic dependent launch (launch_kernel)
 };
 
 // Defined in step.cu.  Kernel ids follow MACLAB_KERNEL_* of maclab.h.
@@ -170,11 +200,11 @@ cudaError_t launch_adjoint_finish(const Geometry& g, int precision, const void* 
 // Defined in batch.cu.
 // segw: quads per segment of the work list (30 when it was cut for one step per launch)
 cudaError_t launch_batch_step(int precision, const void* insts, const void* items, int n_items,
-                              int cur, int blocks, int segw, cudaStream_t st);
+                              int cur, int blocks, int segw, cudaStream_t st, int overlap);
 constexpr int kBatchSegW1 = 30, kBatchSegW2 = 28;
 // two time steps per launch (FP32 / FP64 storage, every nx >= 8), 128-thread blocks
 cudaError_t launch_batch_step2(int precision, const void* insts, const void* items, int n_items,
-                               int cur, int blocks, cudaStream_t st);
+                               int cur, int blocks, cudaStream_t st, int overlap);
 size_t batch_inst_bytes();
 size_t batch_item_bytes();
 void batch_fill_inst(void* dst, const Geometry& g, void* buf0, void* buf1, const double force[3]);
@@ -216,6 +246,7 @@ struct maclab_ctx {
   int64_t steps = 0;
   int kernel = MACLAB_KERNEL_REFERENCE;
   int ty = 0, tz = 0;              // tiled-kernel shape (0 = default)
+  int overlap = 1;                 // programmatic dependent launch of the step kernels
   void* d_staging = nullptr;       // device staging for host set/get
   size_t staging_cap = 0;
   bool prev_valid = false;         // buf[cur ^ 1] holds the state one step back

@@ -194,9 +194,9 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel) {
       if (!s.seg_inst || !s.seg_items) return cudaErrorInvalidValue;
       if (s.seg_steps == 2)
         return launch_batch_step2(s.precision, s.seg_inst, s.seg_items, s.seg_n_items, s.cur, s.seg_blocks,
-                                  stream);
+                                  stream, s.overlap);
       return launch_batch_step(s.precision, s.seg_inst, s.seg_items, s.seg_n_items, s.cur, s.seg_blocks,
-                               s.seg_depth == 2 ? kBatchSegW2 : kBatchSegW1, stream);
+                               s.seg_depth == 2 ? kBatchSegW2 : kBatchSegW1, stream, s.overlap);
     default:
       return cudaErrorInvalidValue;
   }

@@ -116,6 +116,7 @@ cudaError_t launch_fold(const StepLaunch& sl, cudaStream_t stream, int ty, int t
   ta.wall_mode = g.wall_mode;
   ta.mask = g.mask;
   for (int i = 0; i < 3; ++i) ta.force[i] = sl.force[i];
+  ta.overlap = sl.overlap;
   return dispatch(sl.in, sl.out, dim3(ta.nzc, ytiles), nullptr);
 }
 

@@ -404,6 +404,8 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
   constexpr int W = Cols<BXC>::W;
   constexpr int RS = Lay::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();  // the previous step's writes are visible from here on
+  pdl_launch_next();
   const int tx = threadIdx.x, r = threadIdx.y;
   const int bxr = ta.nx >> 2;  // threads per row actually used
   const bool active = tx < bxr;
@@ -605,8 +607,8 @@ cudaError_t launch_fold_shape(const TiledArgs& ta, const void* in, void* out, cu
     *resident_out = resident;
     return cudaSuccess;
   }
-  kern<<<grid, dim3(BXC, TY), smem, stream>>>(ta, static_cast<const S*>(in), static_cast<S*>(out));
-  return cudaGetLastError();
+  return launch_kernel(kern, grid, dim3(BXC, TY), smem, stream, ta.overlap, ta, static_cast<const S*>(in),
+                       static_cast<S*>(out));
 }
 
 }  // namespace maclab

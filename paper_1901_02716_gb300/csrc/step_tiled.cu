@@ -158,6 +158,7 @@ static cudaError_t launch_tiled_t(const StepLaunch& sl, cudaStream_t stream, int
   ta.wall_mode = g.wall_mode;
   ta.mask = g.mask;
   for (int i = 0; i < 3; ++i) ta.force[i] = sl.force[i];
+  ta.overlap = sl.overlap;
   const dim3 grid(ta.nzc, ytiles);
   return dispatch<LAT, S>(ta, s, sl.in, sl.out, stream, grid);
 }

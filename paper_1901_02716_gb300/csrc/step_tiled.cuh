@@ -74,6 +74,7 @@ struct TiledArgs {
   int wall_mode;
   const uint8_t* mask;     // node types in storage order (kWallMask)
   double force[3];
+  int overlap;             // host side: launch with programmatic dependent launch
 };
 
 // ------------------------------------------------------------------ lane pairs
@@ -669,6 +670,8 @@ __global__ void __launch_bounds__(BXC * RY, TiledMinBlocks<BXC, RY>::value)
   constexpr int K = D + 1;
   constexpr int W = Cols<BXC>::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();  // the previous step's writes are visible from here on
+  pdl_launch_next();
   const int tx = threadIdx.x, r = threadIdx.y;
   const int bxr = ta.nx >> 2;                  // threads per row actually used
   const bool active = tx < bxr;
@@ -865,9 +868,8 @@ cudaError_t launch_shape(const TiledArgs& ta, const TiledShape& s, const void* i
           cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
       if (e != cudaSuccess) return e;                                                         \
     }                                                                                         \
-    kern<<<grid, dim3(BXC, RY), smem, stream>>>(ta, static_cast<const S*>(in),                \
-                                                static_cast<S*>(out));                        \
-    return cudaGetLastError();                                                                \
+    return launch_kernel(kern, grid, dim3(BXC, RY), smem, stream, ta.overlap, ta,            \
+                         static_cast<const S*>(in), static_cast<S*>(out));                    \
   }
 
 #define MACLAB_TILED_INST(LAT, S, BXC, RY)                                                     \

@@ -70,6 +70,7 @@ SIGNATURES = {
     "maclab_sync": (_S, [_H]),
     "maclab_set_kernel": (_S, [_H, ctypes.c_int32]),
     "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
+    "maclab_set_launch_overlap": (_S, [_H, ctypes.c_int32]),
     "maclab_set_graph": (_S, [_H, ctypes.c_int32]),
     "maclab_diagnostics": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
     "maclab_batch_create": (_S, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_H)]),
@@ -78,6 +79,7 @@ SIGNATURES = {
     "maclab_batch_step": (_S, [_H, ctypes.c_int64]),
     "maclab_batch_set_rows": (_S, [_H, ctypes.c_int32]),
     "maclab_batch_set_depth": (_S, [_H, ctypes.c_int32]),
+    "maclab_batch_set_launch_overlap": (_S, [_H, ctypes.c_int32]),
     "maclab_batch_info": (_S, [_H, ctypes.POINTER(ctypes.c_int64)]),
     "maclab_tune": (_S, [_H, ctypes.POINTER(ctypes.c_int32)]),
     "maclab_batch_tune": (_S, [_H, ctypes.POINTER(ctypes.c_int32)]),
@@ -244,6 +246,10 @@ def maclab_set_kernel(h, kernel):
 
 def maclab_set_tile(h, ty, tz):
     return _check(lib().maclab_set_tile(h, int(ty), int(tz)), "maclab_set_tile")
+
+
+def maclab_set_launch_overlap(h, on):
+    return _check(lib().maclab_set_launch_overlap(h, int(on)), "maclab_set_launch_overlap")
 
 
 def maclab_set_graph(h, steps):
@@ -482,6 +488,10 @@ class Solver:
     def set_tile(self, ty=0, tz=0):
         maclab_set_tile(self.handle, ty, tz)
 
+    def set_launch_overlap(self, on):
+        """Programmatic dependent launch of the step kernels (default on)."""
+        maclab_set_launch_overlap(self.handle, int(on))
+
     def kernel_info(self):
         return maclab_kernel_info(self.handle)
 
@@ -610,6 +620,11 @@ class Batch:
     def set_depth(self, depth):
         """Time steps per launch of the single launch (1 or 2)."""
         _check(lib().maclab_batch_set_depth(self.handle, int(depth)), "maclab_batch_set_depth")
+
+    def set_launch_overlap(self, on):
+        """Programmatic dependent launch of the batch's step kernels (default on)."""
+        _check(lib().maclab_batch_set_launch_overlap(self.handle, int(on)),
+               "maclab_batch_set_launch_overlap")
 
     def tune(self):
         r = ctypes.c_int32()
