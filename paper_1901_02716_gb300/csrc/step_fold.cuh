@@ -50,7 +50,10 @@ struct FoldLayout {
   static constexpr size_t ye_pairs = XSH ? 2 * ye_buf_pairs : (size_t)NYS * TY * 2 * W;
   static constexpr size_t exch_bytes = ((sizeof(P) * (xe_pairs + ye_pairs) + 15) / 16) * 16;
   static constexpr size_t stage_bytes = (size_t)kStages * 4 * RS * BXC * Quad<S>::BYTES;
-  static constexpr size_t smem = exch_bytes + stage_bytes;
+  // box walls at x = 0 and x = nx - 1: each row's two wall lanes keep the four
+  // fields of their wall node for the last two planes taken (walls never change)
+  static constexpr size_t wall_bytes = (size_t)TY * 2 * kStages * 16;
+  static constexpr size_t smem = exch_bytes + stage_bytes + wall_bytes;
   static constexpr int THREADS = BXC * TY;
   static constexpr int MIN_BLOCKS = THREADS <= 128 ? 4 : (THREADS <= 256 ? 2 : 1);
 };
@@ -296,39 +299,50 @@ __device__ __forceinline__ void fold_update_xs(const typename Pair<C>::P (&st)[4
   P xb[3], xa[3];  // x-crossing equilibria leaving pair b (+x) and pair a (-x)
 #pragma unroll
   for (int k = 0; k < 3; ++k) xb[k] = xa[k] = O::splat(C(0));
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  // y rows of this plane's buffer: row r carries the c_y = +1 equilibria of
+  // source row r (read by row r + 1), row r - 1 the c_y = -1 ones (read by r - 1)
+  P* const y_up = xs.ye + r * YROW;
+  P* const y_dn = y_up - YROW;
+  // equilibria of pair q with c_y = FY into the y rows (rows of the tile only:
+  // what leaves it is formed by the next tile's halo)
+  auto publish_y = [&](auto fyc, const Terms<3, C>& t, auto qc) {
+    constexpr int FY = decltype(fyc)::value;
+    constexpr int q = decltype(qc)::value;
+    P* const base = FY == 1 ? y_up : y_dn;
+    static_for<0, L::Q>([&](auto I) {
+      constexpr int a = decltype(I)::value;
+      if constexpr (mode_allows<kD3Q19, MODE>(a) && F::fy(a) == FY) {
+        constexpr int fx = F::fx(a);
+        const P T = term<kD3Q19, C, a>(t);
+        P* const row = base + F::yslot(a) * (TY - 1) * YROW;
+        row[q * BXC + xs.tx] = T;
+        if constexpr (fx == 1 && q == 1) {
+          if (xs.wl) row[SEAM] = O::swap(T);
+        } else if constexpr (fx == -1 && q == 0) {
+          if (xs.wr) row[SEAM] = O::swap(T);
+        }
+      }
+    });
+  };
+  static_for<0, 2>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
     Terms<3, C> t;
     const P u[3] = {st[1][q], st[2][q], st[3][q]};
     make_terms<3, C>(st[0][q], u, t);
     static_for<0, L::Q>([&](auto I) {
       constexpr int a = decltype(I)::value;
-      if constexpr (mode_allows<kD3Q19, MODE>(a)) {
-        constexpr int fx = F::fx(a);
-        if constexpr (F::ycross(a)) {
-          // rows of the tile only: what leaves it is formed by the next tile's halo
-          constexpr int fy = F::fy(a);
-          if (fy == 1 ? r < TY - 1 : r > 0) {
-            const P T = term<kD3Q19, C, a>(t);
-            P* row = xs.ye + (F::yslot(a) * (TY - 1) + (fy == 1 ? r : r - 1)) * YROW;
-            row[q * BXC + xs.tx] = T;
-            if constexpr (fx == 1) {
-              if (q == 1 && xs.wl) row[SEAM] = O::swap(T);
-            } else if constexpr (fx == -1) {
-              if (q == 0 && xs.wr) row[SEAM] = O::swap(T);
-            }
-          }
-        } else {
-          constexpr int fz = F::fz(a);
-          const P T = term<kD3Q19, C, a>(t);
-          const int qd = q + fx;
-          if (qd >= 0 && qd < 2) accum<kD3Q19, C, a>(pick<fz>(ap, ac, an)[qd], T);
-          else if constexpr (fx == 1) xb[fold_xidx(a)] = T;
-          else if constexpr (fx == -1) xa[fold_xidx(a)] = T;
-        }
+      if constexpr (mode_allows<kD3Q19, MODE>(a) && !F::ycross(a)) {
+        constexpr int fx = F::fx(a), fz = F::fz(a);
+        const P T = term<kD3Q19, C, a>(t);
+        constexpr int qd = q + fx;
+        if constexpr (qd >= 0 && qd < 2) accum<kD3Q19, C, a>(pick<fz>(ap, ac, an)[qd], T);
+        else if constexpr (fx == 1) xb[fold_xidx(a)] = T;
+        else if constexpr (fx == -1) xa[fold_xidx(a)] = T;
       }
     });
-  }
+    if (r < TY - 1) publish_y(std::integral_constant<int, 1>{}, t, qc);
+    if (r > 0) publish_y(std::integral_constant<int, -1>{}, t, qc);
+  });
   P hb = O::splat(C(0)), ha = O::splat(C(0));
   if (live && halo != 0) {
     P hs[4][2];
@@ -368,28 +382,69 @@ __device__ __forceinline__ void fold_update_xs(const typename Pair<C>::P (&st)[4
     }
   }
   __syncthreads();
-  if (live) {
+  // gather the equilibria with c_y = FY from source row r - FY, a row of the
+  // tile (the halo rows were folded in already)
+  auto gather_y = [&](auto fyc) {
+    constexpr int FY = decltype(fyc)::value;
+    const P* const base = FY == 1 ? y_dn : y_up;
     static_for<0, L::Q>([&](auto I) {
       constexpr int a = decltype(I)::value;
-      if constexpr (mode_allows<kD3Q19, MODE>(a) && F::ycross(a)) {
-        constexpr int fz = F::fz(a), fx = F::fx(a), fy = F::fy(a);
+      if constexpr (mode_allows<kD3Q19, MODE>(a) && F::fy(a) == FY) {
+        constexpr int fz = F::fz(a), fx = F::fx(a);
         auto& dst = pick<fz>(ap, ac, an);
-        // source row r - fy: a row of the tile (the halo rows were folded in already)
-        if (fy == 1 ? r > 0 : r < TY - 1) {
-          const P* row = xs.ye + (F::yslot(a) * (TY - 1) + (fy == 1 ? r - 1 : r)) * YROW;
-          if constexpr (fx == 0) {
-            accum<kD3Q19, C, a>(dst[0], row[xs.tx]);
-            accum<kD3Q19, C, a>(dst[1], row[BXC + xs.tx]);
-          } else if constexpr (fx == 1) {
-            accum<kD3Q19, C, a>(dst[0], row[xs.li]);          // left neighbour's pair b
-            accum<kD3Q19, C, a>(dst[1], row[xs.tx]);          // own pair a
-          } else {
-            accum<kD3Q19, C, a>(dst[0], row[BXC + xs.tx]);    // own pair b
-            accum<kD3Q19, C, a>(dst[1], row[xs.ri]);          // right neighbour's pair a
-          }
+        const P* const row = base + F::yslot(a) * (TY - 1) * YROW;
+        if constexpr (fx == 0) {
+          accum<kD3Q19, C, a>(dst[0], row[xs.tx]);
+          accum<kD3Q19, C, a>(dst[1], row[BXC + xs.tx]);
+        } else if constexpr (fx == 1) {
+          accum<kD3Q19, C, a>(dst[0], row[xs.li]);          // left neighbour's pair b
+          accum<kD3Q19, C, a>(dst[1], row[xs.tx]);          // own pair a
+        } else {
+          accum<kD3Q19, C, a>(dst[0], row[BXC + xs.tx]);    // own pair b
+          accum<kD3Q19, C, a>(dst[1], row[xs.ri]);          // right neighbour's pair a
         }
       }
     });
+  };
+  if (live) {
+    if (r > 0) gather_y(std::integral_constant<int, 1>{});
+    if (r < TY - 1) gather_y(std::integral_constant<int, -1>{});
+  }
+}
+
+// Store of one destination plane (Eq. (5): u' = M / (36 + R) + F) for box
+// walls, every lane with the same instructions: the lane whose quad holds one
+// x-wall node (a.x at x = 0, b.y at x = nx - 1) puts that node's unchanged
+// value, wv (its four fields, kept when the plane was taken), in place of the
+// computed one and stores the whole quad.  Masks, and a quad holding both
+// x-walls (nx = 4), take store_plane's per-node path.
+template <typename S>
+__device__ __forceinline__ void fold_store(S* const (&fp)[4], const uint8_t* mrow, const TiledArgs& ta,
+                                           int64_t off, bool x_lo_wall, bool x_hi_wall, const float4& wv,
+                                           bool skip, typename Quad<S>::P (&acc)[2][4],
+                                           const typename Quad<S>::P (&force)[3]) {
+  using C = typename Store<S>::C;
+  using O = Pair<C>;
+  using P = typename O::P;
+  if (ta.wall_mode == kWallMask || (x_lo_wall && x_hi_wall)) {
+    store_plane<kD3Q19, S>(fp, mrow, ta, off, x_lo_wall, x_hi_wall, skip, acc, force);
+    return;
+  }
+  if (skip) return;
+  P v[4][2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const P inv = O::rcp(O::add(O::splat(C(36)), acc[q][0]));
+    v[0][q] = O::mul(acc[q][0], O::splat(C(1.0 / 36.0)));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[1 + i][q] = O::fma(acc[q][1 + i], inv, force[i]);
+  }
+  const float w[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (x_lo_wall) v[f][0].x = C(w[f]);
+    if (x_hi_wall) v[f][1].y = C(w[f]);
+    Quad<S>::st(fp[f] + off, v[f][0], v[f][1]);
   }
 }
 
@@ -486,6 +541,10 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
   const uint32_t own_off = (uint32_t)(r + 1) * BXC * QW;
   const uint32_t halo_off = (uint32_t)(halo == 1 ? 0 : TY + 1) * BXC * QW;
   const uint32_t stage_sh = (uint32_t)__cvta_generic_to_shared(stage0);
+  // this lane's wall ring (lanes with exactly one x-wall node only)
+  const bool xwall1 = x_lo_wall != x_hi_wall;
+  float4* const wring = reinterpret_cast<float4*>(smem_raw + Lay::exch_bytes + Lay::stage_bytes) +
+                        (r * 2 + (x_hi_wall ? 1 : 0)) * kStages;
   const int np = z1 - z0 + 2;  // planes z0 - 1 .. z1
   auto fetch = [&](int i) {    // start copying plane z0 - 1 + i into its stage
     const int p = z0 - 1 + i;
@@ -516,6 +575,9 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
         st[f][0] = st[f][1] = O::splat(C(0));
       }
     }
+    if (xwall1 && ok)
+      wring[i & (kStages - 1)] = x_lo_wall ? make_float4(st[0][0].x, st[1][0].x, st[2][0].x, st[3][0].x)
+                                           : make_float4(st[0][1].y, st[1][1].y, st[2][1].y, st[3][1].y);
   };
 
   // one source plane into the sums of destination planes p - 1, p, p + 1
@@ -545,7 +607,9 @@ __global__ void __launch_bounds__(BXC * TY, FoldLayout<S, BXC, TY>::MIN_BLOCKS)
   if (plane_exists(z0 - 1)) update(std::integral_constant<int, kFirst>{}, R0, R2, R1);
 
   auto store = [&](int q, P(&acc)[2][K]) {
-    store_plane<kD3Q19, S>(op, mrow, ta, (int64_t)q * ps, x_lo_wall, x_hi_wall, store_skip(q), acc, force);
+    float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (xwall1) wv = wring[(q - z0 + 1) & (kStages - 1)];  // kept when plane q was taken
+    fold_store<S>(op, mrow, ta, (int64_t)q * ps, x_lo_wall, x_hi_wall, wv, store_skip(q), acc, force);
   };
 
   // full plane p: contributions to the sums A (dest p - 1), B (dest p), N (dest
