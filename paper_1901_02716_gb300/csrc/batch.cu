@@ -117,6 +117,57 @@ __device__ __forceinline__ void batch_row_update(const typename Pair<C>::P (&st)
 }
 
 
+// Store of one final row (Eq. (5): u' = M / (36 + R) + F).  In box mode every
+// lane stores its whole quad: a lane whose quad holds one x-wall node (a.x at
+// x = 0, b.y at x = nx - 1) puts that node's unchanged fields wk in place of
+// the computed ones, so the warp never splits into per-node stores.  Masks,
+// and a quad holding both x-walls (nx = 4), store node by node.
+template <typename S>
+__device__ __forceinline__ void batch_store(S* out, int64_t n, int64_t off, const uint8_t* mask, int wall_mode,
+                                            bool x_lo_wall, bool x_hi_wall,
+                                            const typename Store<S>::C (&wk)[3],
+                                            const typename Pair<typename Store<S>::C>::P (&acc)[2][3],
+                                            const typename Pair<typename Store<S>::C>::P (&force)[2]) {
+  using C = typename Store<S>::C;
+  using O = Pair<C>;
+  using P = typename O::P;
+  constexpr int K = 3;
+  P v[K][2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const P inv = O::rcp(O::add(O::splat(C(36)), acc[q][0]));
+    v[0][q] = O::mul(acc[q][0], O::splat(C(1.0 / 36.0)));
+    v[1][q] = O::fma(acc[q][1], inv, force[0]);
+    v[2][q] = O::fma(acc[q][2], inv, force[1]);
+  }
+  if (wall_mode == kWallMask || (x_lo_wall && x_hi_wall)) {
+    bool wall[4] = {x_lo_wall, false, false, x_hi_wall};
+    if (wall_mode == kWallMask) {
+      const uchar4 m = *reinterpret_cast<const uchar4*>(mask + off);
+      wall[0] = m.x != 0; wall[1] = m.y != 0; wall[2] = m.z != 0; wall[3] = m.w != 0;
+    }
+    if (!(wall[0] || wall[1] || wall[2] || wall[3])) {
+#pragma unroll
+      for (int f = 0; f < K; ++f) Quad<S>::st(out + f * n + off, v[f][0], v[f][1]);
+      return;
+    }
+#pragma unroll
+    for (int f = 0; f < K; ++f) {
+      if (!wall[0]) Quad<S>::st1(out + f * n + off + 0, v[f][0].x);
+      if (!wall[1]) Quad<S>::st1(out + f * n + off + 1, v[f][0].y);
+      if (!wall[2]) Quad<S>::st1(out + f * n + off + 2, v[f][1].x);
+      if (!wall[3]) Quad<S>::st1(out + f * n + off + 3, v[f][1].y);
+    }
+    return;
+  }
+#pragma unroll
+  for (int f = 0; f < K; ++f) {
+    if (x_lo_wall) v[f][0].x = wk[f];
+    if (x_hi_wall) v[f][1].y = wk[f];
+    Quad<S>::st(out + f * n + off, v[f][0], v[f][1]);
+  }
+}
+
 // segw: quads per work item's segment (30, or fewer when the work list was cut
 // for two steps per launch)
 template <typename S>
@@ -162,6 +213,7 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
     }
     const bool x_lo_wall = d_wall == kWallBox && !d_px && t == 0 && interior;
     const bool x_hi_wall = d_wall == kWallBox && !d_px && t == nq - 1 && interior;
+    C wk[K] = {C(0), C(0), C(0)};  // x-wall lanes: the wall node's fields in the row stored next
 
     auto row_exists = [&](int y) { return (y >= 0 && y < d_ny) || d_py; };
     auto row_mem = [&](int y) { return y < 0 ? y + d_ny : (y >= d_ny ? y - d_ny : y); };
@@ -186,33 +238,7 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
       if (!interior) return;
       if (!d_py && (y == 0 || y == d_ny - 1)) return;
       const int64_t off = (int64_t)y * d_nx + 4 * t;
-      bool wall[4] = {x_lo_wall, false, false, x_hi_wall};
-      bool any = x_lo_wall || x_hi_wall;
-      if (d_wall == kWallMask) {
-        const uchar4 m = *reinterpret_cast<const uchar4*>(d_mask + off);
-        wall[0] = m.x != 0; wall[1] = m.y != 0; wall[2] = m.z != 0; wall[3] = m.w != 0;
-        any = wall[0] || wall[1] || wall[2] || wall[3];
-      }
-      P v[K][2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const P inv = O::rcp(O::add(O::splat(C(36)), acc[q][0]));
-        v[0][q] = O::mul(acc[q][0], O::splat(C(1.0 / 36.0)));
-        v[1][q] = O::fma(acc[q][1], inv, force[0]);
-        v[2][q] = O::fma(acc[q][2], inv, force[1]);
-      }
-      if (!any) {
-#pragma unroll
-        for (int f = 0; f < K; ++f) Quad<S>::st(out + f * n + off, v[f][0], v[f][1]);
-      } else {
-#pragma unroll
-        for (int f = 0; f < K; ++f) {
-          if (!wall[0]) Quad<S>::st1(out + f * n + off + 0, v[f][0].x);
-          if (!wall[1]) Quad<S>::st1(out + f * n + off + 1, v[f][0].y);
-          if (!wall[2]) Quad<S>::st1(out + f * n + off + 2, v[f][1].x);
-          if (!wall[3]) Quad<S>::st1(out + f * n + off + 3, v[f][1].y);
-        }
-      }
+      batch_store<S>(out, n, off, d_mask, d_wall, x_lo_wall, x_hi_wall, wk, acc, force);
     };
 
     P R0[2][K], R1[2][K], R2[2][K];
@@ -237,6 +263,8 @@ __global__ void __launch_bounds__(256) batch_step_d2q9(const BatchInst* __restri
       load(y + 1, nxt);
       batch_row_update<C, kMid>(st, A, B, N);
       if (y - 1 >= y0) store(y - 1, A);
+#pragma unroll
+      for (int f = 0; f < K; ++f) wk[f] = x_lo_wall ? st[f][0].x : st[f][1].y;  // row y, stored next
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -394,6 +422,9 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     }
     const bool x_lo_wall = d_wall == kWallBox && !d_px && t == 0 && interior;
     const bool x_hi_wall = d_wall == kWallBox && !d_px && t == nq - 1 && interior;
+    // x-wall lanes: the wall node's fields in the final row stored next (walls
+    // keep their values, so the intermediate row's are the input's)
+    C wk[K] = {C(0), C(0), C(0)};
 
     auto row_exists = [&](int y) { return (y >= 0 && y < d_ny) || d_py; };
     auto row_mem = [&](int y) { return y < 0 ? y + d_ny : (y >= d_ny ? y - d_ny : y); };
@@ -446,33 +477,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
       if (!interior) return;
       if (!d_py && (y == 0 || y == d_ny - 1)) return;
       const int64_t off = (int64_t)y * d_nx + 4 * t;
-      bool wall[4] = {x_lo_wall, false, false, x_hi_wall};
-      bool any = x_lo_wall || x_hi_wall;
-      if (d_wall == kWallMask) {
-        const uchar4 m = *reinterpret_cast<const uchar4*>(d_mask + off);
-        wall[0] = m.x != 0; wall[1] = m.y != 0; wall[2] = m.z != 0; wall[3] = m.w != 0;
-        any = wall[0] || wall[1] || wall[2] || wall[3];
-      }
-      P v[K][2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const P inv = O::rcp(O::add(O::splat(C(36)), acc[q][0]));
-        v[0][q] = O::mul(acc[q][0], O::splat(C(1.0 / 36.0)));
-        v[1][q] = O::fma(acc[q][1], inv, force[0]);
-        v[2][q] = O::fma(acc[q][2], inv, force[1]);
-      }
-      if (!any) {
-#pragma unroll
-        for (int f = 0; f < K; ++f) Quad<S>::st(out + f * n + off, v[f][0], v[f][1]);
-      } else {
-#pragma unroll
-        for (int f = 0; f < K; ++f) {
-          if (!wall[0]) Quad<S>::st1(out + f * n + off + 0, v[f][0].x);
-          if (!wall[1]) Quad<S>::st1(out + f * n + off + 1, v[f][0].y);
-          if (!wall[2]) Quad<S>::st1(out + f * n + off + 2, v[f][1].x);
-          if (!wall[3]) Quad<S>::st1(out + f * n + off + 3, v[f][1].y);
-        }
-      }
+      batch_store<S>(out, n, off, d_mask, d_wall, x_lo_wall, x_hi_wall, wk, acc, force);
     };
 
     // sums of the first update for row d in A[(d - y0 + 3) % 3], of the second in B[...]
@@ -484,6 +489,10 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     auto advance = [&](int y) {  // st <- input row y; start copying row y + kRowRing
       load(y, st, w_st);
       issue(y - y0 + 2 + kRowRing);
+    };
+    auto keep_wall = [&]() {  // wk <- intermediate row just emitted, the final row stored next
+#pragma unroll
+      for (int f = 0; f < K; ++f) wk[f] = x_lo_wall ? mid[f][0].x : mid[f][1].y;
     };
     auto keep = [&]() {  // prev <- st: the input of the row the next emission completes
 #pragma unroll
@@ -510,6 +519,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
     batch_emit<C>(A2, prev, w_prev, row_exists(y0 - 1), force, mid);
     zero_sums(A2);
     keep();
+    keep_wall();
     if (row_exists(y0 - 1)) batch_row_update<C, kFirst>(mid, B1, B2, B0);
 
     // input row ys: intermediate row ys - 1 complete, fed to the second update,
@@ -524,6 +534,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
       keep();
       batch_row_update<C, kMid>(mid, Bp, Bc, Bn);
       if (ys - 2 >= y0) store(ys - 2, Bp);
+      keep_wall();
       zero_sums(Bp);
     };
     // input row y1 + 1: completes intermediate row y1 and final row y1 - 1
