@@ -439,11 +439,12 @@ def suite_leg(M, stream):
             ("cavity2d_8192_hbm", inputs.cavity2d(8192, lid=inputs.lid_speed(1000.0, 8192)), 20, M.F32),
             ("cavity3d_512_hbm", inputs.cavity3d(512, lid=inputs.lid_speed(100.0, 512)), 10, M.F32)):
         s = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
-        s.tune()
+        tile = s.tune()
         ms = _timed_steps(torch, stream, s.step, steps)
         bpl = (4 if prec == M.BF16_STORE else 8) * (case.d + 1)
         mlups = case.n_fluid * steps / (ms * 1e-3) / 1e6
         out[name] = {"mlups": mlups, "fluid_nodes": case.n_fluid, "kernel": s.kernel_tag(),
+                     "tile_ty_tz": list(tile) if tile is not None else None,
                      "hbm_frac_algorithmic": mlups * 1e6 * bpl / (peaks()[0] * 1e9)}
         s.close()
         del case

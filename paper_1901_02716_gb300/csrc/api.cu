@@ -1155,8 +1155,9 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
   int bkernel = MACLAB_KERNEL_TILED, bty = 0, btz = 0;
   drop_graphs(h);
   const int n_ty = h->g.d == 3 ? 3 : 1;
-  // each candidate timed on a captured graph of 8 steps (stepping runs in
-  // graphs, where the launch gaps that separate launches would add are absent)
+  // each candidate timed on a captured graph of 8 launches, or 64 where 8 take
+  // under 0.5 ms (stepping runs in graphs, where the launch gaps that separate
+  // launches would add are absent)
   if (!h->capture_stream && cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(saved);
     return cuda_fail(cudaGetLastError(), "capture stream");
@@ -1197,7 +1198,11 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
     h->ty = c.ty;
     h->tz = c.tz;
     if (segment_prepare(h) != MACLAB_OK) continue;
-    const float ms = graph_ms(8) / (8 * launch_depth(h));  // per time step
+    // per time step; graphs of 64 launches where 8 take under 0.5 ms, so that
+    // the launch of the graph itself does not decide between close shapes
+    float ms = graph_ms(8);
+    if (ms < 0.5f) ms = graph_ms(64) / 8.f;
+    ms /= 8 * launch_depth(h);
     if (ms < best) {
       best = ms;
       bkernel = c.kernel;
@@ -1256,8 +1261,9 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
     cudaMemcpyAsync(saved[i], m->buf[m->cur], state_bytes(m), cudaMemcpyDeviceToDevice, b->stream);
   }
   // rows per work item x time steps per launch, compared per time step on a
-  // captured graph of 8 launches (stepping runs in graphs, where the launch
-  // gaps that separate launches would add are absent)
+  // captured graph of 8 launches, or 64 where 8 take under 0.5 ms (stepping
+  // runs in graphs, where the launch gaps that separate launches would add
+  // are absent)
   if (!b->capture_stream &&
       cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
     return cuda_fail(cudaGetLastError(), "capture stream");
@@ -1287,7 +1293,9 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
   for (int depth = 1; depth <= max_depth; ++depth)
     for (int rows : candidates) {
       if (batch_build_items(b, rows, depth) != MACLAB_OK) continue;
-      const float ms = graph_ms(8) / (8 * depth);
+      float ms = graph_ms(8);
+      if (ms < 0.5f) ms = graph_ms(64) / 8.f;  // short steps: a longer graph
+      ms /= 8 * depth;
       if (ms < best) {
         best = ms;
         best_rows = rows;
