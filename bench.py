@@ -290,9 +290,9 @@ def run_ours(args, rank, world, local_rank):
     }
 
     if not args.no_extras and d == 3:  # the 2D cavity line is a diagnostic run without the extra legs
+        line["suite"] = suite_leg(M, stream)
         line["e2e"] = e2e_leg(M, case, prec, args, stream)
         line["adjoint_forward"] = adjoint_leg(M, case, prec, args, stream)
-        line["suite"] = suite_leg(M, stream)
         if args.precision != "f64":
             line["fp64"] = fp64_leg(M, case, args, stream, flush)
         mlups, steps, secs = oracle_rate(args.side, args.re)

@@ -161,6 +161,9 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel);
  * on is 0 or 1. */
 maclab_status maclab_set_launch_overlap(maclab_handle h, int32_t on);
 
+/* *on receives the handle's launch-overlap setting (1 or 0). */
+maclab_status maclab_get_launch_overlap(maclab_handle h, int32_t *on);
+
 /* Tile shape of the kernel in use.  Tiled and folded kernels: ty rows of y per
  * block (3D only) and tz planes of the slowest axis per block.  Segment kernel:
  * ty time steps per launch (1 or 2; 2 needs FP32 or FP64 storage and nx >= 8,
@@ -239,16 +242,25 @@ maclab_status maclab_batch_set_launch_overlap(maclab_batch b, int32_t on);
 maclab_status maclab_batch_info(maclab_batch b, int64_t out[7]);
 
 /* ---------------------------------------------------------------- tuning
- * Time the candidate shapes of the tiled and folded kernels (rows per tile,
- * planes per block) on this handle's domain and keep the fastest kernel and
- * shape; the state is saved before and restored after (temporary device
- * buffers are allocated).
+ * Time the candidate shapes of the tiled, folded and segment kernels (rows
+ * per tile, planes per block; rows per work item and steps per launch) on
+ * this handle's domain and keep the fastest kernel and shape, then time that
+ * shape with and without launch overlap (maclab_set_launch_overlap) and turn
+ * the overlap off only if plain launches are faster by more than 0.5 %; the
+ * state is saved before and restored after (temporary device buffers are
+ * allocated).
  * Results are cached per (lattice, precision, dims, periodicity, wall mode,
- * device) for the process.  out (may be NULL) receives the chosen ty, tz. */
+ * device model) for the process.  If the environment variable
+ * MACLAB_TUNE_CACHE names a file, a shape not yet tuned in this process is
+ * looked up there first (lines "<key> <kernel> <ty> <tz> [<overlap>]", the
+ * last line for a key wins) and each newly tuned one is appended to it; an
+ * unreadable file or malformed lines are ignored.  out (may be NULL) receives
+ * the chosen ty, tz. */
 maclab_status maclab_tune(maclab_handle h, int32_t out[2]);
 
 /* The same for a batch: chooses the rows per work item and the time steps per
- * launch (1 or 2, compared per step); *rows receives the rows. */
+ * launch (1 or 2, compared per step), then the launch overlap as above;
+ * *rows receives the rows. */
 maclab_status maclab_batch_tune(maclab_batch b, int32_t *rows);
 
 /* ---------------------------------------------------------------- adjoint

@@ -6,7 +6,10 @@
 
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include <map>
 #include <mutex>
@@ -16,6 +19,17 @@
 
 #include "common.cuh"
 #include "lattice.cuh"
+
+namespace {
+
+// Scoped NVTX range (shows the C-ABI calls on a profiler's timeline; no cost
+// without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+}  // namespace
 
 using namespace maclab;
 
@@ -329,6 +343,7 @@ maclab_status maclab_state_bytes(maclab_handle h, size_t* bytes) {
 
 maclab_status maclab_set_state(maclab_handle h, const void* rho, const void* u, int32_t where,
                                int32_t dtype) {
+  NvtxRange nvtx_range("maclab_set_state");
   if (!h || !rho || !u) return fail(MACLAB_ERR_INVALID, "NULL argument");
   if (dtype != MACLAB_DTYPE_F64 && dtype != MACLAB_DTYPE_F32)
     return fail(MACLAB_ERR_INVALID, "dtype must be F64 or F32");
@@ -360,6 +375,7 @@ maclab_status maclab_set_state(maclab_handle h, const void* rho, const void* u, 
 }
 
 maclab_status maclab_get_state(maclab_handle h, void* rho, void* u, int32_t where, int32_t dtype) {
+  NvtxRange nvtx_range("maclab_get_state");
   if (!h || !rho || !u) return fail(MACLAB_ERR_INVALID, "NULL argument");
   if (dtype != MACLAB_DTYPE_F64 && dtype != MACLAB_DTYPE_F32)
     return fail(MACLAB_ERR_INVALID, "dtype must be F64 or F32");
@@ -520,6 +536,7 @@ static maclab_status build_graph(maclab_ctx* h, int c) {
 }
 
 maclab_status maclab_step(maclab_handle h, int64_t n) {
+  NvtxRange nvtx_range("maclab_step");
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (n < 0) return fail(MACLAB_ERR_INVALID, "n must be >= 0");
   DeviceGuard dg(h->device);
@@ -598,6 +615,7 @@ maclab_status maclab_adjoint_bytes(maclab_handle h, size_t* bytes) {
 
 maclab_status maclab_adjoint_step(maclab_handle h, const void* state_n, const void* state_np1,
                                   const void* lam_np1, void* lam_n, double* grad_force) {
+  NvtxRange nvtx_range("maclab_adjoint_step");
   if (!h || !state_n || !state_np1 || !lam_np1 || !lam_n) return fail(MACLAB_ERR_INVALID, "NULL argument");
   if (lam_n == lam_np1) return fail(MACLAB_ERR_INVALID, "lam_n must not alias lam_np1");
   DeviceGuard dg(h->device);
@@ -675,6 +693,7 @@ maclab_status maclab_adjoint_finish(maclab_handle h, const void* lam_0, const vo
 }
 
 maclab_status maclab_diagnostics(maclab_handle h, double out[8]) {
+  NvtxRange nvtx_range("maclab_diagnostics");
   if (!h || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
   DeviceGuard dg(h->device);
   CUDA_TRY(launch_diagnostics(h->g, h->precision, h->buf[h->cur],
@@ -721,6 +740,12 @@ maclab_status maclab_set_launch_overlap(maclab_handle h, int32_t on) {
   if (on != 0 && on != 1) return fail(MACLAB_ERR_INVALID, "on must be 0 or 1");
   drop_graphs(h);
   h->overlap = on;
+  return MACLAB_OK;
+}
+
+maclab_status maclab_get_launch_overlap(maclab_handle h, int32_t* on) {
+  if (!h || !on) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  *on = h->overlap;
   return MACLAB_OK;
 }
 
@@ -977,6 +1002,7 @@ maclab_status maclab_batch_member(maclab_batch b, int32_t i, maclab_handle* out)
 }
 
 maclab_status maclab_batch_step(maclab_batch b, int64_t n) {
+  NvtxRange nvtx_range("maclab_batch_step");
   if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
   if (n < 0) return fail(MACLAB_ERR_INVALID, "n must be >= 0");
   for (maclab_ctx* m : b->members)
@@ -1070,6 +1096,7 @@ namespace {
 std::mutex g_tune_mutex;
 struct TuneChoice {
   int kernel, ty, tz;
+  int overlap = 1;  // programmatic dependent launch on (1) or off (0)
 };
 std::map<std::string, TuneChoice> g_tune_cache;
 
@@ -1081,14 +1108,72 @@ bool shape_supported(const maclab_ctx* h, int kernel, int ty, int tz) {
                                         : tiled_supported(h->g, h->precision, ty, tz);
 }
 
-std::string tune_key(const maclab_ctx* h) {
-  char buf[160];
-  snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%u/%d/%d", h->g.lattice, h->precision, h->g.nx, h->g.ny,
-           h->g.nz, h->g.periodic, h->g.wall_mode, h->device);
-  return buf;
+// Device model as a key part: its name (spaces as '_') and SM count.
+std::string device_tag(int device) {
+  static std::mutex m;
+  static std::map<int, std::string> tags;
+  std::lock_guard<std::mutex> lock(m);
+  auto it = tags.find(device);
+  if (it != tags.end()) return it->second;
+  cudaDeviceProp prop;
+  std::string tag = "unknown";
+  if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) {
+    tag = prop.name;
+    for (char& c : tag)
+      if (c == ' ' || c == '\t') c = '_';
+    tag += "/" + std::to_string(prop.multiProcessorCount);
+  } else {
+    cudaGetLastError();
+  }
+  tags[device] = tag;
+  return tag;
 }
 
-// Median-free simple timing: events around `k` launches of fn after 2 warm-up calls.
+std::string tune_key(const maclab_ctx* h) {
+  char buf[160];
+  snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%u/%d/", h->g.lattice, h->precision, h->g.nx, h->g.ny,
+           h->g.nz, h->g.periodic, h->g.wall_mode);
+  return buf + device_tag(h->device);
+}
+
+// Tuning results kept across processes: MACLAB_TUNE_CACHE names a text file
+// of lines "<key> <kernel> <ty> <tz> [<overlap>]".  A shape not tuned in this
+// process is looked up there first; a newly tuned one is appended.  Malformed
+// lines and an unreadable file are ignored.
+const char* tune_cache_path() {
+  const char* p = getenv("MACLAB_TUNE_CACHE");
+  return p && *p ? p : nullptr;
+}
+
+bool tune_cache_find(const std::string& key, TuneChoice* out) {
+  const char* path = tune_cache_path();
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[512], k[400];
+  int kern = 0, ty = 0, tz = 0, ov = 1;
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {
+    ov = 1;
+    const int got = sscanf(line, "%399s %d %d %d %d", k, &kern, &ty, &tz, &ov);
+    if (got >= 4 && key == k && (ov == 0 || ov == 1)) {
+      *out = TuneChoice{kern, ty, tz, ov};  // the last line for a key wins
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_cache_append(const std::string& key, const TuneChoice& c) {
+  const char* path = tune_cache_path();
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d %d\n", key.c_str(), c.kernel, c.ty, c.tz, c.overlap);
+  fclose(f);
+}
+
 template <typename Fn>
 // Milliseconds per call of fn: the best of three runs of k calls, after three
 // warm-up calls.
@@ -1117,18 +1202,22 @@ float time_ms(cudaStream_t st, int k, Fn fn) {
 extern "C" {
 
 maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
+  NvtxRange nvtx_range("maclab_tune");
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   DeviceGuard dg(h->device);
   const std::string key = tune_key(h);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
+    TuneChoice stored;
+    if (it == g_tune_cache.end() && tune_cache_find(key, &stored)) it = g_tune_cache.emplace(key, stored).first;
     if (it != g_tune_cache.end()) {
       if (shape_supported(h, it->second.kernel, it->second.ty, it->second.tz)) {
         drop_graphs(h);
         h->kernel = it->second.kernel;
         h->ty = it->second.ty;
         h->tz = it->second.tz;
+        h->overlap = it->second.overlap;
       }
       if (out) { out[0] = h->ty; out[1] = h->tz; }
       return MACLAB_OK;
@@ -1210,6 +1299,25 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
       btz = c.tz;
     }
   }
+  // launch overlap for the chosen shape: kept on unless plain launches are
+  // faster by more than 0.5 %
+  const int overlap0 = h->overlap;
+  int bover = overlap0;
+  if (best < 1e29f) {
+    h->kernel = bkernel;
+    h->ty = bty;
+    h->tz = btz;
+    if (segment_prepare(h) == MACLAB_OK) {
+      float t[2];
+      for (int ov = 0; ov < 2; ++ov) {
+        h->overlap = ov;
+        t[ov] = graph_ms(8);
+        if (t[ov] < 0.5f) t[ov] = graph_ms(64) / 8.f;
+      }
+      bover = t[0] < 0.995f * t[1] ? 0 : 1;
+    }
+  }
+  h->overlap = bover;
   cudaError_t e = cudaGetLastError();
   // restore
   h->cur = 0;
@@ -1224,20 +1332,24 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
     h->kernel = kernel0;
     h->ty = ty0;
     h->tz = tz0;
+    h->overlap = overlap0;
     return cuda_fail(e, "tuning launch");
   }
+  drop_graphs(h);
   h->kernel = bkernel;
   h->ty = bty;
   h->tz = btz;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = TuneChoice{bkernel, bty, btz};
+    g_tune_cache[key] = TuneChoice{bkernel, bty, btz, h->overlap};
+    tune_cache_append(key, TuneChoice{bkernel, bty, btz, h->overlap});
   }
   if (out) { out[0] = bty; out[1] = btz; }
   return MACLAB_OK;
 }
 
 maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
+  NvtxRange nvtx_range("maclab_batch_tune");
   if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
   DeviceGuard dg(b->device);
   if (!b->one_launch) {
@@ -1302,6 +1414,19 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
         best_depth = depth;
       }
     }
+  // launch overlap for the chosen work list: kept on unless plain launches
+  // are faster by more than 0.5 %
+  if (best < 1e29f && batch_build_items(b, best_rows, best_depth) == MACLAB_OK) {
+    float t[2];
+    for (int ov = 0; ov < 2; ++ov) {
+      b->overlap = ov;
+      t[ov] = graph_ms(8);
+      if (t[ov] < 0.5f) t[ov] = graph_ms(64) / 8.f;
+    }
+    const int bover = t[0] < 0.995f * t[1] ? 0 : 1;
+    b->overlap = bover;
+    for (maclab_ctx* m : b->members) m->overlap = bover;
+  }
   cudaError_t e = cudaGetLastError();
   b->cur = 0;
   for (size_t i = 0; i < b->members.size(); ++i) {

@@ -71,6 +71,7 @@ SIGNATURES = {
     "maclab_set_kernel": (_S, [_H, ctypes.c_int32]),
     "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "maclab_set_launch_overlap": (_S, [_H, ctypes.c_int32]),
+    "maclab_get_launch_overlap": (_S, [_H, ctypes.POINTER(ctypes.c_int32)]),
     "maclab_set_graph": (_S, [_H, ctypes.c_int32]),
     "maclab_diagnostics": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
     "maclab_batch_create": (_S, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_H)]),
@@ -491,6 +492,11 @@ class Solver:
     def set_launch_overlap(self, on):
         """Programmatic dependent launch of the step kernels (default on)."""
         maclab_set_launch_overlap(self.handle, int(on))
+
+    def launch_overlap(self):
+        v = ctypes.c_int32()
+        _check(lib().maclab_get_launch_overlap(self.handle, ctypes.byref(v)), "maclab_get_launch_overlap")
+        return v.value
 
     def kernel_info(self):
         return maclab_kernel_info(self.handle)
