@@ -144,6 +144,8 @@ FOLD_CASES = [
     ((64, 24, 13), 0b110, "mixed", 8),
     ((512, 8, 4), 0b000, "box", 0),
     ((256, 16, 5), 0b101, "mixed", 8),
+    ((4, 8, 6), 0b000, "box", 0),       # one quad per row: both x-walls in one lane
+    ((8, 16, 7), 0b010, "box", 0),      # two lanes, one x-wall each
 ]
 
 
@@ -232,6 +234,8 @@ SEG_CASES = [
     ((4, 9), 0b11, "none", 16),
     ((256, 70), 0b10, "box", 3),
     ((248, 33), 0b11, "mixed", 0),
+    ((4, 9), 0b00, "box", 2),           # one quad per row: both x-walls in one lane
+    ((8, 12), 0b10, "box", 3),          # two lanes, one x-wall each
 ]
 
 
@@ -261,10 +265,13 @@ def test_segment_kernel(dims, periodic, walls, rows, precision):
 
 @pytest.mark.parametrize("precision", [M.F64, M.F32])
 @pytest.mark.parametrize("steps", [1, 2, 9, 40, 67])
-def test_segment_two_steps_per_launch(precision, steps):
+@pytest.mark.parametrize("dims,periodic,walls", [((136, 45), 0b01, "mixed"), ((136, 45), 0b00, "box"),
+                                                 ((8, 12), 0b10, "box")])
+def test_segment_two_steps_per_launch(precision, steps, dims, periodic, walls):
     """ty = 2: two updates per launch on one domain, runs of n steps ending in a
     one-step launch; the same bits and the same residual as the tiled kernel."""
-    case = inputs.random_case(D2, (136, 45), 0b01, seed=48, u_amp=0.05, walls="mixed", force=(1e-4, 0.0))
+    case = inputs.random_case(D2, dims, periodic, seed=48, u_amp=0.05, walls=walls,
+                              force=(1e-4, 0.0))
     s = M.Solver.from_case(case, precision)
     s.set_kernel(M.KERNEL_SEGMENT)
     s.set_tile(2, 4)
