@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--kernel", default="auto", choices=["auto", "reference", "tiled", "folded", "segment"])
     p.add_argument("--ty", type=int, default=0, help="tiled kernel: rows per tile (0 = default)")
     p.add_argument("--tz", type=int, default=0, help="tiled kernel: planes per block (0 = default)")
-    p.add_argument("--leg", default="main", choices=["main", "adjoint", "batch"],
+    p.add_argument("--leg", default="main", choices=["main", "adjoint", "batch", "lbm"],
                    help="adjoint / batch: run only that leg and print its JSON (for profiling)")
     return p.parse_args()
 
@@ -505,8 +505,9 @@ def dist_max(x, world):
 
 
 def run_leg(args):
-    """One leg alone, on one GPU: the reverse step on the configured cavity, or
-    the 64 batched cavities; prints the leg's JSON."""
+    """One leg alone, on one GPU: the reverse step on the configured cavity, the
+    64 batched cavities, or the SRT-BGK comparator on the periodic 1024^2
+    Taylor-Green field; prints the leg's JSON."""
     import torch
     from paper_1901_02716_gb300 import _build
     from paper_1901_02716_gb300 import maclab as M
@@ -516,6 +517,17 @@ def run_leg(args):
     stream = torch.cuda.current_stream()
     if args.leg == "adjoint":
         out = adjoint_leg(M, cavity_case(args.side, args.re), M.PRECISION_NAMES[args.precision], args, stream)
+    elif args.leg == "lbm":
+        from paper_1901_02716_gb300 import inputs
+        tg = inputs.tgv2d(1024, 0.02)
+        lb = M.Lbm(1024, 1024, 0.8, M.F32, stream=ctypes_stream(stream))
+        lb.set_state(tg.rho, tg.u)
+        ms = _timed_steps(torch, stream, lb.step, 640)
+        li = lb.info()
+        lb.close()
+        mlups = li["nodes"] * 640 / (ms * 1e-3) / 1e6
+        out = {"mlups": mlups, "bytes_per_update": li["bytes_per_update"],
+               "hbm_frac_algorithmic": mlups * 1e6 * li["bytes_per_update"] / (peaks()[0] * 1e9)}
     else:
         from paper_1901_02716_gb300 import inputs
         sides, res, lids = inputs.batch_cavity_sides(64, seed=4)
