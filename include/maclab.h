@@ -108,11 +108,17 @@ maclab_status maclab_params(maclab_handle h, double out[8]);
 
 /* Set the state from physical fields: rho (N values) and u (d * N values) of
  * the given dtype, in host or device memory.  Wall nodes are overwritten with
- * their wall id's values.  Resets the step counter. */
+ * their wall id's values.  Resets the step counter.  Host buffers that are
+ * page-locked and mapped for the handle's device (cudaHostAlloc,
+ * cudaHostRegister) are read by the conversion kernel directly; other host
+ * memory goes through a device staging buffer.  Either way the call returns
+ * only after the host buffers have been read. */
 maclab_status maclab_set_state(maclab_handle h, const void *rho, const void *u,
                                int32_t where, int32_t dtype);
 
-/* Read the current physical state into rho (N) and u (d * N).  Synchronises. */
+/* Read the current physical state into rho (N) and u (d * N).  Synchronises.
+ * Page-locked host buffers mapped for the device are written by the
+ * conversion kernel directly, other host memory through a staging buffer. */
 maclab_status maclab_get_state(maclab_handle h, void *rho, void *u, int32_t where,
                                int32_t dtype);
 

@@ -341,6 +341,20 @@ maclab_status maclab_state_bytes(maclab_handle h, size_t* bytes) {
   return MACLAB_OK;
 }
 
+// Device address of page-locked host memory mapped for this device (pinned
+// with cudaHostAlloc or cudaHostRegister), else nullptr: the conversion
+// kernels then read or write the caller's buffer directly over the host link
+// instead of going through the staging buffer and a copy.
+static void* pinned_device_ptr(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != device) return nullptr;
+  return a.devicePointer;
+}
+
 maclab_status maclab_set_state(maclab_handle h, const void* rho, const void* u, int32_t where,
                                int32_t dtype) {
   NvtxRange nvtx_range("maclab_set_state");
@@ -353,7 +367,12 @@ maclab_status maclab_set_state(maclab_handle h, const void* rho, const void* u, 
   const size_t nb = (size_t)h->g.n * es;
   const void* r = rho;
   const void* v = u;
-  if (where == MACLAB_HOST) {
+  const void* pr = where == MACLAB_HOST ? pinned_device_ptr(rho, h->device) : nullptr;
+  const void* pu = pr ? pinned_device_ptr(u, h->device) : nullptr;
+  if (pr && pu) {
+    r = pr;
+    v = pu;
+  } else if (where == MACLAB_HOST) {
     maclab_status s = ensure_staging(h, nb * (h->g.d + 1));
     if (s != MACLAB_OK) return s;
     char* st = (char*)h->d_staging;
@@ -383,9 +402,11 @@ maclab_status maclab_get_state(maclab_handle h, void* rho, void* u, int32_t wher
   DeviceGuard dg(h->device);
   const size_t es = dtype == MACLAB_DTYPE_F64 ? 8 : 4;
   const size_t nb = (size_t)h->g.n * es;
-  if (where == MACLAB_DEVICE) {
-    CUDA_TRY(launch_get_physical(h->g, h->precision, h->buf[h->cur], rho, u, dtype, h->rho0, h->e,
-                                 h->stream),
+  void* pr = where == MACLAB_HOST ? pinned_device_ptr(rho, h->device) : nullptr;
+  void* pu = pr ? pinned_device_ptr(u, h->device) : nullptr;
+  if (where == MACLAB_DEVICE || (pr && pu)) {
+    CUDA_TRY(launch_get_physical(h->g, h->precision, h->buf[h->cur], pr ? pr : rho, pu ? pu : u, dtype,
+                                 h->rho0, h->e, h->stream),
              "get_state kernel");
   } else {
     maclab_status s = ensure_staging(h, nb * (h->g.d + 1));
