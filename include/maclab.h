@@ -45,7 +45,7 @@ typedef int32_t maclab_status;
 #define MACLAB_ERR_NONFINITE (-3)  /* NaN or Inf found in the state */
 #define MACLAB_ERR_TIMEOUT (-4)    /* a bounded device-side wait ran out */
 #define MACLAB_ERR_OOM (-5)        /* device or host allocation failed */
-#define MACLAB_ERR_UNSUPPORTED (-6)/* valid request that this build does not serve */
+#define MACLAB_ERR_UNSUPPORTED (-6)/* valid request that this library does not serve */
 
 typedef enum { MACLAB_D2Q9 = 0, MACLAB_D3Q19 = 1 } maclab_lattice;
 

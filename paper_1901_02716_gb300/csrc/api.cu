@@ -136,7 +136,7 @@ const char* maclab_status_string(maclab_status s) {
     case MACLAB_ERR_NONFINITE: return "MACLAB_ERR_NONFINITE: non-finite value in the state";
     case MACLAB_ERR_TIMEOUT: return "MACLAB_ERR_TIMEOUT: bounded device wait expired";
     case MACLAB_ERR_OOM: return "MACLAB_ERR_OOM: allocation failed";
-    case MACLAB_ERR_UNSUPPORTED: return "MACLAB_ERR_UNSUPPORTED: not supported by this build";
+    case MACLAB_ERR_UNSUPPORTED: return "MACLAB_ERR_UNSUPPORTED: not supported by this library";
   }
   return "unknown maclab_status";
 }
