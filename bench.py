@@ -290,6 +290,14 @@ def run_ours(args, rank, world, local_rank):
     }
 
     if not args.no_extras and d == 3:  # the 2D cavity line is a diagnostic run without the extra legs
+        # the arithmetic ceiling beside the memory roofline: algorithmic flops
+        # per update (D3Q19 ~200, D2Q9 ~80) against the measured paired-FP32 rate
+        fpl = 200 if d == 3 else 80
+        fp_peak = M.maclab_measure_fp32_peak()
+        fp_ach = value * 1e6 * fpl / 1e12
+        line["fp32"] = {"flops_per_lup": fpl, "achieved_tflops": fp_ach, "peak_tflops": fp_peak,
+                        "frac": fp_ach / fp_peak if fp_peak > 0 else None,
+                        "peak_kind": "measured (paired FP32 FMA chains, maclab_measure_fp32_peak)"}
         line["suite"] = suite_leg(M, stream)
         line["e2e"] = e2e_leg(M, case, prec, args, stream)
         line["adjoint_forward"] = adjoint_leg(M, case, prec, args, stream)

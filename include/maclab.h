@@ -358,6 +358,14 @@ maclab_status maclab_diagnostics_noalloc(int32_t lattice, int32_t precision, int
  * Errors: MACLAB_ERR_INVALID (arguments), MACLAB_ERR_OOM, MACLAB_ERR_CUDA. */
 maclab_status maclab_check_reciprocal(float lo, float hi, int32_t n, double *max_rel_err);
 
+/* Measure the current device's paired-FP32 FMA rate (the arithmetic the FP32
+ * kernels use: one instruction, two fused multiply-adds on a float2) in
+ * TFLOP/s, counting two operations per FMA: independent chains at full
+ * occupancy, the best of three timed launches after a warm-up.  The D3Q19
+ * step is checked against it beside the memory roofline.  Synchronous.
+ * Errors: MACLAB_ERR_INVALID, MACLAB_ERR_OOM, MACLAB_ERR_CUDA. */
+maclab_status maclab_measure_fp32_peak(double *tflops);
+
 /* Run the handle's stream to completion and report any CUDA error. */
 maclab_status maclab_sync(maclab_handle h);
 

@@ -164,6 +164,40 @@ maclab_status maclab_check_reciprocal(float lo, float hi, int32_t n, double* max
   return MACLAB_OK;
 }
 
+maclab_status maclab_measure_fp32_peak(double* tflops) {
+  if (!tflops) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return cuda_fail(cudaGetLastError(), "device query");
+  float2* sink = nullptr;
+  if (cudaMalloc(&sink, 256 * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MACLAB_ERR_OOM, "peak measurement allocation failed");
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  double flops = 0, best = 0;
+  cudaError_t e = cudaSuccess;
+  // 8 blocks of 256 threads per SM (full occupancy); warm-up, then the best of 3
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(a, nullptr);
+    e = launch_fp32_peak(8 * sms, 256, 1 << 14, sink, nullptr, &flops);
+    cudaEventRecord(b, nullptr);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && rep > 0 && ms > 0) best = fmax(best, flops / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "peak measurement");
+  *tflops = best;
+  return MACLAB_OK;
+}
+
 const char* maclab_last_error(void) { return g_last_error.c_str(); }
 
 maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {

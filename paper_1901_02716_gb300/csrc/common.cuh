@@ -185,6 +185,10 @@ cudaError_t launch_adjoint_step(const Geometry& g, int precision, const void* st
 // reciprocal over n points in [lo, hi], as double bits, into *d_worst.
 cudaError_t launch_check_reciprocal(float lo, float hi, int n, unsigned long long* d_worst,
                                     cudaStream_t st);
+// Defined in selfcheck.cu: one launch of the paired-FP32 FMA rate kernel;
+// *flops receives the floating-point operations it performs.
+cudaError_t launch_fp32_peak(int blocks, int threads, int iters, float2* sink, cudaStream_t st,
+                             double* flops);
 // Defined in adjoint_tiled.cu (domains with interleaved rows).
 bool tiled_adjoint_supported(const Geometry& g, int precision);
 cudaError_t launch_tiled_adjoint(const Geometry& g, int precision, const void* state_n,

@@ -97,6 +97,7 @@ SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_char_p)]),
     "maclab_status_string": (ctypes.c_char_p, [_S]),
     "maclab_version": (ctypes.c_char_p, []),
+    "maclab_measure_fp32_peak": (_S, [ctypes.POINTER(ctypes.c_double)]),
     "maclab_check_reciprocal": (_S, [ctypes.c_float, ctypes.c_float, ctypes.c_int32,
                                      ctypes.POINTER(ctypes.c_double)]),
     "maclab_lbm_create": (_S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -346,6 +347,13 @@ def maclab_check_reciprocal(lo, hi, n):
     out = ctypes.c_double()
     _check(lib().maclab_check_reciprocal(float(lo), float(hi), int(n), ctypes.byref(out)),
            "maclab_check_reciprocal")
+    return out.value
+
+
+def maclab_measure_fp32_peak():
+    """The device's paired-FP32 FMA rate, TFLOP/s (two operations per FMA)."""
+    out = ctypes.c_double()
+    _check(lib().maclab_measure_fp32_peak(ctypes.byref(out)), "maclab_measure_fp32_peak")
     return out.value
 
 

@@ -436,3 +436,10 @@ def test_pair_reciprocal_error_bound(lo, hi):
     relative) of 1/x over the ranges those arguments take, and beyond."""
     err = M.maclab_check_reciprocal(lo, hi, 1 << 20)
     assert 0.0 <= err <= 2.0 ** -23
+
+
+def test_fp32_peak_measurement():
+    """The device's paired-FP32 FMA rate: a GB300 (152 SMs x 128 lanes x 2 flops
+    at about 2 GHz) gives some tens of TFLOP/s."""
+    t = M.maclab_measure_fp32_peak()
+    assert 20.0 < t < 250.0
