@@ -283,6 +283,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "dram_gbs_measured": (traffic / (avg_launch_ms * 1e-3) / 1e9) if traffic else None,
                      "kernel": kernel_tag, "bytes_per_lup": bytes_per_lup,
                      "peak_kind": peak_kind, "avg_launch_us": avg_launch_ms * 1e3},
         "gpu_launches": int(launches_per_step * args.steps),
@@ -301,6 +302,9 @@ def run_ours(args, rank, world, local_rank):
         line["suite"] = suite_leg(M, stream)
         line["e2e"] = e2e_leg(M, case, prec, args, stream)
         line["adjoint_forward"] = adjoint_leg(M, case, prec, args, stream)
+        # the differentiable workload: periodic 96^3 Taylor-Green field with the seeded perturbation
+        from paper_1901_02716_gb300 import inputs
+        line["adjoint_forward_tgv96"] = adjoint_leg(M, inputs.tgv3d(96, 0.02, 1e-3, 5), prec, args, stream)
         if args.precision != "f64":
             line["fp64"] = fp64_leg(M, case, args, stream, flush)
         mlups, steps, secs = oracle_rate(args.side, args.re)
