@@ -419,3 +419,22 @@ def test_params_eq6():
     assert dt == pytest.approx(0.02 ** 2 / (6 * 0.001), rel=1e-14)
     # R_le = U dx / nu = 6 U / e: the lattice Mach number times six
     assert orc.lattice_reynolds(0.1, 0.02, 0.001) == pytest.approx(6 * 0.1 / e, rel=1e-14)
+
+
+def test_diagnostics_hand_computed():
+    """The FP64 diagnostics on a 2 x 2 field worked out by hand (values chosen
+    so every sum is exact in binary); the wall node, with large values, must
+    not count."""
+    rho = np.array([[1.0, 2.0], [0.5, 4.0]])                    # [y, x]
+    u = np.array([[[0.5, -0.25], [1.0, 3.0]],                   # u_x
+                  [[0.0, 0.5], [-0.5, 7.0]]])                   # u_y
+    fluid = np.array([[True, True], [True, False]])             # node (y=1, x=1) is a wall
+    d = orc.diagnostics(rho, u, u_prev=0.5 * u, fluid=fluid)
+    # mass 1 + 2 + 0.5; kinetic 1/2 (1*0.25 + 2*(0.0625 + 0.25) + 0.5*(1 + 0.25))
+    assert d["mass"] == 3.5
+    assert d["kinetic"] == 0.75
+    # momentum: x 0.5 - 0.5 + 0.5, y 0 + 1 - 0.25
+    assert d["momentum"] == [0.5, 0.75]
+    # u - u_prev = u / 2 on the fluid nodes
+    assert d["residual"] == pytest.approx(0.5, rel=1e-15)
+    assert orc.diagnostics(rho, u, u_prev=u, fluid=fluid)["residual"] == 0.0
