@@ -16,9 +16,12 @@ __device__ __forceinline__ double ld_user(const T* p, int64_t i) {
 }
 
 // User arrays are in logical order (x fastest); the state in storage order.
-__device__ __forceinline__ int64_t user_index(const Geometry& g, int64_t m) {
-  const int64_t row = m / g.nx;
-  return row * g.nx + log_x(g, (int)(m - row * g.nx));
+// The maps walk the user arrays in order (a warp touches one contiguous run of
+// each user array, which may be page-locked host memory read or written over
+// the host link) and place each node at its storage index.
+__device__ __forceinline__ int64_t storage_index(const Geometry& g, int64_t j) {
+  const int64_t row = j / g.nx;
+  return row * g.nx + mem_x(g, (int)(j - row * g.nx));
 }
 
 template <typename S, typename T>
@@ -26,15 +29,15 @@ __global__ void set_physical_k(Geometry g, int d, int64_t N, const T* __restrict
                                double inv_rho0, double inv_e, const uint8_t* __restrict__ node_type,
                                const double* __restrict__ wall_lat, int n_wall_ids,
                                S* __restrict__ state) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = storage_index(g, j);
     const int k = node_type ? (int)node_type[i] : 0;
     if (k > 0 && k <= n_wall_ids) {
       const double* w = wall_lat + 4 * (k - 1);
       state[i] = Store<S>::to(typename Store<S>::C(w[0]));
       for (int c = 0; c < d; ++c) state[(1 + c) * N + i] = Store<S>::to(typename Store<S>::C(w[1 + c]));
     } else {
-      const int64_t j = user_index(g, i);
       state[i] = Store<S>::to(typename Store<S>::C(ld_user(rho, j) * inv_rho0 - 1.0));
       for (int c = 0; c < d; ++c)
         state[(1 + c) * N + i] = Store<S>::to(typename Store<S>::C(ld_user(u, c * N + j) * inv_e));
@@ -60,9 +63,9 @@ __global__ void fill_walls_k(int d, int64_t N, const uint8_t* __restrict__ node_
 template <typename S, typename T>
 __global__ void get_physical_k(Geometry g, int d, int64_t N, const S* __restrict__ state, double rho0,
                                double e, T* __restrict__ rho, T* __restrict__ u) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = user_index(g, i);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = storage_index(g, j);
     rho[j] = (T)(rho0 * (1.0 + (double)Store<S>::from(state[i])));
     for (int c = 0; c < d; ++c) u[c * N + j] = (T)(e * (double)Store<S>::from(state[(1 + c) * N + i]));
   }
