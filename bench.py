@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--kernel", default="auto", choices=["auto", "reference", "tiled", "folded", "segment"])
     p.add_argument("--ty", type=int, default=0, help="tiled kernel: rows per tile (0 = default)")
     p.add_argument("--tz", type=int, default=0, help="tiled kernel: planes per block (0 = default)")
-    p.add_argument("--leg", default="main", choices=["main", "adjoint", "batch", "lbm"],
+    p.add_argument("--leg", default="main", choices=["main", "adjoint", "batch", "lbm", "diag"],
                    help="adjoint / batch: run only that leg and print its JSON (for profiling)")
     return p.parse_args()
 
@@ -305,6 +305,7 @@ def run_ours(args, rank, world, local_rank):
         # the differentiable workload: periodic 96^3 Taylor-Green field with the seeded perturbation
         from paper_1901_02716_gb300 import inputs
         line["adjoint_forward_tgv96"] = adjoint_leg(M, inputs.tgv3d(96, 0.02, 1e-3, 5), prec, args, stream)
+        line["diagnostics"] = diagnostics_leg(M, case, prec, stream)
         if args.precision != "f64":
             line["fp64"] = fp64_leg(M, case, args, stream, flush)
         mlups, steps, secs = oracle_rate(args.side, args.re)
@@ -383,6 +384,30 @@ def adjoint_leg(M, case, prec, args, stream):
     s.close()
     return {"forward_ms": t_fwd, "adjoint_ms": t_adj, "ratio": t_adj / t_fwd,
             "adjoint_launches_per_step": 1}
+
+
+def diagnostics_leg(M, case, prec, stream):
+    """Time of one FP64 diagnostics call (mass, kinetic energy, momentum,
+    residual: both state buffers read once) on the same workload, against the
+    memory roofline on those bytes."""
+    import torch
+    s = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
+    s.step(3)
+    for _ in range(3):
+        s.diagnostics()
+    best = None
+    for _ in range(10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.diagnostics()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b)
+        best = t if best is None else min(best, t)
+    nbytes = 2 * s.state_bytes()
+    s.close()
+    gbs = nbytes / (best * 1e-3) / 1e9
+    return {"ms": best, "bytes": nbytes, "gbs": gbs, "frac": gbs / peaks()[0]}
 
 
 def _timed_steps(torch, stream, step, n, reps=3):
@@ -517,9 +542,9 @@ def dist_max(x, world):
 
 
 def run_leg(args):
-    """One leg alone, on one GPU: the reverse step on the configured cavity, the
-    64 batched cavities, or the SRT-BGK comparator on the periodic 1024^2
-    Taylor-Green field; prints the leg's JSON."""
+    """One leg alone, on one GPU: the reverse step or the FP64 diagnostics on the
+    configured cavity, the 64 batched cavities, or the SRT-BGK comparator on
+    the periodic 1024^2 Taylor-Green field; prints the leg's JSON."""
     import torch
     from paper_1901_02716_gb300 import _build
     from paper_1901_02716_gb300 import maclab as M
@@ -529,6 +554,8 @@ def run_leg(args):
     stream = torch.cuda.current_stream()
     if args.leg == "adjoint":
         out = adjoint_leg(M, cavity_case(args.side, args.re), M.PRECISION_NAMES[args.precision], args, stream)
+    elif args.leg == "diag":
+        out = diagnostics_leg(M, cavity_case(args.side, args.re), M.PRECISION_NAMES[args.precision], stream)
     elif args.leg == "lbm":
         from paper_1901_02716_gb300 import inputs
         tg = inputs.tgv2d(1024, 0.02)

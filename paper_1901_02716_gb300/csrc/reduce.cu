@@ -1,7 +1,8 @@
 // reduce.cu -- FP64 diagnostics of the stored state.
 //
 // Sums over fluid nodes (walls excluded), accumulated in FP64 whatever the
-// storage type:
+// storage type (each node's products are formed in the storage's arithmetic
+// type, FP32 for FP32 and 16-bit storage, where FP64 arithmetic is slow):
 //   slot 0  sum drho                      (mass = rho0 (n_fluid + slot 0))
 //   slot 1  sum rho |u|^2                 (kinetic energy = rho0 e^2 slot 1 / 2)
 //   slot 2..4  sum rho u_i                (momentum = rho0 e slot)
@@ -27,45 +28,64 @@ template <typename S>
 __global__ void __launch_bounds__(256) diag_partial(Geometry g, const S* __restrict__ cur,
                                                     const S* __restrict__ prev,
                                                     double* __restrict__ partial) {
+  using C = typename Store<S>::C;
   double acc[kDiagSlots];
 #pragma unroll
   for (int k = 0; k < kDiagSlots; ++k) acc[k] = 0.0;
+  C umax2 = C(0);
   const int64_t N = g.n;
-  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < N;
-       m += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // storage position (mx, y, z) of m, advanced by the stride without dividing
+  int64_t q = m / g.nx;
+  int mx = (int)(m - q * g.nx), y = (int)(q % g.ny);
+  int64_t z = q / g.ny;
+  const int64_t sq = stride / g.nx;
+  const int sx = (int)(stride - sq * g.nx), sy = (int)(sq % g.ny);
+  const int64_t sz = sq / g.ny;
+  for (; m < N; m += stride) {
     bool wall = false;
     if (g.wall_mode == kWallMask) {
       wall = g.mask[m] != 0;
     } else if (g.wall_mode == kWallBox) {
-      const int x = log_x(g, (int)(m % g.nx));
-      const int y = (int)((m / g.nx) % g.ny);
-      const int z = (int)(m / ((int64_t)g.nx * g.ny));
+      const int x = log_x(g, mx);
       if (!(g.periodic & 1u)) wall |= (x == 0) | (x == g.nx - 1);
       if (!(g.periodic & 2u)) wall |= (y == 0) | (y == g.ny - 1);
       if (g.d == 3 && !(g.periodic & 4u)) wall |= (z == 0) | (z == g.nz - 1);
     }
+    mx += sx;
+    const int carry = mx >= g.nx ? 1 : 0;
+    mx -= carry * g.nx;
+    y += sy + carry;
+    if (y >= g.ny) {
+      y -= g.ny;
+      z += 1;
+    }
+    z += sz;
     if (wall) continue;
-    const double dr = (double)Store<S>::from(cur[m]);
-    const double rho = 1.0 + dr;
-    double uu = 0.0, du = 0.0;
+    // per-node products in the storage's arithmetic type, sums in FP64
+    const C dr = Store<S>::from(cur[m]);
+    const C rho = C(1) + dr;
+    C uu = C(0), du = C(0);
     bool finite = isfinite(dr);
-    acc[0] += dr;
+    acc[0] += (double)dr;
     for (int i = 0; i < g.d; ++i) {
-      const double u = (double)Store<S>::from(cur[(1 + i) * N + m]);
+      const C u = Store<S>::from(cur[(1 + i) * N + m]);
       finite = finite && isfinite(u);
-      uu += u * u;
-      acc[2 + i] += rho * u;
+      uu = fma(u, u, uu);
+      acc[2 + i] += (double)(rho * u);
       if (prev) {
-        const double d = u - (double)Store<S>::from(prev[(1 + i) * N + m]);
-        du += d * d;
+        const C d = u - Store<S>::from(prev[(1 + i) * N + m]);
+        du = fma(d, d, du);
       }
     }
-    acc[1] += rho * uu;
-    acc[5] += du;
-    acc[6] += uu;
-    acc[7] = fmax(acc[7], sqrt(uu));
+    acc[1] += (double)(rho * uu);
+    acc[5] += (double)du;
+    acc[6] += (double)uu;
+    umax2 = fmax(umax2, uu);  // max |u|^2 here, its root below (the root is monotonic)
     if (!finite) acc[8] += 1.0;
   }
+  acc[7] = sqrt((double)umax2);
   // block reduction: warp shuffles, then one value per warp through shared memory
   __shared__ double red[kDiagSlots][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
