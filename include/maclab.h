@@ -142,9 +142,10 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * rows); MACLAB_KERNEL_SEGMENT is the batched D2Q9 kernel run on one domain
  * (a warp per 30-quad row segment, x exchange by warp shuffles; with two
  * steps per launch the rows are staged four ahead in the warp's own shared
- * memory; nx % 4 == 0; the tile's tz is its rows per work item, default 4,
- * and ty = 2 asks for two time steps per launch, see maclab_batch_set_depth),
- * the default for D2Q9 grids of at least 65,536 quads.  All compute Eqs.
+ * memory; nx % 4 == 0; the tile's tz is its rows per work item, default 2
+ * up to 65,536 quads and 4 above, and ty the time steps per launch, 1 or 2,
+ * default 2 below 200,000 quads where two steps are supported, see
+ * maclab_batch_set_depth), the default for D2Q9 grids with nx % 4 == 0.  All compute Eqs.
  * (4)-(5) with the same terms per node (the folded kernel sums them in
  * another order; the segment and tiled kernels give identical bits). */
 #define MACLAB_KERNEL_AUTO 0
@@ -175,7 +176,7 @@ maclab_status maclab_get_launch_overlap(maclab_handle h, int32_t *on);
  * ty time steps per launch (1 or 2; 2 needs FP32 or FP64 storage and nx >= 8,
  * and a run of n steps then ends with a one-step launch so that the previous
  * state is step n - 1) and tz rows per work item.  0 keeps the library's
- * default.  MACLAB_ERR_UNSUPPORTED if no built instance has that shape for this
+ * default (for the segment kernel it depends on the grid's size).  MACLAB_ERR_UNSUPPORTED if no built instance has that shape for this
  * domain (the previous shape is kept). */
 maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz);
 

@@ -526,7 +526,7 @@ static int device_sms() {
 // uploads.
 static maclab_status segment_prepare(maclab_ctx* h) {
   if (h->kernel != MACLAB_KERNEL_SEGMENT) return MACLAB_OK;
-  const int rows = h->tz > 0 ? h->tz : 4;
+  const int rows = segment_rows(h->g, h->tz);
   const int depth = segment_depth(h->g, h->precision, h->ty);
   if (h->d_seg_inst && h->d_seg_items && h->seg_rows == rows && h->seg_depth == depth) return MACLAB_OK;
   if (!h->d_seg_inst) {
@@ -1015,6 +1015,10 @@ maclab_status maclab_batch_create(const maclab_config* cfgs, int32_t count, macl
   DeviceGuard dg(b->device);
   b->one_launch = b->lattice == MACLAB_D2Q9;
   for (maclab_ctx* m : b->members) b->one_launch = b->one_launch && m->g.ilv == 1;
+  if (!b->one_launch)  // one launch per member and step: the segment kernel's work list is not built
+    for (maclab_ctx* m : b->members)
+      if (m->kernel == MACLAB_KERNEL_SEGMENT)
+        m->kernel = tiled_supported(m->g, m->precision, 0, 0) ? MACLAB_KERNEL_TILED : MACLAB_KERNEL_REFERENCE;
   if (b->one_launch) {
     std::vector<unsigned char> insts(batch_inst_bytes() * b->members.size());
     for (size_t i = 0; i < b->members.size(); ++i) {
@@ -1334,7 +1338,7 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
   for (int kernel : {MACLAB_KERNEL_TILED, MACLAB_KERNEL_FOLDED})
     for (int a = 0; a < n_ty; ++a)
       for (int tz : tzs) cands.push_back(Cand{kernel, h->g.d == 3 ? tys3[a] : 0, tz});
-  for (int ty : {0, 2})
+  for (int ty : {1, 2})
     for (int tz : {2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_SEGMENT, ty, tz});
   for (const Cand& c : cands) {
     if (!shape_supported(h, c.kernel, c.ty, c.tz)) continue;

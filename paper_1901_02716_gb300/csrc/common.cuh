@@ -152,6 +152,7 @@ struct KernelInfo {
 };
 bool step_kernel_supported(const Geometry& g, int precision, int kernel);
 int segment_depth(const Geometry& g, int precision, int ty);
+int segment_rows(const Geometry& g, int tz);
 int pick_step_kernel(const Geometry& g, int precision);
 KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, int ty, int tz);
 // Queue one launch group of `kernel` (advances steps_per_launch steps).

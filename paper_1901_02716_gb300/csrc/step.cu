@@ -120,8 +120,18 @@ static cudaError_t launch_naive_lat(const StepLaunch& s, cudaStream_t stream) {
 
 // Time steps per launch of the segment kernel for the tile setting ty (2 asks
 // for two steps per launch: FP32 or FP64 storage and nx >= 8; otherwise 1).
+// Segment kernel defaults (measured on a GB300, FP32 cavities of 64^2 to
+// 1024^2): two steps per launch below 200,000 quads (small grids are bound by
+// the launches), and 2 rows per work item up to 65,536 quads, 4 above.
 int segment_depth(const Geometry& g, int precision, int ty) {
-  return ty == 2 && (precision == MACLAB_F32 || precision == MACLAB_F64) && g.nx >= 8 ? 2 : 1;
+  const bool two_ok = (precision == MACLAB_F32 || precision == MACLAB_F64) && g.nx >= 8;
+  if (ty == 0) return two_ok && (int64_t)(g.nx / 4) * g.ny < 200000 ? 2 : 1;
+  return ty == 2 && two_ok ? 2 : 1;
+}
+
+int segment_rows(const Geometry& g, int tz) {
+  if (tz > 0) return tz;
+  return (int64_t)(g.nx / 4) * g.ny <= 65536 ? 2 : 4;
 }
 
 bool step_kernel_supported(const Geometry& g, int precision, int kernel) {
@@ -133,13 +143,12 @@ bool step_kernel_supported(const Geometry& g, int precision, int kernel) {
 }
 
 // The folded kernel where it is built (D3Q19 FP32, ny a multiple of its tile
-// rows); for D2Q9 grids of at least 65,536 quads the segment kernel (faster
-// there; on smaller grids its row chunks leave too few warps); else the tiled
-// one, else the reference kernel.
+// rows); for D2Q9 grids with nx % 4 == 0 the segment kernel (with its size
+// defaults it is faster than the tiled one from 64^2 to 1024^2); else the
+// tiled one, else the reference kernel.
 int pick_step_kernel(const Geometry& g, int precision) {
   if (step_kernel_supported(g, precision, MACLAB_KERNEL_FOLDED)) return MACLAB_KERNEL_FOLDED;
-  if (step_kernel_supported(g, precision, MACLAB_KERNEL_SEGMENT) && (int64_t)(g.nx / 4) * g.ny >= 65536)
-    return MACLAB_KERNEL_SEGMENT;
+  if (step_kernel_supported(g, precision, MACLAB_KERNEL_SEGMENT)) return MACLAB_KERNEL_SEGMENT;
   return step_kernel_supported(g, precision, MACLAB_KERNEL_TILED) ? MACLAB_KERNEL_TILED
                                                                  : MACLAB_KERNEL_REFERENCE;
 }

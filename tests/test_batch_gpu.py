@@ -194,3 +194,22 @@ def test_two_steps_per_launch_refused(kind):
     assert b.info()["steps_per_launch"] == 1
     b.step(3)
     b.close()
+
+
+def test_batch_2d_fallback_with_a_non_interleaved_member():
+    """A D2Q9 batch with a member whose nx is not a multiple of 4 steps one
+    launch per member; the other members then use the tiled kernel (their
+    default segment kernel needs the single launch's work list) and still equal
+    standalone runs bit for bit."""
+    cases = [inputs.random_case(D2, (64, 40), 0b00, seed=86, walls="box"),
+             inputs.random_case(D2, (30, 20), 0b11, seed=87),
+             inputs.random_case(D2, (512, 300), 0b01, seed=88, walls="mixed")]
+    b = M.Batch.from_cases(cases, M.F32)
+    assert b.info()["launches_per_step"] == 3
+    b.step(9)
+    for m, case in zip(b.members, cases):
+        s = M.Solver.from_case(case, M.F32)
+        s.step(9)
+        assert np.array_equal(s.get_lattice_state(), m.get_lattice_state())
+        s.close()
+    b.close()
