@@ -70,3 +70,32 @@ def test_dist_max_over_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert got == [(0, 15.0), (1, 15.0)]
+
+
+def test_traffic_lookup_follows_the_source_hash(tmp_path, monkeypatch):
+    """bench.py reports an ncu traffic figure only while the profiled sources
+    are unchanged (same hash), and only for the profiled kernel."""
+    import bench
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "k.md").write_text(
+        "# title\n\nkernel_tag: step_fold<D3Q19,f32>\nsource_sha256: 0123456789abcdef\n"
+        "traffic_bytes_per_launch: 12345678\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("step_fold<D3Q19,f32>", "0123456789abcdef") == 12345678.0
+    assert bench.traffic_from_profiles("step_fold<D3Q19,f32>", "fedcba9876543210") is None
+    assert bench.traffic_from_profiles("segment<D2Q9,f32>", "0123456789abcdef") is None
+
+
+def test_committed_profiles_are_well_formed():
+    """Every ncu summary names the command that made it; those that carry a
+    traffic figure give the kernel, a 16-digit source hash and a number."""
+    import re
+    pdir = os.path.join(ROOT, "profiles")
+    names = [n for n in os.listdir(pdir) if n.endswith(".md")]
+    assert names
+    for n in names:
+        txt = open(os.path.join(pdir, n)).read()
+        assert "ncu " in txt and "--clock-control none" in txt, n
+        if re.search(r"^kernel_tag:", txt, re.M):
+            assert re.search(r"^source_sha256:\s*[0-9a-f]{16}\s*$", txt, re.M), n
+            assert re.search(r"^traffic_bytes_per_launch:\s*[0-9]+\s*$", txt, re.M), n
