@@ -164,11 +164,14 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel);
  * kernel to complete, and for its writes to be visible, before reading or
  * writing any state, so the results are bit-identical with on = 0 (plain
  * stream-ordered launches).  It shortens the gap between consecutive steps.
- * The reference kernel is always launched plainly.  MACLAB_ERR_INVALID unless
- * on is 0 or 1. */
+ * The reference kernel is always launched plainly; maclab_tune may change the
+ * setting.  No paper counterpart (a launch detail of Eqs. (4)-(5)'s time
+ * loop).  Drops the handle's captured graphs.  Errors: MACLAB_ERR_INVALID (NULL
+ * handle, on not 0 or 1). */
 maclab_status maclab_set_launch_overlap(maclab_handle h, int32_t on);
 
-/* *on receives the handle's launch-overlap setting (1 or 0). */
+/* *on receives the handle's launch-overlap setting (1 or 0).  Errors:
+ * MACLAB_ERR_INVALID (NULL argument). */
 maclab_status maclab_get_launch_overlap(maclab_handle h, int32_t *on);
 
 /* Tile shape of the kernel in use.  Tiled and folded kernels: ty rows of y per
@@ -240,7 +243,9 @@ maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows);
  * step, stores FP32 or FP64 and every nx >= 8.  Rebuilds the work list. */
 maclab_status maclab_batch_set_depth(maclab_batch b, int32_t depth);
 
-/* maclab_set_launch_overlap for the batch's launches and its members. */
+/* maclab_set_launch_overlap for the batch's launches and its members
+ * (maclab_batch_tune may change it).  Errors: MACLAB_ERR_INVALID (NULL batch,
+ * on not 0 or 1). */
 maclab_status maclab_batch_set_launch_overlap(maclab_batch b, int32_t on);
 
 /* out[0] members, out[1] total nodes, out[2] fluid nodes, out[3] work items
@@ -363,8 +368,11 @@ maclab_status maclab_check_reciprocal(float lo, float hi, int32_t n, double *max
  * kernels use: one instruction, two fused multiply-adds on a float2) in
  * TFLOP/s, counting two operations per FMA: independent chains at full
  * occupancy, the best of three timed launches after a warm-up.  The D3Q19
- * step is checked against it beside the memory roofline.  Synchronous.
- * Errors: MACLAB_ERR_INVALID, MACLAB_ERR_OOM, MACLAB_ERR_CUDA. */
+ * step is checked against it beside the memory roofline.  No paper
+ * counterpart (a measurement of the device).  Runs on the current device and
+ * the default stream, synchronously; allocates 2 KB of device memory for the
+ * call.  Errors: MACLAB_ERR_INVALID (NULL tflops), MACLAB_ERR_OOM,
+ * MACLAB_ERR_CUDA. */
 maclab_status maclab_measure_fp32_peak(double *tflops);
 
 /* Run the handle's stream to completion and report any CUDA error. */
