@@ -32,11 +32,31 @@
  * gains force[i] (the pressure-gradient term of Test 2 in lattice units; its
  * sign is taken so that the closed form Eq. (8) holds).
  *
- * Build: plain C99, -O2 -ffp-contract=off, no -ffast-math.
+ * Threads.  With OpenMP the node loops run on several host threads.  Every
+ * output value is still formed by one thread with exactly the operations and
+ * operand order of the single-thread loop, so results are bitwise independent
+ * of the thread count (oracle_set_threads); no sum is split across threads.
+ *
+ * Build: plain C99, -O2 -ffp-contract=off, no -ffast-math, -fopenmp if the
+ * compiler has it (without it every loop runs on one thread).
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads for the node loops (OpenMP builds); returns the count in use. */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* D2Q9 velocities in the order listed after Eq. (1), alpha = 0..8. */
 static const int D2Q9_C[9][3] = {
@@ -124,6 +144,8 @@ int oracle_step(int lattice, int64_t nx, int64_t ny, int64_t nz, uint32_t period
     if (nx < 1 || ny < 1 || nz < 1 || (L.d == 2 && nz != 1)) return ORACLE_BAD_ARG;
     const int64_t n[3] = {nx, ny, nz};
     const int64_t N = nx * ny * nz;
+    int outside = 0;  /* set when a fluid node's upstream node leaves a closed axis */
+#pragma omp parallel for schedule(static)
     for (int64_t node = 0; node < N; ++node) {
         const int64_t x[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
         if (wall && wall[node]) {
@@ -133,12 +155,14 @@ int oracle_step(int lattice, int64_t nx, int64_t ny, int64_t nz, uint32_t period
             continue;
         }
         double rho_new = 0.0, mom[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < L.q; ++a) {
+        int bad = 0;
+        for (int a = 0; a < L.q && !bad; ++a) {
             int64_t y[3] = {0, 0, 0};
             for (int i = 0; i < 3; ++i) {
                 y[i] = upstream(x[i], L.c[a][i], n[i], (periodic >> i) & 1u);
-                if (y[i] < 0) return ORACLE_OUTSIDE;
+                if (y[i] < 0) bad = 1;
             }
+            if (bad) break;
             const int64_t src = (y[2] * ny + y[1]) * nx + y[0];
             double ut[3] = {0.0, 0.0, 0.0};
             for (int i = 0; i < L.d; ++i) ut[i] = u[i * N + src];
@@ -146,11 +170,16 @@ int oracle_step(int lattice, int64_t nx, int64_t ny, int64_t nz, uint32_t period
             rho_new += f;                                       /* Eq. (4) */
             for (int i = 0; i < L.d; ++i) mom[i] += (double)L.c[a][i] * f;  /* Eq. (5) */
         }
+        if (bad) {
+#pragma omp atomic write
+            outside = 1;
+            continue;
+        }
         rho_out[node] = rho_new;
         for (int i = 0; i < L.d; ++i)
             u_out[i * N + node] = mom[i] / rho_new + (force ? force[i] : 0.0);
     }
-    return ORACLE_OK;
+    return outside ? ORACLE_OUTSIDE : ORACLE_OK;
 }
 
 /* Step (v): repeat the update nsteps times (ping-pong). In-place on rho/u. */
@@ -261,5 +290,134 @@ int oracle_adjoint_step(int lattice, int64_t nx, int64_t ny, int64_t nz, uint32_
                                     (3.0 * L.c[a][i] + 9.0 * cu * L.c[a][i] - 3.0 * ut[i]);
         }
     }
+    return ORACLE_OK;
+}
+
+/* Downstream coordinate x + c along one axis; -1 if it leaves a closed axis. */
+static int64_t downstream(int64_t x, int c, int64_t n, int periodic) {
+    int64_t y = x + c;
+    if (y < 0 || y >= n) {
+        if (!periodic) return -1;
+        y = (y % n + n) % n;
+    }
+    return y;
+}
+
+/*
+ * The same adjoint as oracle_adjoint_step, written as a gather so that the
+ * node loops can run on several threads.  Pass 1 forms (lam_r, lam_m) of every
+ * fluid node x exactly as oracle_adjoint_step does.  Pass 2 visits every source
+ * node s and adds, for each direction a whose downstream node x = s + c_a is
+ * fluid, the same term the scatter adds, in the scatter's order (ascending x,
+ * then ascending a), starting from the same initial value.  Every lam value is
+ * therefore the same sequence of operations on the same operands, and the
+ * result is bitwise equal to oracle_adjoint_step's for any thread count.
+ */
+int oracle_adjoint_step_gather(int lattice, int64_t nx, int64_t ny, int64_t nz,
+                               uint32_t periodic, const uint8_t *wall, const double *rho,
+                               const double *u, const double *force,
+                               const double *lam_rho_next, const double *lam_u_next,
+                               double *lam_rho, double *lam_u, double *grad_force) {
+    lattice_t L;
+    if (get_lattice(lattice, &L)) return ORACLE_BAD_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || (L.d == 2 && nz != 1)) return ORACLE_BAD_ARG;
+    const int64_t n[3] = {nx, ny, nz};
+    const int64_t N = nx * ny * nz;
+    (void)force;
+    double *lr = (double *)malloc(sizeof(double) * (size_t)N);
+    double *lm = (double *)malloc(sizeof(double) * (size_t)N * 3);
+    if (!lr || !lm) { free(lr); free(lm); return ORACLE_NOMEM; }
+    int outside = 0;
+    /* pass 1: the adjoints of each fluid node's two outputs */
+#pragma omp parallel for schedule(static)
+    for (int64_t node = 0; node < N; ++node) {
+        if (wall && wall[node]) continue;
+        const int64_t x[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+        double rho_new = 0.0, mom[3] = {0.0, 0.0, 0.0};
+        int bad = 0;
+        for (int a = 0; a < L.q && !bad; ++a) {
+            int64_t y[3] = {0, 0, 0};
+            for (int i = 0; i < 3; ++i) {
+                y[i] = upstream(x[i], L.c[a][i], n[i], (periodic >> i) & 1u);
+                if (y[i] < 0) bad = 1;
+            }
+            if (bad) break;
+            const int64_t src = (y[2] * ny + y[1]) * nx + y[0];
+            double ut[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < L.d; ++i) ut[i] = u[i * N + src];
+            const double f = feq(&L, a, rho[src], ut);
+            rho_new += f;
+            for (int i = 0; i < L.d; ++i) mom[i] += (double)L.c[a][i] * f;
+        }
+        if (bad) {
+#pragma omp atomic write
+            outside = 1;
+            continue;
+        }
+        double lam_r = lam_rho_next[node];
+        for (int i = 0; i < L.d; ++i) {
+            const double lu = lam_u_next[i * N + node];
+            lam_r -= lu * mom[i] / (rho_new * rho_new);
+            lm[3 * node + i] = lu / rho_new;
+        }
+        lr[node] = lam_r;
+    }
+    if (outside) { free(lr); free(lm); return ORACLE_OUTSIDE; }
+    /* d output / d force = identity on fluid nodes, summed in node order */
+    if (grad_force)
+        for (int64_t node = 0; node < N; ++node) {
+            if (wall && wall[node]) continue;
+            for (int i = 0; i < L.d; ++i) grad_force[i] += lam_u_next[i * N + node];
+        }
+    /* pass 2: every source gathers what the scatter would have sent it */
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < N; ++s) {
+        const int64_t y[3] = {s % nx, (s / nx) % ny, s / (nx * ny)};
+        int64_t dst[19];
+        int dir[19], k = 0;
+        for (int a = 0; a < L.q; ++a) {
+            int64_t x[3] = {0, 0, 0};
+            int ok = 1;
+            for (int i = 0; i < 3 && ok; ++i) {
+                x[i] = downstream(y[i], L.c[a][i], n[i], (periodic >> i) & 1u);
+                if (x[i] < 0) ok = 0;
+            }
+            if (!ok) continue;
+            const int64_t xn = (x[2] * ny + x[1]) * nx + x[0];
+            if (wall && wall[xn]) continue;
+            /* insert (xn, a) keeping ascending (x, a) order */
+            int j = k++;
+            while (j > 0 && dst[j - 1] > xn) {
+                dst[j] = dst[j - 1];
+                dir[j] = dir[j - 1];
+                --j;
+            }
+            dst[j] = xn;
+            dir[j] = a;
+        }
+        double acc_r = (wall && wall[s]) ? lam_rho_next[s] : 0.0;
+        double acc_u[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < L.d; ++i) acc_u[i] = (wall && wall[s]) ? lam_u_next[i * N + s] : 0.0;
+        for (int t = 0; t < k; ++t) {
+            const int a = dir[t];
+            const int64_t xn = dst[t];
+            double ut[3] = {0.0, 0.0, 0.0}, cu = 0.0, uu = 0.0;
+            for (int i = 0; i < L.d; ++i) {
+                ut[i] = u[i * N + s];
+                cu += (double)L.c[a][i] * ut[i];
+                uu += ut[i] * ut[i];
+            }
+            double g = lr[xn];
+            for (int i = 0; i < L.d; ++i) g += (double)L.c[a][i] * lm[3 * xn + i];
+            const double w = L.w[a];
+            acc_r += g * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            for (int i = 0; i < L.d; ++i)
+                acc_u[i] += g * w * rho[s] * (3.0 * L.c[a][i] + 9.0 * cu * L.c[a][i] - 3.0 * ut[i]);
+        }
+        lam_rho[s] = acc_r;
+        for (int i = 0; i < L.d; ++i) lam_u[i * N + s] = acc_u[i];
+    }
+    free(lr);
+    free(lm);
     return ORACLE_OK;
 }

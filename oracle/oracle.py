@@ -37,14 +37,20 @@ DIMS = {D2Q9: 2, D3Q19: 3}
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle (gcc, -O2, no FMA contraction, no fast-math)."""
+    """Compile the C oracle (gcc, -O2, no FMA contraction, no fast-math).
+
+    With OpenMP where gcc has it (the node loops then run on several host
+    threads, with results bitwise independent of the thread count); without it
+    if that build fails.
+    """
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.run(
-            ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-             "-shared", "-o", tmp, _SRC, "-lm"],
-            check=True)
+        base = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                "-shared", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _SO)
     return _SO
 
@@ -62,12 +68,33 @@ def _load():
             lib.oracle_adjoint_step.argtypes = [ctypes.c_int, i64, i64, i64, u32, vp, dp, dp, dp,
                                                 dp, dp, dp, dp, dp]
             lib.oracle_adjoint_step.restype = ctypes.c_int
+            lib.oracle_adjoint_step_gather.argtypes = lib.oracle_adjoint_step.argtypes
+            lib.oracle_adjoint_step_gather.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = ctypes.c_int
             lib.oracle_lattice_table.argtypes = [ctypes.c_int, vp, vp]
             lib.oracle_lattice_table.restype = ctypes.c_int
             lib.oracle_feq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
             lib.oracle_feq.restype = ctypes.c_double
             _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's node loops (0: keep); returns the count in use.
+
+    Results do not depend on it (each value is formed by one thread in the
+    single-thread order).
+    """
+    return _load().oracle_set_threads(int(n))
+
+
+def host_cores() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def _ptr(a):
@@ -132,8 +159,13 @@ def step(lattice, rho, u, periodic, wall=None, force=None, nsteps=1):
     return rho, u
 
 
-def adjoint_step(lattice, rho, u, periodic, lam_rho_next, lam_u_next, wall=None, force=None):
-    """Adjoint of one ``step``: returns (lam_rho, lam_u, grad_force)."""
+def adjoint_step(lattice, rho, u, periodic, lam_rho_next, lam_u_next, wall=None, force=None,
+                 gather=False):
+    """Adjoint of one ``step``: returns (lam_rho, lam_u, grad_force).
+
+    gather=False: the plain scatter, one thread.  gather=True: the same sums
+    as a gather over sources, on the oracle's host threads (bitwise equal).
+    """
     rho = _f64(rho)
     d, nx, ny, nz = _shape(lattice, rho)
     u = _f64(u)
@@ -142,28 +174,43 @@ def adjoint_step(lattice, rho, u, periodic, lam_rho_next, lam_u_next, wall=None,
     gf = np.zeros(d)
     wall_b = None if wall is None else np.ascontiguousarray(wall, dtype=np.uint8)
     f = None if force is None else _f64(np.asarray(force, dtype=np.float64).reshape(d))
-    rc = _load().oracle_adjoint_step(lattice, nx, ny, nz, int(periodic), _ptr(wall_b), _ptr(rho),
-                                     _ptr(u), _ptr(f), _ptr(lr1), _ptr(lu1), _ptr(lr), _ptr(lu),
-                                     _ptr(gf))
+    lib = _load()
+    fn = lib.oracle_adjoint_step_gather if gather else lib.oracle_adjoint_step
+    rc = fn(lattice, nx, ny, nz, int(periodic), _ptr(wall_b), _ptr(rho), _ptr(u), _ptr(f),
+            _ptr(lr1), _ptr(lu1), _ptr(lr), _ptr(lu), _ptr(gf))
     _check(rc, "adjoint_step")
     return lr, lu, gf
 
 
 def rollout_adjoint(lattice, rho0, u0, periodic, nsteps, lam_rho_T, lam_u_T, wall=None,
-                    force=None):
-    """Reverse-mode gradient of an n-step rollout, storing every state (small cases).
+                    force=None, checkpoint_every=None, gather=False):
+    """Reverse-mode gradient of an n-step rollout.
 
     Returns (lam_rho_0, lam_u_0, grad_force) for a loss whose adjoint on the
-    final state is (lam_rho_T, lam_u_T).
+    final state is (lam_rho_T, lam_u_T).  checkpoint_every=None stores every
+    state; an integer K keeps only the states of steps 0, K, 2K, ... and
+    recomputes each segment's states from its checkpoint when the reverse pass
+    reaches it (the forward step is deterministic, so the states and the
+    result are the same).  gather: see ``adjoint_step``.
     """
-    states = [(_f64(rho0), _f64(u0))]
-    for _ in range(nsteps):
-        states.append(step(lattice, *states[-1], periodic, wall=wall, force=force))
     lr, lu = _f64(lam_rho_T), _f64(lam_u_T)
     gf = np.zeros(DIMS[lattice])
-    for s in range(nsteps - 1, -1, -1):
-        lr, lu, g = adjoint_step(lattice, *states[s], periodic, lr, lu, wall=wall, force=force)
-        gf += g
+    k = nsteps if not checkpoint_every else max(1, int(checkpoint_every))
+    checkpoints = {0: (_f64(rho0), _f64(u0))}
+    state = checkpoints[0]
+    for s in range(1, nsteps + 1):
+        state = step(lattice, *state, periodic, wall=wall, force=force)
+        if s % k == 0 and s < nsteps:
+            checkpoints[s] = state
+    for start in sorted(checkpoints, reverse=True):
+        stop = min(start + k, nsteps)
+        seg = [checkpoints[start]]
+        for _ in range(start, stop - 1):
+            seg.append(step(lattice, *seg[-1], periodic, wall=wall, force=force))
+        for s in range(stop - 1, start - 1, -1):
+            lr, lu, g = adjoint_step(lattice, *seg[s - start], periodic, lr, lu, wall=wall,
+                                     force=force, gather=gather)
+            gf += g
     return lr, lu, gf
 
 
