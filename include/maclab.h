@@ -344,12 +344,21 @@ maclab_status maclab_adjoint_finish(maclab_handle h, const void *lam_0, const vo
  *   [5] sum |u - u_prev|^2, [6] sum |u|^2, [7] max |u|, [8] non-finite count.
  * stream: cudaStream_t (NULL = default stream); the call is asynchronous.
  *
- * The first call on a device looks up the array's address on that device
- * (with that device current); make that first call before any stream capture.
+ * All four pointers must be device (or managed) memory usable by the current
+ * device; anything else (a host buffer, another GPU's memory) is rejected with
+ * MACLAB_ERR_INVALID before any launch.
+ *
+ * The first call on a device (and again after the device's context is
+ * replaced, e.g. by cudaDeviceReset) sets up, with that device current: it
+ * loads the reduction kernels, whose code lazy module loading would otherwise
+ * load -- possibly taking device memory -- at their first launch, and looks up
+ * the array's address.  Make that first call before reserving the device's
+ * memory for other uses and before any stream capture.
  * Every call on a device reuses the same array: calls that overlap on the GPU
  * race.  Nothing in it needs clearing between calls (each call writes the
  * entries it reads).  No cudaMalloc, cudaFree or other allocating routine is
- * called.  Errors: MACLAB_ERR_INVALID (arguments, size), MACLAB_ERR_CUDA. */
+ * called.  Errors: MACLAB_ERR_INVALID (arguments, size, pointers),
+ * MACLAB_ERR_CUDA. */
 maclab_status maclab_diagnostics_noalloc(int32_t lattice, int32_t precision, int64_t n_nodes,
                                          const void *state, const void *prev_state,
                                          const uint8_t *exclude, double *out_sums,

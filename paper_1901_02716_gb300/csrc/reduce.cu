@@ -175,44 +175,94 @@ cudaError_t launch_diagnostics(const Geometry& g, int precision, const void* cur
 // For callers that cannot allocate device memory while they run (for example a
 // host loop that reserved all device memory for its own pool up front, or code
 // that may not block on an allocation): the same two kernels, with the
-// per-block partial sums in a fixed array that the library reserves when it is
-// loaded, instead of a buffer owned by a handle.
+// per-block partial sums in a fixed array that the module holds, instead of a
+// buffer owned by a handle.
 //
-// Each block folds a fixed run of kNoAllocNodesPerBlock nodes, so the partials
-// a call needs grow with the node count; the array holds kNoAllocMaxBlocks of
-// them, which bounds one call to kNoAllocMaxNodes nodes.
+// A call launches ceil(n / kNoAllocNodesPerBlock) blocks, so each block folds
+// about kNoAllocNodesPerBlock nodes (interleaved with the other blocks' by the
+// grid stride); the array holds kNoAllocMaxBlocks partials, which bounds one
+// call to kNoAllocMaxNodes nodes.
 
 constexpr int64_t kNoAllocMaxBlocks = 4096;
 constexpr int64_t kNoAllocNodesPerBlock = 8192;
 constexpr int64_t kNoAllocMaxNodes = kNoAllocMaxBlocks * kNoAllocNodesPerBlock;  // 33,554,432
 
-// Held by every GPU that loads the library, until the process exits
+// Held by every GPU that loads this module, until the process exits
 // (4096 x 9 doubles = 288 KiB).  Every call overwrites the entries it reads
 // before reading them, so nothing here has to start at zero; calls that
 // overlap on the GPU share it and race.
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * kDiagSlots];
 
 namespace {
+using CtxGetCurrent = int (*)(void**);  // cuCtxGetCurrent(CUcontext*), through the runtime
 std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[64] = {};  // device address of g_noalloc_partials, per device
+struct NoAllocSlot {
+  void* ctx = nullptr;     // context the address below belongs to
+  double* ptr = nullptr;   // device address of g_noalloc_partials in that context
+};
+NoAllocSlot g_noalloc_slot[64];  // per device
+CtxGetCurrent g_ctx_get = nullptr;
+bool g_ctx_get_looked_up = false;
 }  // namespace
 
-// Address of the array on the current device: looked up once per device (the
-// first call on a device does it) with that device current.
+// Set-up on the current device, once per device and context: load the
+// reduction kernels (with lazy module loading a kernel's code is otherwise
+// loaded, and may take device memory, at its first launch) and look up the
+// array's address with that device current.  A context that replaces the
+// device's previous one (cudaDeviceReset) has another handle and gets the
+// set-up again; a recreated context that happened to reuse the old handle
+// would not be told apart.
 static cudaError_t noalloc_scratch(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_ctx_get_looked_up) {
+    g_ctx_get_looked_up = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_ctx_get = reinterpret_cast<CtxGetCurrent>(fn);
+    cudaGetLastError();
+  }
+  void* ctx = nullptr;
+  if (g_ctx_get) g_ctx_get(&ctx);
+  NoAllocSlot& slot = g_noalloc_slot[dev];
+  if (!slot.ptr || slot.ctx != ctx) {
+    cudaFuncAttributes fa{};
+    const void* kernels[] = {(const void*)diag_partial<double>, (const void*)diag_partial<float>,
+                             (const void*)diag_partial<__nv_bfloat16>, (const void*)diag_partial<__half>,
+                             (const void*)diag_final};
+    for (const void* k : kernels) {
+      e = cudaFuncGetAttributes(&fa, k);
+      if (e != cudaSuccess) return e;
+    }
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
+    slot.ptr = static_cast<double*>(p);
+    slot.ctx = ctx;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = slot.ptr;
   return cudaSuccess;
+}
+
+// True if p is device (or managed) memory that the current device can use.
+static bool noalloc_device_pointer(const void* p) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace maclab
@@ -237,6 +287,10 @@ extern "C" maclab_status maclab_diagnostics_noalloc(int32_t lattice, int32_t pre
     return err(MACLAB_ERR_INVALID,
                "n_nodes exceeds the 33554432 nodes the fixed scratch of "
                "maclab_diagnostics_noalloc can reduce in one call");
+  if (!noalloc_device_pointer(state) || (prev_state && !noalloc_device_pointer(prev_state)) ||
+      (exclude && !noalloc_device_pointer(exclude)) || !noalloc_device_pointer(out_sums))
+    return err(MACLAB_ERR_INVALID,
+               "state, prev_state, exclude and out_sums must be device memory of the current device");
   double* partials = nullptr;
   cudaError_t e = noalloc_scratch(&partials);
   if (e != cudaSuccess) {

@@ -83,3 +83,16 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(M, "library_path", lambda: str(tmp_path / "nope.so"))
     with pytest.raises(M.MacLABError):
         M.lib()
+
+
+def test_noalloc_diagnostics_refuses_host_buffers(lib):
+    """maclab_diagnostics_noalloc checks that its buffers are device memory
+    before it launches anything: host arrays give MACLAB_ERR_INVALID (here
+    without a GPU, where no pointer can be device memory) and stay untouched."""
+    state = np.zeros(4 * 64, dtype=np.float32)
+    out = np.full(9, 3.0)
+    with pytest.raises(M.MacLABError) as ei:
+        M.maclab_diagnostics_noalloc(M.D3Q19, M.F32, 64, state.ctypes.data, None, None,
+                                     out.ctypes.data, None)
+    assert ei.value.status == M.ERR_INVALID
+    assert np.all(out == 3.0)

@@ -40,16 +40,37 @@ def storage_order(case):
     return out.reshape(-1).copy()
 
 
-@pytest.mark.parametrize("lat,dims,periodic,walls", [
-    (inputs.D3Q19, (32, 20, 12), 0b000, "box"),      # interleaved rows, walls excluded
-    (inputs.D2Q9, (30, 17), 0b01, "mixed"),          # plain order, mask walls
-    (inputs.D2Q9, (64, 48), 0b11, "none"),           # no walls
-])
-def test_noalloc_matches_handle_diagnostics(lat, dims, periodic, walls):
+def _cases():
+    small = [
+        # (label, case builder, storage type)
+        ("d3q19-box-f32", lambda: inputs.random_case(inputs.D3Q19, (32, 20, 12), 0b000, seed=61,
+                                                     u_amp=0.08, rho_amp=0.02, walls="box"), M.F32),
+        ("d3q19-box-f64", lambda: inputs.random_case(inputs.D3Q19, (32, 20, 12), 0b000, seed=62,
+                                                     u_amp=0.08, rho_amp=0.02, walls="box"), M.F64),
+        ("d3q19-box-bf16", lambda: inputs.random_case(inputs.D3Q19, (32, 20, 12), 0b000, seed=63,
+                                                      u_amp=0.08, rho_amp=0.02, walls="box"),
+         M.BF16_STORE),
+        ("d2q9-mask-f32", lambda: inputs.random_case(inputs.D2Q9, (30, 17), 0b01, seed=64,
+                                                     u_amp=0.08, rho_amp=0.02, walls="mixed"), M.F32),
+        ("d2q9-periodic-f32", lambda: inputs.random_case(inputs.D2Q9, (64, 48), 0b11, seed=65,
+                                                         u_amp=0.08, rho_amp=0.02), M.F32),
+    ]
+    large = [
+        # 2,097,152 nodes: 256 partial blocks
+        ("cavity3d-128-f32", lambda: inputs.cavity3d(128, lid=inputs.lid_speed(100.0, 128)), M.F32),
+        # 33,524,100 nodes: 4093 of the 4096 partial blocks the fixed array holds
+        ("cavity2d-5790-f32", lambda: inputs.cavity2d(5790, lid=inputs.lid_speed(1000.0, 5790)),
+         M.F32),
+    ]
+    return small + large
+
+
+@pytest.mark.parametrize("label,make,precision", _cases(), ids=[c[0] for c in _cases()])
+def test_noalloc_matches_handle_diagnostics(label, make, precision):
     torch = pytest.importorskip("torch")
-    case = inputs.random_case(lat, dims, periodic, seed=61, u_amp=0.08, rho_amp=0.02,
-                              walls=walls)
-    s = M.Solver.from_case(case, M.F32)          # dx = 1, nu = 1/6: e = 1, rho0 = 1
+    case = make()
+    lat = case.lattice
+    s = M.Solver.from_case(case, precision)      # dx = 1, nu = 1/6: e = 1, rho0 = 1
     nbytes = s.state_bytes()
     prev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     cur = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -70,17 +91,19 @@ def test_noalloc_matches_handle_diagnostics(lat, dims, periodic, walls):
     results = []
     for _ in range(2):                           # two calls in a row share the scratch
         out.fill_(float("nan"))
-        M.maclab_diagnostics_noalloc(lat, M.F32, n, cur.data_ptr(), prev.data_ptr(),
+        M.maclab_diagnostics_noalloc(lat, precision, n, cur.data_ptr(), prev.data_ptr(),
                                      None if excl is None else excl.data_ptr(),
                                      out.data_ptr(), stream)
         torch.cuda.synchronize()
         results.append(out.cpu().numpy().copy())
+    # momentum sums cancel: their rounding is bounded by n |u|max, not by the sum
+    mom_abs = 1e-12 * n * max(ref["max_u_lattice"], 1e-30)
     for sums in results:
         assert np.all(np.isfinite(sums))
         assert n_fluid + sums[0] == pytest.approx(ref["mass"], rel=1e-12)
         assert 0.5 * sums[1] == pytest.approx(ref["kinetic"], rel=1e-12)
-        for i in range(len(dims)):
-            assert sums[2 + i] == pytest.approx(ref["momentum"][i], rel=1e-10, abs=1e-12)
+        for i in range(case.d):
+            assert sums[2 + i] == pytest.approx(ref["momentum"][i], rel=1e-10, abs=mom_abs)
         assert math.sqrt(sums[5] / sums[6]) == pytest.approx(ref["residual"], rel=1e-12)
         assert sums[7] == pytest.approx(ref["max_u_lattice"], rel=1e-15)
         assert sums[8] == ref["nonfinite"] == 0
@@ -92,3 +115,21 @@ def test_noalloc_rejects_oversized_input():
         M.maclab_diagnostics_noalloc(inputs.D3Q19, M.F32, 33554432 + 1, 1, None, None, 1)
     assert ei.value.status == M.ERR_INVALID
     assert "33554432" in str(ei.value)
+
+
+def test_noalloc_rejects_host_buffers():
+    """A host out_sums (or state) is refused before any launch; a device
+    buffer it would have written stays untouched."""
+    torch = pytest.importorskip("torch")
+    n = 4096
+    state = torch.zeros(4 * n, dtype=torch.float32, device="cuda")
+    out_dev = torch.full((9,), 7.0, dtype=torch.float64, device="cuda")
+    out_host = np.full(9, 7.0)
+    state_host = np.zeros(4 * n, dtype=np.float32)
+    for st, o in ((state.data_ptr(), out_host.ctypes.data), (state_host.ctypes.data, out_dev.data_ptr())):
+        with pytest.raises(M.MacLABError) as ei:
+            M.maclab_diagnostics_noalloc(inputs.D3Q19, M.F32, n, st, None, None, o, None)
+        assert ei.value.status == M.ERR_INVALID
+    torch.cuda.synchronize()
+    assert np.all(out_host == 7.0)
+    assert torch.all(out_dev == 7.0)
