@@ -147,12 +147,20 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * default 2 below 200,000 quads where two steps are supported, see
  * maclab_batch_set_depth), the default for D2Q9 grids with nx % 4 == 0.  All compute Eqs.
  * (4)-(5) with the same terms per node (the folded kernel sums them in
- * another order; the segment and tiled kernels give identical bits). */
+ * another order; the segment and tiled kernels give identical bits).
+ * MACLAB_KERNEL_ROWS2 is the D3Q19 kernel with two rows per thread (FP32,
+ * BF16 or FP16 storage; nx % 4 == 0 with nx <= 128; ny divisible by the
+ * tile's rows, 8 by default; the tile's ty is its rows, 4 or 8, and 8 for
+ * 16-bit storage; the default for FP32 storage where it applies): the
+ * equilibria moving between a thread's rows stay in registers and the rest of
+ * the y exchange is read 16 bytes per direction; its terms are formed and
+ * summed in yet another order, so it agrees with the others to rounding. */
 #define MACLAB_KERNEL_AUTO 0
 #define MACLAB_KERNEL_REFERENCE 1
 #define MACLAB_KERNEL_TILED 2
 #define MACLAB_KERNEL_FOLDED 3
 #define MACLAB_KERNEL_SEGMENT 4
+#define MACLAB_KERNEL_ROWS2 5
 
 /* Choose the step kernel.  MACLAB_ERR_UNSUPPORTED if the tiled kernel cannot
  * serve this domain (then the handle keeps its previous choice). */

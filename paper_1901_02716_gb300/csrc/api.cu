@@ -779,13 +779,14 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
     return MACLAB_OK;
   }
   if (kernel != MACLAB_KERNEL_REFERENCE && kernel != MACLAB_KERNEL_TILED && kernel != MACLAB_KERNEL_FOLDED &&
-      kernel != MACLAB_KERNEL_SEGMENT)
+      kernel != MACLAB_KERNEL_SEGMENT && kernel != MACLAB_KERNEL_ROWS2)
     return fail(MACLAB_ERR_INVALID, "unknown kernel id");
   if (!step_kernel_supported(h->g, h->precision, kernel))
     return fail(MACLAB_ERR_UNSUPPORTED, "kernel does not support this domain");
   h->kernel = kernel;
   // a tile shape the new kernel lacks falls back to its default
   if (kernel == MACLAB_KERNEL_FOLDED && !fold_supported(h->g, h->precision, h->ty)) h->ty = 0;
+  if (kernel == MACLAB_KERNEL_ROWS2 && !rows2_supported(h->g, h->precision, h->ty)) h->ty = 0;
   if (kernel == MACLAB_KERNEL_TILED && !tiled_supported(h->g, h->precision, h->ty, h->tz)) h->ty = 0;
   return MACLAB_OK;
 }
@@ -808,6 +809,7 @@ maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (ty < 0 || tz < 0 || tz > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad tile shape");
   const bool ok = h->kernel == MACLAB_KERNEL_FOLDED    ? fold_supported(h->g, h->precision, ty)
+                  : h->kernel == MACLAB_KERNEL_ROWS2   ? rows2_supported(h->g, h->precision, ty)
                   : h->kernel == MACLAB_KERNEL_SEGMENT
                       ? (ty <= 1 || segment_depth(h->g, h->precision, ty) == 2)  // ty: steps per launch, tz: rows
                                                        : tiled_supported(h->g, h->precision, ty, tz);
@@ -1163,6 +1165,7 @@ bool shape_supported(const maclab_ctx* h, int kernel, int ty, int tz) {
   if (kernel == MACLAB_KERNEL_SEGMENT)
     return step_kernel_supported(h->g, h->precision, MACLAB_KERNEL_SEGMENT) &&
            (ty <= 1 || segment_depth(h->g, h->precision, ty) == 2);
+  if (kernel == MACLAB_KERNEL_ROWS2) return rows2_supported(h->g, h->precision, ty);
   return kernel == MACLAB_KERNEL_FOLDED ? fold_supported(h->g, h->precision, ty)
                                         : tiled_supported(h->g, h->precision, ty, tz);
 }
@@ -1340,6 +1343,9 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
       for (int tz : tzs) cands.push_back(Cand{kernel, h->g.d == 3 ? tys3[a] : 0, tz});
   for (int ty : {1, 2})
     for (int tz : {2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_SEGMENT, ty, tz});
+  if (h->g.d == 3)
+    for (int ty : {4, 8})
+      for (int tz : tzs) cands.push_back(Cand{MACLAB_KERNEL_ROWS2, ty, tz});
   for (const Cand& c : cands) {
     if (!shape_supported(h, c.kernel, c.ty, c.tz)) continue;
     h->kernel = c.kernel;

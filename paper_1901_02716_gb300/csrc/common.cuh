@@ -167,6 +167,14 @@ int tiled_threads(const Geometry& g, int precision, int ty, int tz);
 bool fold_supported(const Geometry& g, int precision, int ty);
 int fold_threads(const Geometry& g, int precision, int ty);
 cudaError_t launch_fold(const StepLaunch& s, cudaStream_t stream, int ty, int tz);
+// Chunks of the march axis for a grid of ytiles tiles per plane with per_sm
+// resident blocks per SM (tz_req > 0: planes per chunk as asked).
+int fold_chunks(int nplanes, int ytiles, int tz_req, int per_sm);
+
+// Defined in step_rows2.cu (D3Q19, two rows per thread; FP32 arithmetic).
+bool rows2_supported(const Geometry& g, int precision, int ty);
+int rows2_threads(const Geometry& g, int precision, int ty);
+cudaError_t launch_rows2(const StepLaunch& s, cudaStream_t stream, int ty, int tz);
 
 // Defined in api.cu: message returned by maclab_last_error on this thread.
 void record_error(const char* msg);

@@ -139,14 +139,18 @@ bool step_kernel_supported(const Geometry& g, int precision, int kernel) {
   if (kernel == MACLAB_KERNEL_TILED) return tiled_supported(g, precision, 0, 0);
   if (kernel == MACLAB_KERNEL_FOLDED) return fold_supported(g, precision, 0);
   if (kernel == MACLAB_KERNEL_SEGMENT) return g.lattice == kD2Q9 && g.ilv == 1;
+  if (kernel == MACLAB_KERNEL_ROWS2) return rows2_supported(g, precision, 0);
   return false;
 }
 
-// The folded kernel where it is built (D3Q19 FP32, ny a multiple of its tile
-// rows); for D2Q9 grids with nx % 4 == 0 the segment kernel (with its size
-// defaults it is faster than the tiled one from 64^2 to 1024^2); else the
-// tiled one, else the reference kernel.
+// D3Q19 with FP32 storage: the two-rows-per-thread kernel where it applies
+// (rows of up to 128 nodes), else the folded one where it is built (ny a
+// multiple of its tile rows); for D2Q9 grids with nx % 4 == 0 the segment
+// kernel (with its size defaults it is faster than the tiled one from 64^2 to
+// 1024^2); else the tiled one, else the reference kernel.
 int pick_step_kernel(const Geometry& g, int precision) {
+  if (precision == MACLAB_F32 && step_kernel_supported(g, precision, MACLAB_KERNEL_ROWS2))
+    return MACLAB_KERNEL_ROWS2;
   if (step_kernel_supported(g, precision, MACLAB_KERNEL_FOLDED)) return MACLAB_KERNEL_FOLDED;
   if (step_kernel_supported(g, precision, MACLAB_KERNEL_SEGMENT)) return MACLAB_KERNEL_SEGMENT;
   return step_kernel_supported(g, precision, MACLAB_KERNEL_TILED) ? MACLAB_KERNEL_TILED
@@ -154,6 +158,11 @@ int pick_step_kernel(const Geometry& g, int precision) {
 }
 
 static const char* kernel_name(const Geometry& g, int precision, int kernel) {
+  if (kernel == MACLAB_KERNEL_ROWS2) {
+    static const char* rows2[4] = {"step_rows2<D3Q19,f64>", "step_rows2<D3Q19,f32>", "step_rows2<D3Q19,bf16>",
+                                   "step_rows2<D3Q19,f16>"};
+    return rows2[precision & 3];
+  }
   if (kernel == MACLAB_KERNEL_FOLDED) {
     static const char* fold[4] = {"step_fold<D3Q19,f64>", "step_fold<D3Q19,f32>", "step_fold<D3Q19,bf16>",
                                   "step_fold<D3Q19,f16>"};
@@ -183,6 +192,9 @@ KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, in
   if (kernel == MACLAB_KERNEL_FOLDED)
     return KernelInfo{MACLAB_KERNEL_FOLDED, 1, 1, fold_threads(g, precision, ty),
                       kernel_name(g, precision, kernel)};
+  if (kernel == MACLAB_KERNEL_ROWS2)
+    return KernelInfo{MACLAB_KERNEL_ROWS2, 1, 1, rows2_threads(g, precision, ty), kernel_name(g, precision, kernel)};
+
   if (kernel == MACLAB_KERNEL_SEGMENT) {
     const int depth = segment_depth(g, precision, ty);
     return KernelInfo{MACLAB_KERNEL_SEGMENT, depth, 1, depth == 2 ? 128 : 256, kernel_name(g, precision, kernel)};
@@ -199,6 +211,8 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel) {
       return launch_tiled(s, stream, s.ty, s.tz);
     case MACLAB_KERNEL_FOLDED:
       return launch_fold(s, stream, s.ty, s.tz);
+    case MACLAB_KERNEL_ROWS2:
+      return launch_rows2(s, stream, s.ty, s.tz);
     case MACLAB_KERNEL_SEGMENT:
       if (!s.seg_inst || !s.seg_items) return cudaErrorInvalidValue;
       if (s.seg_steps == 2)

@@ -49,7 +49,9 @@ cudaError_t fold_dispatch(const FoldShape& s, const TiledArgs& ta, const void* i
   return cudaErrorInvalidValue;
 }
 
-int sm_count() {
+}  // namespace
+
+static int sm_count() {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -78,7 +80,6 @@ int fold_chunks(int nplanes, int ytiles, int tz_req, int per_sm) {
   return nzc;
 }
 
-}  // namespace
 
 bool fold_supported(const Geometry& g, int precision, int ty) {
   FoldShape s;

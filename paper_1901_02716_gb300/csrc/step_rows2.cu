@@ -1,0 +1,99 @@
+// step_rows2.cu -- host side of the D3Q19 step with two rows per thread
+// (step_rows2.cuh): block shapes, chunking of the march axis, instances.
+
+#include "step_rows2.cuh"
+
+namespace maclab {
+
+namespace {
+
+// (BXC, TYT) in order of preference for each row width (the first whose tile
+// of 2 TYT rows divides ny is the default); 16-bit storage: TYT = 4 only.
+struct Rows2Shape {
+  int bxc, tyt;
+};
+constexpr Rows2Shape kRows2Shapes[] = {{16, 4}, {32, 4}, {32, 2}};
+
+bool rows2_precision(int precision) {
+  return precision == MACLAB_F32 || precision == MACLAB_BF16_STORE || precision == MACLAB_F16_STORE;
+}
+
+// ty: rows per tile asked (0 = default), i.e. 2 TYT
+bool rows2_shape(const Geometry& g, int precision, int ty, Rows2Shape* out) {
+  if (g.d != 3 || g.lattice != kD3Q19 || !g.ilv || !rows2_precision(precision)) return false;
+  const int bx = g.nx / 4;
+  int bxc = 0;
+  for (int c : {16, 32})
+    if (bx <= c) { bxc = c; break; }
+  if (!bxc) return false;
+  for (const Rows2Shape& s : kRows2Shapes) {
+    if (s.bxc != bxc || (ty > 0 && 2 * s.tyt != ty)) continue;
+    if (precision != MACLAB_F32 && s.tyt != 4) continue;
+    if (g.ny % (2 * s.tyt) != 0) continue;
+    *out = s;
+    return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+template <typename S>
+cudaError_t rows2_dispatch(int bxc, int tyt, const TiledArgs& ta, const void* in, void* out,
+                           cudaStream_t st, dim3 grid, int* resident) {
+  switch (bxc * 100 + tyt) {
+    case 1604: return launch_rows2_shape<S, 16, 4>(ta, in, out, st, grid, resident);
+    case 3202: return launch_rows2_shape<S, 32, 2>(ta, in, out, st, grid, resident);
+    case 3204: return launch_rows2_shape<S, 32, 4>(ta, in, out, st, grid, resident);
+  }
+  return cudaErrorInvalidValue;
+}
+template cudaError_t rows2_dispatch<float>(int, int, const TiledArgs&, const void*, void*, cudaStream_t, dim3,
+                                          int*);
+
+bool rows2_supported(const Geometry& g, int precision, int ty) {
+  Rows2Shape s;
+  return rows2_shape(g, precision, ty, &s);
+}
+
+int rows2_threads(const Geometry& g, int precision, int ty) {
+  Rows2Shape s;
+  return rows2_shape(g, precision, ty, &s) ? s.bxc * s.tyt : 0;
+}
+
+cudaError_t launch_rows2(const StepLaunch& sl, cudaStream_t stream, int ty, int tz) {
+  const Geometry& g = sl.g;
+  Rows2Shape s;
+  if (!rows2_shape(g, sl.precision, ty, &s)) return cudaErrorInvalidValue;
+  TiledArgs ta{};
+  ta.nx = g.nx;
+  ta.ny = g.ny;
+  ta.nplanes = g.nz;
+  ta.n = g.n;
+  ta.plane_stride = (int64_t)g.nx * g.ny;
+  ta.ty = 2 * s.tyt;
+  const int ytiles = g.ny / ta.ty;
+  auto dispatch = [&](const void* in, void* out, dim3 grid, int* resident) {
+    switch (sl.precision) {
+      case MACLAB_F32: return rows2_dispatch<float>(s.bxc, s.tyt, ta, in, out, stream, grid, resident);
+      case MACLAB_BF16_STORE:
+        return rows2_dispatch<__nv_bfloat16>(s.bxc, s.tyt, ta, in, out, stream, grid, resident);
+      case MACLAB_F16_STORE: return rows2_dispatch<__half>(s.bxc, s.tyt, ta, in, out, stream, grid, resident);
+    }
+    return cudaErrorInvalidValue;
+  };
+  int resident = 0;
+  cudaError_t e = dispatch(nullptr, nullptr, dim3(), &resident);
+  if (e != cudaSuccess) return e;
+  ta.nzc = fold_chunks(ta.nplanes, ytiles, tz, resident);
+  ta.px = (g.periodic & 1u) ? 1 : 0;
+  ta.py = (g.periodic & 2u) ? 1 : 0;
+  ta.pz = (g.periodic & 4u) ? 1 : 0;
+  ta.wall_mode = g.wall_mode;
+  ta.mask = g.mask;
+  for (int i = 0; i < 3; ++i) ta.force[i] = sl.force[i];
+  ta.overlap = sl.overlap;
+  return dispatch(sl.in, sl.out, dim3(ta.nzc, ytiles), nullptr);
+}
+
+}  // namespace maclab

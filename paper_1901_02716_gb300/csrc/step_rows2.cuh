@@ -1,0 +1,595 @@
+// step_rows2.cuh -- D3Q19 MacLAB step with two rows per thread (Eqs. (2),
+// (4), (5); the same update as step_naive, summed in another order).
+//
+// Layout and march as in step_tiled.cuh: storage rows interleaved in halves
+// (a thread's 16-byte quad is the node pairs a = (2t, 2t + H), b = (2t + 1,
+// 2t + 1 + H)), a block marches z over a chunk of planes keeping the sums of
+// the destination planes p - 1, p, p + 1 in registers.  What differs:
+//
+//  * Each thread owns the quads of two adjacent rows (r0 = 2 tr, r1 = r0 + 1)
+//    of a tile of TY = 2 TYT rows.  Equilibria moving between its two rows
+//    stay in registers (or go to a neighbouring lane by a warp shuffle when
+//    they also move in x); only those leaving the thread's row pair in y go
+//    through shared memory: half the exchange of one row per thread.
+//  * The y exchange is laid out for the receiver: for each direction and each
+//    receiving thread-row there is one 16-byte unit per column holding the two
+//    values its pairs a and b gather, so a receiver reads a direction with one
+//    16-byte load.  Senders of the diagonal directions write their pair-b (+x)
+//    or pair-a (-x) value into the neighbouring column; at the seam between
+//    the row's halves the lane-swapped value is written, chosen per lane with
+//    selects (no divergent stores).
+//  * The halo rows next to the tile are loaded by the first and last
+//    thread-rows, which publish the halo's inward equilibria into the same
+//    exchange units a neighbouring thread-row would have filled: every thread
+//    then gathers the same way, with no branch on its position.
+//  * Terms of Eq. (2) per node: B_i = 3 rho u_i, P_ii = 3/2 B_i u_i,
+//    A = drho - (P_xx + P_yy + P_zz) / 3, S_i = A + P_ii, and for each axis
+//    pair (i, j) the sums S_i + P_jj +- 3 B_i u_j and B_i +- B_j.  A direction
+//    along an axis has T = S_i +- B_i and is added with its integer weight 2 by
+//    a fused multiply-add; the rest direction adds 12 A; the diagonals add 1 T.
+//    The sums are R = 36 drho' and M = 36 m', u' = M / (36 + R) + F.
+//  * Box x-walls: the lanes holding x = 0 or x = nx - 1 store the wall node's
+//    unchanged values (read from the input buffer at the start of the step)
+//    in place of the computed ones, with selects, so every lane stores whole
+//    quads.
+//
+// Requires: D3Q19, FP32 arithmetic (FP32, BF16 or FP16 storage), nx % 4 == 0,
+// nx / 4 <= BXC, ny % TY == 0, TYT >= 2.
+
+#pragma once
+#include "step_fold.cuh"
+
+namespace maclab {
+
+// ------------------------------------------------------------------ terms
+
+template <typename C>
+struct Terms3 {
+  using P = typename Pair<C>::P;
+  P A;      // drho - 3/2 rho u.u
+  P B[3];   // 3 rho u_i
+  P S[3];   // A + 9/2 rho u_i^2
+  P Ep[3], Em[3];  // pair k = (i, j): S_i + 9/2 rho u_j^2 +- 9 rho u_i u_j
+  P Op[3], Om[3];  // B_i +- B_j
+};
+
+template <typename C>
+__device__ __forceinline__ void make_terms3(typename Pair<C>::P r, const typename Pair<C>::P (&u)[3],
+                                            Terms3<C>& t) {
+  using O = Pair<C>;
+  using P = typename O::P;
+  const P g = O::fma(r, O::splat(C(3)), O::splat(C(3)));  // 3 (1 + drho)
+  P Pd[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    t.B[i] = O::mul(g, u[i]);
+    Pd[i] = O::mul(O::mul(t.B[i], u[i]), O::splat(C(1.5)));
+  }
+  const P psum = O::add(O::add(Pd[0], Pd[1]), Pd[2]);
+  t.A = O::fma(psum, O::splat(C(-1.0 / 3.0)), r);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t.S[i] = O::add(t.A, Pd[i]);
+  // 9 rho u_i u_j = (3 B_i) u_j, formed inside the fused multiply-adds
+  const P B30 = O::mul(t.B[0], O::splat(C(3)));
+  const P B31 = O::mul(t.B[1], O::splat(C(3)));
+  const P nu1 = O::sub(O::splat(C(0)), u[1]);
+  const P nu2 = O::sub(O::splat(C(0)), u[2]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 3; ++j) {
+      const int k = pair_index(i, j);
+      const P base = O::add(t.S[i], Pd[j]);
+      const P b3 = i == 0 ? B30 : B31;
+      t.Ep[k] = O::fma(b3, u[j], base);
+      t.Em[k] = O::fma(b3, j == 1 ? nu1 : nu2, base);
+      t.Op[k] = O::add(t.B[i], t.B[j]);
+      t.Om[k] = O::sub(t.B[i], t.B[j]);
+    }
+}
+
+// T_a of both lanes (axis directions undoubled: they carry the weight 2)
+template <typename C, int A>
+__device__ __forceinline__ typename Pair<C>::P term3(const Terms3<C>& t) {
+  using L = Lattice<kD3Q19>;
+  using O = Pair<C>;
+  constexpr int nzc = Dir<kD3Q19>::nz(A);
+  constexpr int i0 = Dir<kD3Q19>::first(A), i1 = Dir<kD3Q19>::second(A);
+  if constexpr (nzc == 0) {
+    return t.A;
+  } else if constexpr (nzc == 1) {
+    if constexpr (L::c(A, i0) > 0) return O::add(t.S[i0], t.B[i0]);
+    else return O::sub(t.S[i0], t.B[i0]);
+  } else {
+    constexpr int k = pair_index(i0, i1);
+    constexpr int s0 = L::c(A, i0), s1 = L::c(A, i1);
+    if constexpr (s0 == s1) {
+      if constexpr (s0 > 0) return O::add(t.Ep[k], t.Op[k]);
+      else return O::sub(t.Ep[k], t.Op[k]);
+    } else {
+      if constexpr (s0 > 0) return O::add(t.Em[k], t.Om[k]);
+      else return O::sub(t.Em[k], t.Om[k]);
+    }
+  }
+}
+
+// Constants of the weighted sums, held in registers once.
+template <typename C>
+struct Weights3 {
+  using P = typename Pair<C>::P;
+  P w12, w2, wm2;
+};
+
+// acc[0] += w36 T; acc[1 + i] += c_i w36 T
+template <typename C, int A>
+__device__ __forceinline__ void accum3(typename Pair<C>::P (&acc)[4], typename Pair<C>::P T,
+                                       const Weights3<C>& w) {
+  using L = Lattice<kD3Q19>;
+  using O = Pair<C>;
+  constexpr int wt = L::w36(A);
+  if constexpr (wt == 1) {
+    acc[0] = O::add(acc[0], T);
+    static_for<0, 3>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (L::c(A, i) == 1) acc[1 + i] = O::add(acc[1 + i], T);
+      else if constexpr (L::c(A, i) == -1) acc[1 + i] = O::sub(acc[1 + i], T);
+    });
+  } else if constexpr (wt == 2) {
+    acc[0] = O::fma(w.w2, T, acc[0]);
+    static_for<0, 3>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (L::c(A, i) == 1) acc[1 + i] = O::fma(w.w2, T, acc[1 + i]);
+      else if constexpr (L::c(A, i) == -1) acc[1 + i] = O::fma(w.wm2, T, acc[1 + i]);
+    });
+  } else {
+    acc[0] = O::fma(w.w12, T, acc[0]);
+  }
+}
+
+// index of direction a among the five with the same c_y (c_y != 0)
+__host__ __device__ constexpr int rows2_ykey(int a) {
+  using F = Frame<kD3Q19>;
+  int k = 0;
+  for (int b = 0; b < a; ++b) k += F::fy(b) == F::fy(a) ? 1 : 0;
+  return k;
+}
+
+// ------------------------------------------------------------------ layout
+
+template <typename S, int BXC, int TYT>
+struct Rows2Layout {
+  static constexpr int TY = 2 * TYT;
+  static constexpr int RS = TY + 2;       // staged rows: lower halo, TY own, upper halo
+  static constexpr int YC = BXC + 1;      // units per slot row (+1: the idle lanes' column)
+  static constexpr int NSLOT = TYT + 1;   // receiving rows per sign (see step_rows2)
+  static constexpr int DIR_UNITS = NSLOT * YC;
+  static constexpr int SIGN_UNITS = 5 * DIR_UNITS;
+  static constexpr int BUF_UNITS = 2 * SIGN_UNITS;
+  static constexpr size_t y_bytes = (size_t)2 * BUF_UNITS * 16;  // two buffers of 16-byte units
+  static constexpr size_t stage_bytes = (size_t)kStages * 4 * RS * BXC * Quad<S>::BYTES;
+  static constexpr size_t smem = y_bytes + stage_bytes;
+  static constexpr int THREADS = BXC * TYT;
+  // at least eight warps per SM where shared memory allows
+  static constexpr int SMEM_BLOCKS = (int)((220 * 1024) / smem) < 1 ? 1 : (int)((220 * 1024) / smem);
+  static constexpr int WANT = 256 / THREADS < 1 ? 1 : 256 / THREADS;
+  static constexpr int MIN_BLOCKS = WANT < SMEM_BLOCKS ? WANT : SMEM_BLOCKS;
+};
+
+// ------------------------------------------------------------------ kernel
+
+template <typename S, int BXC, int TYT>
+__global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCKS)
+    step_rows2(TiledArgs ta, const S* __restrict__ in, S* __restrict__ out) {
+  using Lay = Rows2Layout<S, BXC, TYT>;
+  using C = float;
+  using O = Pair<C>;
+  using P = typename O::P;
+  using L = Lattice<kD3Q19>;
+  using F = Frame<kD3Q19>;
+  constexpr int TY = Lay::TY;
+  constexpr int RS = Lay::RS;
+  constexpr int YC = Lay::YC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();  // the previous step's writes are visible from here on
+  pdl_launch_next();
+
+  const int tx = threadIdx.x, tr = threadIdx.y;
+  const int bxr = ta.nx >> 2;  // threads per row actually used
+  const bool active = tx < bxr;
+  float4* const Y = reinterpret_cast<float4*>(smem_raw);
+
+  // columns: own, the right neighbour's (the unit a +x diagonal value goes to)
+  // and the left one's (-x); idle lanes write into the spare column BXC
+  const int col = tx;
+  const int col_r = !active ? BXC : (tx + 1 == bxr ? 0 : tx + 1);
+  const int col_l = !active ? BXC : (tx == 0 ? bxr - 1 : tx - 1);
+  const bool seam_r = tx == bxr - 1;  // +x across the seam: send lane-swapped
+  const bool seam_l = tx == 0;        // -x across the seam
+  // shuffle sources and lane swaps of the x exchange (width BXC)
+  const int src_l = tx == 0 ? bxr - 1 : tx - 1;
+  const int src_r = tx == bxr - 1 ? 0 : tx + 1;
+
+  // rows: own rows 2 tr, 2 tr + 1 of the tile; the first thread-row also
+  // stages the row below the tile, the last one the row above
+  const int row0 = blockIdx.y * TY + 2 * tr;
+  int halo = tr == 0 ? 1 : (tr == TYT - 1 ? -1 : 0);
+  int hrow = halo == 1 ? row0 - 1 : row0 + 2;
+  if (halo != 0 && (hrow < 0 || hrow >= ta.ny)) {
+    if (ta.py) hrow = (hrow + ta.ny) % ta.ny;
+    else halo = 0;  // beyond a closed y boundary: the row next to it is a wall row
+  }
+  bool row_wall[2];
+  row_wall[0] = !ta.py && row0 == 0;
+  row_wall[1] = !ta.py && row0 + 1 == ta.ny - 1;
+  const int64_t row_off = (int64_t)row0 * ta.nx + 4 * tx;
+  const int64_t halo_delta = (int64_t)(hrow - row0) * ta.nx;
+  const bool x_lo_wall = ta.wall_mode == kWallBox && !ta.px && tx == 0;
+  const bool x_hi_wall = ta.wall_mode == kWallBox && !ta.px && tx == bxr - 1;
+  const bool box_x = ta.wall_mode == kWallBox && !ta.px;
+  const bool per_node_store = ta.wall_mode == kWallMask || (x_lo_wall && x_hi_wall);
+
+  const S* ip[4];
+  S* op[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    ip[f] = in + (int64_t)f * ta.n + row_off;
+    op[f] = out + (int64_t)f * ta.n + row_off;
+  }
+  const uint8_t* mrow = ta.wall_mode == kWallMask ? ta.mask + row_off : nullptr;
+  P force[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) force[i] = O::splat(C(ta.force[i]));
+  Weights3<C> wts;
+  wts.w12 = O::splat(C(12));
+  wts.w2 = O::splat(C(2));
+  wts.wm2 = O::splat(C(-2));
+
+  const int z0 = (int)(((int64_t)blockIdx.x * ta.nplanes) / ta.nzc);
+  const int z1 = (int)(((int64_t)(blockIdx.x + 1) * ta.nplanes) / ta.nzc);
+  const int64_t ps = ta.plane_stride;
+  const int64_t nx64 = ta.nx;
+  auto plane_exists = [&](int p) { return (p >= 0 && p < ta.nplanes) || ta.pz; };
+  auto plane_mem = [&](int p) { return p < 0 ? p + ta.nplanes : (p >= ta.nplanes ? p - ta.nplanes : p); };
+  const bool zwall = !ta.pz;
+
+  // stage [kStages][4 fields][RS rows][BXC] quads; own row j at staged row
+  // 2 tr + 1 + j, the halo at 0 (below) or TY + 1 (above)
+  constexpr int QW = Quad<S>::BYTES;
+  constexpr uint32_t kFieldStride = RS * BXC * QW;
+  constexpr uint32_t kSlotStride = 4 * kFieldStride;
+  unsigned char* const stage0 = smem_raw + Lay::y_bytes + (size_t)tx * QW;
+  const uint32_t own_off = (uint32_t)(2 * tr + 1) * BXC * QW;
+  const uint32_t halo_off = (uint32_t)(halo == 1 ? 0 : TY + 1) * BXC * QW;
+  const uint32_t stage_sh = (uint32_t)__cvta_generic_to_shared(stage0);
+  const int np = z1 - z0 + 2;  // planes z0 - 1 .. z1
+  auto fetch = [&](int i) {
+    const int p = z0 - 1 + i;
+    if (i < np && active && plane_exists(p)) {
+      const int64_t off = (int64_t)plane_mem(p) * ps;
+      const uint32_t sh = stage_sh + (uint32_t)(i & (kStages - 1)) * kSlotStride + own_off;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        Quad<S>::copy(sh + f * kFieldStride, ip[f] + off);
+        Quad<S>::copy(sh + f * kFieldStride + BXC * QW, ip[f] + off + nx64);
+      }
+      if (halo != 0) {
+        const uint32_t hs = stage_sh + (uint32_t)(i & (kStages - 1)) * kSlotStride + halo_off;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) Quad<S>::copy(hs + f * kFieldStride, ip[f] + off + halo_delta);
+      }
+    }
+    cp_async_commit();
+  };
+  P st[2][4][2];
+  const unsigned char* slot_base = stage0;
+  auto take = [&](int i) {
+    cp_async_wait<kStages - 1>();
+    const int p = z0 - 1 + i;
+    const bool ok = active && plane_exists(p);
+    slot_base = stage0 + (size_t)(i & (kStages - 1)) * kSlotStride;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        if (ok) {
+          Quad<S>::lds(reinterpret_cast<const S*>(slot_base + own_off + j * BXC * QW + f * kFieldStride),
+                       st[j][f][0], st[j][f][1]);
+        } else {
+          st[j][f][0] = st[j][f][1] = O::splat(C(0));
+        }
+      }
+  };
+
+  // ---------------------------------------------------------------- one plane
+  int ybuf = 0;
+  // publish the equilibria of pair values (Ta, Tb) of direction A into the
+  // units of slot row `slot` of sign FY (receivers: the thread-row that owns
+  // that slot)
+  auto publish = [&](float4* ybase, auto dir, int slot, P Ta, P Tb) {
+    constexpr int A = decltype(dir)::value;
+    constexpr int FY = F::fy(A), FX = F::fx(A);
+    float4* const u = ybase + (FY == 1 ? 0 : Lay::SIGN_UNITS) + rows2_ykey(A) * Lay::DIR_UNITS + slot * YC;
+    if constexpr (FX == 0) {
+      u[col] = make_float4(Ta.x, Ta.y, Tb.x, Tb.y);
+    } else if constexpr (FX == 1) {
+      // receiver column c gathers (left neighbour's b, own a)
+      reinterpret_cast<float2*>(u + col)[1] = Ta;
+      const P b = seam_r ? O::swap(Tb) : Tb;
+      reinterpret_cast<float2*>(u + col_r)[0] = b;
+    } else {
+      // receiver column c gathers (own b, right neighbour's a)
+      reinterpret_cast<float2*>(u + col)[0] = Tb;
+      const P a = seam_l ? O::swap(Ta) : Ta;
+      reinterpret_cast<float2*>(u + col_l)[1] = a;
+    }
+  };
+
+  auto update = [&](auto mode, P(&ap)[2][2][4], P(&ac)[2][2][4], P(&an)[2][2][4]) {
+    constexpr int MODE = decltype(mode)::value;
+    float4* const ybase = Y + ybuf * Lay::BUF_UNITS;
+    ybuf ^= 1;
+    // x-crossing values per destination row: [row][k] +x (from pair b), -x (from pair a)
+    P xb[2][4], xa[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xb[j][k] = xa[j][k] = O::splat(C(0));
+    // ---- own rows
+    static_for<0, 2>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      Terms3<C> t[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const P u[3] = {st[j][1][q], st[j][2][q], st[j][3][q]};
+        make_terms3<C>(st[j][0][q], u, t[q]);
+      }
+      static_for<0, L::Q>([&](auto I) {
+        constexpr int a = decltype(I)::value;
+        if constexpr (mode_allows<kD3Q19, MODE>(a)) {
+          constexpr int fx = F::fx(a), fy = F::fy(a), fz = F::fz(a);
+          const P T0 = term3<C, a>(t[0]), T1 = term3<C, a>(t[1]);
+          if constexpr (fy == 0) {
+            // within the row: a -> b (+x), b -> a (-x) in the thread; the rest by shuffles
+            auto& dst = pick<fz>(ap, ac, an)[j];
+            if constexpr (fx == 0) {
+              accum3<C, a>(dst[0], T0, wts);
+              accum3<C, a>(dst[1], T1, wts);
+            } else if constexpr (fx == 1) {
+              accum3<C, a>(dst[1], T0, wts);
+              xb[j][fold_xidx(a)] = T1;
+            } else {
+              accum3<C, a>(dst[0], T1, wts);
+              xa[j][fold_xidx(a)] = T0;
+            }
+          } else if constexpr ((j == 0 && fy == 1) || (j == 1 && fy == -1)) {
+            // to the thread's other row
+            constexpr int jd = 1 - j;
+            auto& dst = pick<fz>(ap, ac, an)[jd];
+            if constexpr (fx == 0) {
+              accum3<C, a>(dst[0], T0, wts);
+              accum3<C, a>(dst[1], T1, wts);
+            } else if constexpr (fx == 1) {  // c_z = 0 here
+              accum3<C, a>(dst[1], T0, wts);
+              xb[jd][3] = T1;
+            } else {
+              accum3<C, a>(dst[0], T1, wts);
+              xa[jd][3] = T0;
+            }
+          } else {
+            // leaving the row pair: row 1 up to thread-row tr + 1 (slot tr + 1 of
+            // the +y sign), row 0 down to thread-row tr - 1 (slot tr of -y)
+            publish(ybase, I, j == 1 ? tr + 1 : tr, T0, T1);
+          }
+        }
+      });
+    });
+    // ---- halo row: its inward equilibria into the slot its neighbour reads
+    if (halo != 0) {  // idle lanes publish into their own or the spare column
+      P hs[4][2];
+      const unsigned char* hsrc = slot_base + halo_off;
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        Quad<S>::lds(reinterpret_cast<const S*>(hsrc + f * kFieldStride), hs[f][0], hs[f][1]);
+      Terms3<C> t[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const P u[3] = {hs[1][q], hs[2][q], hs[3][q]};
+        make_terms3<C>(hs[0][q], u, t[q]);
+      }
+      if (halo == 1) {
+        static_for<0, L::Q>([&](auto I) {
+          constexpr int a = decltype(I)::value;
+          if constexpr (mode_allows<kD3Q19, MODE>(a) && F::fy(a) == 1)
+            publish(ybase, I, 0, term3<C, a>(t[0]), term3<C, a>(t[1]));
+        });
+      } else {
+        static_for<0, L::Q>([&](auto I) {
+          constexpr int a = decltype(I)::value;
+          if constexpr (mode_allows<kD3Q19, MODE>(a) && F::fy(a) == -1)
+            publish(ybase, I, TYT, term3<C, a>(t[0]), term3<C, a>(t[1]));
+        });
+      }
+    }
+    // ---- x exchange by shuffles: +x into pair a from the left lane's b,
+    // -x into pair b from the right lane's a (lane-swapped across the seam)
+    static_for<0, 2>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      // c_y = 0 directions of row j, then the diagonal arriving from the other row
+      static_for<0, L::Q>([&](auto I) {
+        constexpr int a = decltype(I)::value;
+        constexpr int fx = F::fx(a), fy = F::fy(a), fz = F::fz(a);
+        constexpr bool own = fy == 0 && fx != 0;
+        constexpr bool diag = fz == 0 && fx != 0 && ((j == 1 && fy == 1) || (j == 0 && fy == -1));
+        if constexpr (mode_allows<kD3Q19, MODE>(a) && (own || diag)) {
+          constexpr int k = own ? fold_xidx(a) : 3;
+          auto& dst = pick<fz>(ap, ac, an)[j];
+          if constexpr (fx == 1) {
+            P v = fold_shfl<BXC>(xb[j][k], src_l);
+            if (seam_l) v = O::swap(v);
+            accum3<C, a>(dst[0], v, wts);
+          } else {
+            P v = fold_shfl<BXC>(xa[j][k], src_r);
+            if (seam_r) v = O::swap(v);
+            accum3<C, a>(dst[1], v, wts);
+          }
+        }
+      });
+    });
+    __syncthreads();
+    // ---- gather: row 0 the +y units of slot tr, row 1 the -y units of slot tr + 1
+    static_for<0, L::Q>([&](auto I) {
+      constexpr int a = decltype(I)::value;
+      constexpr int fy = F::fy(a), fz = F::fz(a);
+      if constexpr (mode_allows<kD3Q19, MODE>(a) && fy != 0) {
+        constexpr int j = fy == 1 ? 0 : 1;
+        const int slot = fy == 1 ? tr : tr + 1;
+        const float4 v = ybase[(fy == 1 ? 0 : Lay::SIGN_UNITS) + rows2_ykey(a) * Lay::DIR_UNITS + slot * YC + col];
+        auto& dst = pick<fz>(ap, ac, an)[j];
+        accum3<C, a>(dst[0], O::make(v.x, v.y), wts);
+        accum3<C, a>(dst[1], O::make(v.z, v.w), wts);
+      }
+    });
+  };
+
+  // ---------------------------------------------------------------- store
+  // box x-walls: the wall node's four values of the plane being stored, read
+  // from the input at the start of the step (walls never change)
+  float wv[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) wv[j][f] = 0.f;
+  const bool xwall_lane = x_lo_wall || x_hi_wall;
+  // node (x = 0 or nx - 1, row0) of field 0: in bounds for every lane
+  const S* const wall_src = in + (int64_t)row0 * ta.nx + (x_hi_wall ? ta.nx - 1 : 0);
+  auto load_walls = [&](int q) {
+    if (box_x && q >= 0 && q < ta.nplanes) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          wv[j][f] = xwall_lane ? Store<S>::from(wall_src[(int64_t)f * ta.n + (int64_t)q * ps + j * nx64]) : 0.f;
+    }
+  };
+  auto store = [&](int q, P(&acc)[2][2][4]) {
+    const bool zskip = zwall && (q == 0 || q == ta.nplanes - 1);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const bool skip = !active || row_wall[j] || zskip;
+      const int64_t off = (int64_t)q * ps + j * nx64;
+      if (per_node_store) {
+        S* const fp[4] = {op[0], op[1], op[2], op[3]};
+        store_plane<kD3Q19, S>(fp, mrow, ta, off, x_lo_wall, x_hi_wall, skip, acc[j], force);
+        continue;
+      }
+      if (skip) continue;
+      P v[4][2];
+#pragma unroll
+      for (int qq = 0; qq < 2; ++qq) {
+        const P inv = O::rcp(O::add(O::splat(C(36)), acc[j][qq][0]));
+        v[0][qq] = O::mul(acc[j][qq][0], O::splat(C(1.0 / 36.0)));
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v[1 + i][qq] = O::fma(acc[j][qq][1 + i], inv, force[i]);
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        v[f][0].x = x_lo_wall ? wv[j][f] : v[f][0].x;
+        v[f][1].y = x_hi_wall ? wv[j][f] : v[f][1].y;
+        Quad<S>::st(op[f] + off, v[f][0], v[f][1]);
+      }
+    }
+  };
+
+  P R0[2][2][4], R1[2][2][4], R2[2][2][4];
+  auto zero = [&](P(&A)[2][2][4]) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) A[j][q][k] = O::splat(C(0));
+  };
+  zero(R0);
+  zero(R1);
+  zero(R2);
+
+#pragma unroll
+  for (int i = 0; i < kStages - 1; ++i) fetch(i);
+  // first (halo) plane z0 - 1: only the equilibria moving up the march axis
+  fetch(kStages - 1);
+  take(0);
+  if (plane_exists(z0 - 1)) update(std::integral_constant<int, kFirst>{}, R0, R2, R1);
+
+  // full planes: R0, R1, R2 hold the sums of planes p - 1, p, p + 1; after
+  // plane p, p - 1 is complete and the sums move down by one plane.  The
+  // loop body is not unrolled: one copy of the two-row update keeps the code
+  // within the instruction cache (the moves cost less than the misses of a
+  // three-way unrolled body, whose copies would rename the sums instead).
+#pragma unroll 1
+  for (int p = z0; p < z1; ++p) {
+    const int i = p - z0 + 1;
+    fetch(i + kStages - 1);
+    load_walls(p - 1);
+    take(i);
+    update(std::integral_constant<int, kMid>{}, R0, R1, R2);
+    if (p - 1 >= z0) store(p - 1, R0);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          R0[j][q][k] = R1[j][q][k];
+          R1[j][q][k] = R2[j][q][k];
+          R2[j][q][k] = O::splat(C(0));
+        }
+  }
+  // last (halo) plane z1: only the equilibria moving down, into plane z1 - 1 (R0)
+  {
+    const int i = np - 1;
+    fetch(i + kStages - 1);
+    load_walls(z1 - 1);
+    take(i);
+    if (plane_exists(z1)) update(std::integral_constant<int, kLast>{}, R0, R1, R1);
+    store(z1 - 1, R0);
+  }
+  cp_async_wait<0>();
+}
+
+// Launch of the instance (bxc, tyt) for storage type S (FP32 instances in
+// step_rows2.cu, 16-bit storage in step_rows2_s16.cu).
+template <typename S>
+cudaError_t rows2_dispatch(int bxc, int tyt, const TiledArgs& ta, const void* in, void* out,
+                           cudaStream_t st, dim3 grid, int* resident);
+
+// Launch one instance.  With resident_out set,
+// only report the blocks of this shape one SM holds.
+template <typename S, int BXC, int TYT>
+cudaError_t launch_rows2_shape(const TiledArgs& ta, const void* in, void* out, cudaStream_t stream,
+                               dim3 grid, int* resident_out) {
+  auto kern = step_rows2<S, BXC, TYT>;
+  constexpr size_t smem = Rows2Layout<S, BXC, TYT>::smem;
+  static int resident_dev[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int& resident = resident_dev[dev & 63];
+  if (!resident) {
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BXC * TYT, smem);
+    if (e != cudaSuccess) return e;
+    resident = nb < 1 ? 1 : nb;
+  }
+  if (resident_out) {
+    *resident_out = resident;
+    return cudaSuccess;
+  }
+  return launch_kernel(kern, grid, dim3(BXC, TYT), smem, stream, ta.overlap, ta, static_cast<const S*>(in),
+                       static_cast<S*>(out));
+}
+
+}  // namespace maclab
