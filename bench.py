@@ -152,9 +152,11 @@ def cavity_case(n, re):
 
 # ---------------------------------------------------------------- CPU oracle leg
 
-def oracle_rate(n, re, budget_s=10.0, max_steps=None):
-    """FP64 CPU oracle MLUPS on the same cavity; steps chosen to fill ~budget_s."""
+def oracle_rate(n, re, budget_s=10.0, max_steps=None, threads=0):
+    """FP64 CPU oracle MLUPS on the same cavity, on `threads` host threads (0:
+    every core this process may use); steps chosen to fill ~budget_s."""
     from oracle import oracle as orc
+    used = orc.set_threads(threads if threads > 0 else orc.host_cores())
     case = cavity_case(n, re)
     rho, u = case.rho.copy(), case.u.copy()
     t0 = time.perf_counter()
@@ -166,7 +168,7 @@ def oracle_rate(n, re, budget_s=10.0, max_steps=None):
     t0 = time.perf_counter()
     rho, u = orc.step(case.lattice, rho, u, case.periodic, wall=case.wall_mask, nsteps=steps)
     dt = time.perf_counter() - t0
-    return case.n_fluid * steps / dt / 1e6, steps, dt
+    return case.n_fluid * steps / dt / 1e6, steps, dt, used
 
 
 # ---------------------------------------------------------------- reference arm
@@ -175,6 +177,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from oracle import oracle as orc
+    cores = orc.set_threads(orc.host_cores())
     case = cavity_case(args.side, args.re)
     rho, u = case.rho.copy(), case.u.copy()
     for _ in range(args.warmup):
@@ -187,7 +190,7 @@ def run_reference(args, rank, world):
     total = sum(times)
     value = case.n_fluid * args.steps / total / 1e6
     sample = (f"{args.steps} MacLAB steps of the {args.side}^3 D3Q19 cavity (one per benchmark "
-              f"step), FP64 CPU oracle, single thread")
+              f"step), FP64 CPU oracle on {cores} host threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -195,7 +198,7 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"3D lid-driven cavity D3Q19 {args.side}^3, Re={args.re:g}",
                    "inner_steps": 1, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -308,11 +311,14 @@ def run_ours(args, rank, world, local_rank):
         line["diagnostics"] = diagnostics_leg(M, case, prec, stream)
         if args.precision != "f64":
             line["fp64"] = fp64_leg(M, case, args, stream, flush)
-        mlups, steps, secs = oracle_rate(args.side, args.re)
+        mlups, steps, secs, cores = oracle_rate(args.side, args.re)
+        mlups1, steps1, secs1, _ = oracle_rate(args.side, args.re, budget_s=8.0, threads=1)
         line["cpu_baseline"] = {
-            "value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{steps} MacLAB steps of the same {args.side}^3 cavity from rest "
-                      f"({secs:.1f} s, FP64, single thread)"}
+                      f"({secs:.1f} s, FP64, {cores} host threads)",
+            "one_core": {"value": mlups1, "unit": "MLUPS", "cores": 1,
+                         "sample": f"{steps1} steps ({secs1:.1f} s, FP64, one thread)"}}
     solver.close()
     print(json.dumps(line), flush=True)
 
@@ -486,6 +492,20 @@ def suite_leg(M, stream):
                      "hbm_frac_algorithmic": mlups * 1e6 * bpl / (peaks()[0] * 1e9)}
         s.close()
         del case
+    # obstacle workload: 128 x 128 x 256 channel with a sphere spinning about the
+    # axis (per-node wall velocity), walls from an explicit byte mask: 32 B of
+    # state + 1 B of mask per update
+    case, field = inputs.channel3d_sphere(spin=0.01)
+    s = M.Solver.from_case(case, M.F32, stream=ctypes_stream(stream))
+    s.set_wall_state(np.ones(case.grid), field)
+    tile = s.tune()
+    ms = _timed_steps(torch, stream, s.step, 50)
+    mlups = case.n_fluid * 50 / (ms * 1e-3) / 1e6
+    out["channel3d_sphere_128x128x256"] = {
+        "mlups": mlups, "fluid_nodes": case.n_fluid, "kernel": s.kernel_tag(),
+        "tile_ty_tz": list(tile) if tile is not None else None, "bytes_per_lup": 33,
+        "hbm_frac_algorithmic": mlups * 1e6 * 33 / (peaks()[0] * 1e9)}
+    s.close()
     return out
 
 

@@ -98,7 +98,9 @@ typedef struct {
  * MACLAB_ERR_OOM, MACLAB_ERR_CUDA.  On error *out is NULL. */
 maclab_status maclab_create(const maclab_config *cfg, maclab_handle *out);
 
-/* Free the handle and its device memory (synchronises its stream). NULL is OK. */
+/* Free the handle and its device memory (synchronises its stream). NULL is OK.
+ * No paper counterpart: the end of the procedure after Eq. (6) (step (v):
+ * repeat until a solution is reached) leaves the owner to release the state. */
 maclab_status maclab_destroy(maclab_handle h);
 
 /* out[0] = e (Eq. (6)), out[1] = dt = dx / e, out[2] = lattice Reynolds number
@@ -107,8 +109,11 @@ maclab_status maclab_destroy(maclab_handle h);
 maclab_status maclab_params(maclab_handle h, double out[8]);
 
 /* Set the state from physical fields: rho (N values) and u (d * N values) of
- * the given dtype, in host or device memory.  Wall nodes are overwritten with
- * their wall id's values.  Resets the step counter.  Host buffers that are
+ * the given dtype, in host or device memory -- step (i) of the procedure after
+ * Eq. (6), the initial rho and u, stored in lattice units (u / e with e from
+ * Eq. (6), rho / rho0).  Wall nodes are overwritten with their wall id's
+ * values (the physical variables retained on walls, Tests 1-3 and 5).  Resets
+ * the step counter.  Host buffers that are
  * page-locked and mapped for the handle's device (cudaHostAlloc,
  * cudaHostRegister) are read by the conversion kernel directly; other host
  * memory goes through a device staging buffer.  Either way the call returns
@@ -116,7 +121,9 @@ maclab_status maclab_params(maclab_handle h, double out[8]);
 maclab_status maclab_set_state(maclab_handle h, const void *rho, const void *u,
                                int32_t where, int32_t dtype);
 
-/* Read the current physical state into rho (N) and u (d * N).  Synchronises.
+/* Read the current physical state into rho (N) and u (d * N): the macroscopic
+ * variables of Eqs. (4)-(5) mapped back to physical units (u = e ut,
+ * rho = rho0 (1 + drho)).  Synchronises.
  * Page-locked host buffers mapped for the device are written by the
  * conversion kernel directly, other host memory through a staging buffer. */
 maclab_status maclab_get_state(maclab_handle h, void *rho, void *u, int32_t where,

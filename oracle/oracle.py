@@ -187,13 +187,15 @@ def rollout_adjoint(lattice, rho0, u0, periodic, nsteps, lam_rho_T, lam_u_T, wal
     """Reverse-mode gradient of an n-step rollout.
 
     Returns (lam_rho_0, lam_u_0, grad_force) for a loss whose adjoint on the
-    final state is (lam_rho_T, lam_u_T).  checkpoint_every=None stores every
+    final state is (lam_rho_T, lam_u_T).  lam_rho_T may instead be a function
+    of the final state, (rho_T, u_T) -> (lam_rho_T, lam_u_T) (lam_u_T is then
+    ignored), for a loss on the state the forward pass reaches.
+    checkpoint_every=None stores every
     state; an integer K keeps only the states of steps 0, K, 2K, ... and
     recomputes each segment's states from its checkpoint when the reverse pass
     reaches it (the forward step is deterministic, so the states and the
     result are the same).  gather: see ``adjoint_step``.
     """
-    lr, lu = _f64(lam_rho_T), _f64(lam_u_T)
     gf = np.zeros(DIMS[lattice])
     k = nsteps if not checkpoint_every else max(1, int(checkpoint_every))
     checkpoints = {0: (_f64(rho0), _f64(u0))}
@@ -202,6 +204,9 @@ def rollout_adjoint(lattice, rho0, u0, periodic, nsteps, lam_rho_T, lam_u_T, wal
         state = step(lattice, *state, periodic, wall=wall, force=force)
         if s % k == 0 and s < nsteps:
             checkpoints[s] = state
+    if callable(lam_rho_T):
+        lam_rho_T, lam_u_T = lam_rho_T(*state)
+    lr, lu = _f64(lam_rho_T), _f64(lam_u_T)
     for start in sorted(checkpoints, reverse=True):
         stop = min(start + k, nsteps)
         seg = [checkpoints[start]]
