@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--kernel", default="auto", choices=["auto", "reference", "tiled", "folded", "segment", "rows2"])
     p.add_argument("--ty", type=int, default=0, help="tiled kernel: rows per tile (0 = default)")
     p.add_argument("--tz", type=int, default=0, help="tiled kernel: planes per block (0 = default)")
+    p.add_argument("--replicas", action="store_true",
+                   help="N > 1: independent replicas instead of one domain split into slabs")
+    p.add_argument("--halo", type=int, default=8, help="N > 1 slabs: ghost planes per side (exchange period)")
     p.add_argument("--leg", default="main", choices=["main", "adjoint", "batch", "lbm", "diag"],
                    help="adjoint / batch: run only that leg and print its JSON (for profiling)")
     return p.parse_args()
@@ -204,6 +207,82 @@ def run_reference(args, rank, world):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm, N > 1
+
+def run_slabs(args, rank, world, local_rank):
+    """One 128^3-per-rank cavity of 128 x 128 x (128 N) nodes split into N slabs
+    along z (weak scaling): every rank steps its slab with the library and
+    swaps `--halo` ghost planes with its neighbours over NCCL every `--halo`
+    steps.  value = fluid updates of the whole domain / max-over-ranks time."""
+    import torch
+    import torch.distributed as dist
+    from paper_1901_02716_gb300 import _build, inputs, slabs
+    from paper_1901_02716_gb300 import maclab as M
+
+    torch.cuda.set_device(local_rank)
+    if not os.path.exists(M.library_path()):
+        _build.build()
+    prec = M.PRECISION_NAMES[args.precision]
+    case = inputs.cavity3d(args.side, lid=inputs.lid_speed(args.re, args.side), nz=args.side * world)
+    stream = torch.cuda.current_stream()
+    sl = slabs.DistributedSlab(case, lambda sub: slabs.SolverStepper(sub, prec), depth=args.halo)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        sl.step(args.inner)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    per = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sl.step(args.inner)
+        b.record(stream)
+        torch.cuda.synchronize()
+        per.append(a.elapsed_time(b))
+    dist_barrier(world)
+    clocks = sampler.stop() if sampler else None
+    total_ms = dist_max(sum(per), world)
+    value = case.n_fluid * args.inner * args.steps / (total_ms * 1e-3) / 1e6
+    # end to end: each rank's slab state in from and out to pinned host buffers every step
+    sub = sl.sub
+    rho_h = torch.from_numpy(sub.rho.astype(np.float32)).pin_memory()
+    u_h = torch.from_numpy(sub.u.astype(np.float32)).pin_memory()
+    s = sl.stepper.solver
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    t0 = time.perf_counter()
+    k = max(2, min(args.steps, 5))
+    for _ in range(k):
+        s.set_state(rho_h.numpy(), u_h.numpy())
+        sl.exchange()
+        sl.step(args.inner)
+        s.get_state_into(rho_h.numpy(), u_h.numpy())
+    e2e_s = dist_max(time.perf_counter() - t0, world)
+    nbytes = (rho_h.numel() + u_h.numel()) * 4
+    kinfo = s.kernel_info()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"3D lid-driven cavity D3Q19 {args.side}x{args.side}x{args.side * world} "
+                                   f"(walls included), Re={args.re:g}, {args.precision} storage",
+                       "inner_steps": args.inner, "fluid_nodes": case.n_fluid,
+                       "l2": "flushed (256 MiB write) before each timed step",
+                       "parallelism": f"slabs x{world} along z, {args.halo} ghost planes per side, NCCL"},
+            "gpu_launches": int(s.launches_per_step() * args.inner * args.steps),
+            "kernel": kinfo["name"], "clocks": clocks,
+            "e2e": {"value": case.n_fluid * args.inner * k / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": nbytes * world, "d2h_bytes_per_step": nbytes * world},
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
 
 
 # ---------------------------------------------------------------- our arm
@@ -609,6 +688,8 @@ def main():
     rank, world, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif world > 1 and not args.replicas:
+        run_slabs(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

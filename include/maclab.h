@@ -121,6 +121,20 @@ maclab_status maclab_params(maclab_handle h, double out[8]);
 maclab_status maclab_set_state(maclab_handle h, const void *rho, const void *u,
                                int32_t where, int32_t dtype);
 
+/* Per-node wall values: every wall node takes the physical (rho, u) given at
+ * its position in rho (N values) and u (d * N values, logical order, same
+ * layout, dtype and host/device rules as maclab_set_state); entries at fluid
+ * nodes are not read.  Wall nodes keep these values through every step: the
+ * paper retains the physical variables on walls with no calculation there
+ * (the boundary treatment of Tests 1-3 and 5), and this extends the per-id
+ * table of maclab_config to any field over the walls (a moving or curved
+ * body, an inflow profile).  Written into both state buffers; may be called
+ * between steps (the step counter is kept).  maclab_set_state afterwards puts
+ * the id table's values back.  A handle without wall nodes ignores the call.
+ * Errors: MACLAB_ERR_INVALID, MACLAB_ERR_OOM (host staging), MACLAB_ERR_CUDA. */
+maclab_status maclab_set_wall_state(maclab_handle h, const void *rho, const void *u,
+                                    int32_t where, int32_t dtype);
+
 /* Read the current physical state into rho (N) and u (d * N): the macroscopic
  * variables of Eqs. (4)-(5) mapped back to physical units (u = e ut,
  * rho = rho0 (1 + drho)).  Synchronises.
@@ -215,6 +229,33 @@ maclab_status maclab_kernel_info(maclab_handle h, int32_t out[4], const char **n
  * (Eq. (15)).  Synchronises the stream.  Returns MACLAB_ERR_NONFINITE (with
  * out filled) if out[7] > 0. */
 maclab_status maclab_diagnostics(maclab_handle h, double out[8]);
+
+/* The same reduction as raw FP64 sums over the fluid nodes, in lattice units,
+ * so that the diagnostics of several sub-domains (maclab_get_planes) can be
+ * added up exactly: out[0] sum drho, out[1] sum rho |u|^2, out[2..4] sum
+ * rho u_i, out[5] sum |u - u_prev|^2 and out[6] sum |u|^2 (both -1 when the
+ * previous state is not held), out[7] max |u|, out[8] non-finite count (the
+ * layout of maclab_diagnostics_noalloc).  Mass and momentum are the
+ * invariants of Eq. (15).  Synchronises the stream. */
+maclab_status maclab_diagnostics_sums(maclab_handle h, double out[9]);
+
+/* Raw planes of the march axis (z in 3D, y in 2D) of the current lattice
+ * state, for decomposing a domain into slabs along that axis.  A slab is a
+ * domain closed along the axis whose first and last planes are wall nodes
+ * (never computed into, Tests 1-3 and 5: values retained) that hold copies of
+ * the neighbouring slabs' edge planes: the one-layer ghost exchange of a
+ * radius-1 stencil (every c_a has |c_a,z| <= 1 in Eqs. (4)-(5)).
+ * maclab_get_planes copies planes [p0, p0 + count) of every field into dst
+ * laid out [field][plane][stored values of a plane] (storage order, storage
+ * type); maclab_set_planes writes src (same layout) into them.  where:
+ * MACLAB_HOST or MACLAB_DEVICE (a device buffer may be on another device with
+ * peer access).  One copy per field on the handle's stream; with host buffers
+ * the call synchronises.  set_planes changes the current state only: the
+ * residual of maclab_diagnostics compares it with the previous step's state as
+ * that is held (ghost planes are walls and take no part).  Errors: MACLAB_ERR_INVALID (range, where),
+ * MACLAB_ERR_CUDA. */
+maclab_status maclab_get_planes(maclab_handle h, int64_t p0, int64_t count, void *dst, int32_t where);
+maclab_status maclab_set_planes(maclab_handle h, int64_t p0, int64_t count, const void *src, int32_t where);
 
 /* Capture maclab_step's launches in CUDA graphs of `steps` time steps each
  * (rounded up to an even count; 0 turns graphs off, the default is 32).

@@ -427,6 +427,41 @@ maclab_status maclab_set_state(maclab_handle h, const void* rho, const void* u, 
   return MACLAB_OK;
 }
 
+maclab_status maclab_set_wall_state(maclab_handle h, const void* rho, const void* u, int32_t where,
+                                    int32_t dtype) {
+  NvtxRange nvtx_range("maclab_set_wall_state");
+  if (!h || !rho || !u) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (dtype != MACLAB_DTYPE_F64 && dtype != MACLAB_DTYPE_F32)
+    return fail(MACLAB_ERR_INVALID, "dtype must be F64 or F32");
+  if (where != MACLAB_HOST && where != MACLAB_DEVICE) return fail(MACLAB_ERR_INVALID, "bad where");
+  if (!h->d_node_type) return MACLAB_OK;  // no wall nodes
+  DeviceGuard dg(h->device);
+  const size_t es = dtype == MACLAB_DTYPE_F64 ? 8 : 4;
+  const size_t nb = (size_t)h->g.n * es;
+  const void* r = rho;
+  const void* v = u;
+  const void* pr = where == MACLAB_HOST ? pinned_device_ptr(rho, h->device) : nullptr;
+  const void* pu = pr ? pinned_device_ptr(u, h->device) : nullptr;
+  if (pr && pu) {
+    r = pr;
+    v = pu;
+  } else if (where == MACLAB_HOST) {
+    maclab_status s = ensure_staging(h, nb * (h->g.d + 1));
+    if (s != MACLAB_OK) return s;
+    char* st = (char*)h->d_staging;
+    CUDA_TRY(cudaMemcpyAsync(st, rho, nb, cudaMemcpyHostToDevice, h->stream), "set_wall_state H2D");
+    CUDA_TRY(cudaMemcpyAsync(st + nb, u, nb * h->g.d, cudaMemcpyHostToDevice, h->stream),
+             "set_wall_state H2D");
+    r = st;
+    v = st + nb;
+  }
+  CUDA_TRY(launch_set_wall_values(h->g, h->precision, r, v, dtype, h->rho0, h->e, h->d_node_type,
+                                  h->buf[0], h->buf[1], h->stream),
+           "set_wall_state kernel");
+  if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "set_wall_state sync");
+  return MACLAB_OK;
+}
+
 maclab_status maclab_get_state(maclab_handle h, void* rho, void* u, int32_t where, int32_t dtype) {
   NvtxRange nvtx_range("maclab_get_state");
   if (!h || !rho || !u) return fail(MACLAB_ERR_INVALID, "NULL argument");
@@ -768,6 +803,63 @@ maclab_status maclab_diagnostics(maclab_handle h, double out[8]) {
   out[6] = r[7];
   out[7] = r[8];
   if (r[8] > 0) return fail(MACLAB_ERR_NONFINITE, "non-finite values in the state");
+  return MACLAB_OK;
+}
+
+maclab_status maclab_diagnostics_sums(maclab_handle h, double out[9]) {
+  NvtxRange nvtx_range("maclab_diagnostics_sums");
+  if (!h || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  DeviceGuard dg(h->device);
+  CUDA_TRY(launch_diagnostics(h->g, h->precision, h->buf[h->cur],
+                              h->prev_valid ? h->buf[h->cur ^ 1] : nullptr, h->d_partial,
+                              h->diag_nblocks, h->d_diag, h->stream),
+           "diagnostics kernel");
+  CUDA_TRY(cudaMemcpyAsync(out, h->d_diag, kDiagOut * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+           "diagnostics D2H");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "diagnostics sync");
+  if (!h->prev_valid) out[5] = out[6] = -1.0;
+  return MACLAB_OK;
+}
+
+// Planes of the march axis (z in 3D, y in 2D) of the current state: plane p of
+// field f is the contiguous run of plane_size stored values at f * N + p * plane_size.
+static maclab_status planes_args(maclab_ctx* h, int64_t p0, int64_t count, const void* buf, int32_t where,
+                                 size_t* plane_bytes) {
+  if (!h || !buf) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (where != MACLAB_HOST && where != MACLAB_DEVICE) return fail(MACLAB_ERR_INVALID, "bad where");
+  const int64_t np = h->g.d == 3 ? h->g.nz : h->g.ny;
+  if (count < 1 || p0 < 0 || p0 + count > np) return fail(MACLAB_ERR_INVALID, "plane range outside the domain");
+  *plane_bytes = (size_t)(h->g.n / np) * h->elem;
+  return MACLAB_OK;
+}
+
+maclab_status maclab_get_planes(maclab_handle h, int64_t p0, int64_t count, void* dst, int32_t where) {
+  NvtxRange nvtx_range("maclab_get_planes");
+  size_t pb = 0;
+  maclab_status s = planes_args(h, p0, count, dst, where, &pb);
+  if (s != MACLAB_OK) return s;
+  DeviceGuard dg(h->device);
+  const size_t field = (size_t)h->g.n * h->elem;
+  for (int f = 0; f <= h->g.d; ++f)
+    CUDA_TRY(cudaMemcpyAsync((char*)dst + f * count * pb, (const char*)h->buf[h->cur] + f * field + p0 * pb,
+                             count * pb, cudaMemcpyDefault, h->stream),
+             "get_planes copy");
+  if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "get_planes sync");
+  return MACLAB_OK;
+}
+
+maclab_status maclab_set_planes(maclab_handle h, int64_t p0, int64_t count, const void* src, int32_t where) {
+  NvtxRange nvtx_range("maclab_set_planes");
+  size_t pb = 0;
+  maclab_status s = planes_args(h, p0, count, src, where, &pb);
+  if (s != MACLAB_OK) return s;
+  DeviceGuard dg(h->device);
+  const size_t field = (size_t)h->g.n * h->elem;
+  for (int f = 0; f <= h->g.d; ++f)
+    CUDA_TRY(cudaMemcpyAsync((char*)h->buf[h->cur] + f * field + p0 * pb, (const char*)src + f * count * pb,
+                             count * pb, cudaMemcpyDefault, h->stream),
+             "set_planes copy");
+  if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "set_planes sync");
   return MACLAB_OK;
 }
 

@@ -231,6 +231,9 @@ cudaError_t launch_set_physical(const Geometry& g, int precision, const void* rh
 cudaError_t launch_get_physical(const Geometry& g, int precision, const void* state,
                                 void* rho, void* u, int dtype, double rho0, double e,
                                 cudaStream_t stream);
+cudaError_t launch_set_wall_values(const Geometry& g, int precision, const void* rho, const void* u,
+                                   int dtype, double rho0, double e, const uint8_t* node_type, void* s0,
+                                   void* s1, cudaStream_t stream);
 cudaError_t launch_fill_walls(const Geometry& g, int precision, const uint8_t* node_type,
                               const double* wall_lat, int n_wall_ids, void* state,
                               cudaStream_t stream);

@@ -60,6 +60,29 @@ __global__ void fill_walls_k(int d, int64_t N, const uint8_t* __restrict__ node_
   }
 }
 
+// Per-node wall values: every wall node (node type > 0) takes the given
+// physical (rho, u), in both state buffers (the step kernels never write a
+// wall node, so whichever buffer is current reads them); fluid entries of the
+// arrays are not read.
+template <typename S, typename T>
+__global__ void set_walls_k(Geometry g, int d, int64_t N, const T* __restrict__ rho, const T* __restrict__ u,
+                            double inv_rho0, double inv_e, const uint8_t* __restrict__ node_type,
+                            S* __restrict__ s0, S* __restrict__ s1) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = storage_index(g, j);
+    if (node_type[i] == 0) continue;
+    const S r = Store<S>::to(typename Store<S>::C(ld_user(rho, j) * inv_rho0 - 1.0));
+    s0[i] = r;
+    s1[i] = r;
+    for (int c = 0; c < d; ++c) {
+      const S v = Store<S>::to(typename Store<S>::C(ld_user(u, c * N + j) * inv_e));
+      s0[(1 + c) * N + i] = v;
+      s1[(1 + c) * N + i] = v;
+    }
+  }
+}
+
 template <typename S, typename T>
 __global__ void get_physical_k(Geometry g, int d, int64_t N, const S* __restrict__ state, double rho0,
                                double e, T* __restrict__ rho, T* __restrict__ u) {
@@ -122,6 +145,31 @@ cudaError_t launch_get_physical(const Geometry& g, int precision, const void* st
     case MACLAB_F32: return get_t<float>(g, state, rho, u, dtype, rho0, e, st);
     case MACLAB_BF16_STORE: return get_t<__nv_bfloat16>(g, state, rho, u, dtype, rho0, e, st);
     case MACLAB_F16_STORE: return get_t<__half>(g, state, rho, u, dtype, rho0, e, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename S>
+static cudaError_t walls_t(const Geometry& g, const void* rho, const void* u, int dtype, double rho0,
+                           double e, const uint8_t* nt, void* s0, void* s1, cudaStream_t st) {
+  if (dtype == MACLAB_DTYPE_F64)
+    set_walls_k<S, double><<<grid_for(g.n), 256, 0, st>>>(g, g.d, g.n, (const double*)rho, (const double*)u,
+                                                         1.0 / rho0, 1.0 / e, nt, (S*)s0, (S*)s1);
+  else
+    set_walls_k<S, float><<<grid_for(g.n), 256, 0, st>>>(g, g.d, g.n, (const float*)rho, (const float*)u,
+                                                        1.0 / rho0, 1.0 / e, nt, (S*)s0, (S*)s1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_wall_values(const Geometry& g, int precision, const void* rho, const void* u,
+                                   int dtype, double rho0, double e, const uint8_t* nt, void* s0,
+                                   void* s1, cudaStream_t st) {
+  if (!nt) return cudaSuccess;
+  switch (precision) {
+    case MACLAB_F64: return walls_t<double>(g, rho, u, dtype, rho0, e, nt, s0, s1, st);
+    case MACLAB_F32: return walls_t<float>(g, rho, u, dtype, rho0, e, nt, s0, s1, st);
+    case MACLAB_BF16_STORE: return walls_t<__nv_bfloat16>(g, rho, u, dtype, rho0, e, nt, s0, s1, st);
+    case MACLAB_F16_STORE: return walls_t<__half>(g, rho, u, dtype, rho0, e, nt, s0, s1, st);
   }
   return cudaErrorInvalidValue;
 }

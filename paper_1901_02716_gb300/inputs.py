@@ -166,20 +166,23 @@ def cavity2d(n=256, lid=0.1, nx=None):
     return Case(D2Q9, (nx, ny), 0, rho, u, nt, wall_rho, wall_u, name=f"cavity2d-{nx}x{ny}")
 
 
-def cavity3d(n=128, lid=0.1):
-    """Test 5 set-up: closed D3Q19 cube; walls id 1, lid id 2 on z = n - 1 moving +x.
+def cavity3d(n=128, lid=0.1, nz=None):
+    """Test 5 set-up: closed D3Q19 box (a cube unless nz is given); walls id 1,
+    lid id 2 on z = nz - 1 moving +x.
 
     The lid holds the top-face nodes strictly inside the four side walls.
     """
-    nt = np.zeros((n, n, n), dtype=np.uint8)
+    nz = nz or n
+    nt = np.zeros((nz, n, n), dtype=np.uint8)
     nt[0], nt[-1] = 1, 1
     nt[:, 0, :], nt[:, -1, :] = 1, 1
     nt[:, :, 0], nt[:, :, -1] = 1, 1
     nt[-1, 1:-1, 1:-1] = 2
     wall_rho = np.array([1.0, 1.0])
     wall_u = np.array([[0.0, 0.0, 0.0], [lid, 0.0, 0.0]])
-    rho, u = place_walls(np.ones((n, n, n)), np.zeros((3, n, n, n)), nt, wall_rho, wall_u)
-    return Case(D3Q19, (n, n, n), 0, rho, u, nt, wall_rho, wall_u, name=f"cavity3d-{n}")
+    rho, u = place_walls(np.ones((nz, n, n)), np.zeros((3, nz, n, n)), nt, wall_rho, wall_u)
+    name = f"cavity3d-{n}" if nz == n else f"cavity3d-{n}x{n}x{nz}"
+    return Case(D3Q19, (n, n, nz), 0, rho, u, nt, wall_rho, wall_u, name=name)
 
 
 def channel2d(nx=20, ny=51, u_top=0.1, force_x=0.0):
@@ -203,3 +206,38 @@ def batch_cavity_sides(count=64, seed=4):
     re = np.exp(g.uniform(math.log(100.0), math.log(3200.0), size=count))
     lids = np.minimum([lid_speed(r, int(s)) for r, s in zip(re, sides)], 1.0 / 6.0)
     return [int(s) for s in sides], [float(r) for r in re], [float(v) for v in lids]
+
+
+def channel3d_sphere(nx=128, ny=128, nz=256, radius=None, force_z=1e-5, spin=0.0):
+    """Obstacle workload: a D3Q19 channel along z (periodic in z) with no-slip
+    side walls (id 1) at x = 0, nx - 1 and y = 0, ny - 1, and a sphere of nodes
+    (id 2) centred in the channel a quarter of the way along z, driven by a
+    body-force increment force_z along z (lattice units).
+
+    spin != 0 gives the sphere a per-node wall velocity: rotation about the
+    channel axis at angular rate spin (lattice units per lattice spacing), i.e.
+    u = spin * (-(y - yc), x - xc, 0) on its nodes.  Returns (case, wall_u_field):
+    wall_u_field is None without spin, else a [3, nz, ny, nx] velocity field
+    that is nonzero only on the sphere's nodes (for per-node wall values).
+    """
+    radius = radius if radius is not None else min(nx, ny) / 8.0
+    xc, yc, zc = (nx - 1) / 2.0, (ny - 1) / 2.0, nz / 4.0
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    nt = np.zeros((nz, ny, nx), dtype=np.uint8)
+    nt[:, 0, :] = nt[:, -1, :] = 1
+    nt[:, :, 0] = nt[:, :, -1] = 1
+    sphere = (x - xc) ** 2 + (y - yc) ** 2 + (z - zc) ** 2 <= radius * radius
+    nt[sphere & (nt == 0)] = 2
+    wall_rho = np.array([1.0, 1.0])
+    wall_u = np.zeros((2, 3))
+    rho, u = place_walls(np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)), nt, wall_rho, wall_u)
+    field = None
+    if spin != 0.0:
+        field = np.zeros((3, nz, ny, nx))
+        on = nt == 2
+        field[0][on] = -spin * (y[on] - yc)
+        field[1][on] = spin * (x[on] - xc)
+        u = np.where(on[None], field, u)
+    case = Case(D3Q19, (nx, ny, nz), 0b100, rho, u, nt, wall_rho, wall_u,
+                force=(0.0, 0.0, force_z), name=f"channel3d-sphere-{nx}x{ny}x{nz}")
+    return case, field

@@ -63,6 +63,10 @@ SIGNATURES = {
     "maclab_params": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
     "maclab_set_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
     "maclab_get_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
+    "maclab_set_wall_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
+    "maclab_diagnostics_sums": (_S, [_H, _VP]),
+    "maclab_get_planes": (_S, [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int32]),
+    "maclab_set_planes": (_S, [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int32]),
     "maclab_state_bytes": (_S, [_H, ctypes.POINTER(ctypes.c_size_t)]),
     "maclab_get_lattice_state": (_S, [_H, _VP, ctypes.c_int32]),
     "maclab_set_lattice_state": (_S, [_H, _VP, ctypes.c_int32]),
@@ -207,6 +211,17 @@ def maclab_set_state(h, rho, u):
     return _check(lib().maclab_set_state(h, pr, pu, wr, dt), "maclab_set_state")
 
 
+def maclab_set_wall_state(h, rho, u):
+    pr, wr = _ptr(rho)
+    pu, wu = _ptr(u)
+    if wr != wu:
+        raise ValueError("rho and u must live in the same memory")
+    dt = _dtype_code(rho)
+    if _dtype_code(u) != dt:
+        raise ValueError("rho and u must have the same dtype")
+    return _check(lib().maclab_set_wall_state(h, pr, pu, wr, dt), "maclab_set_wall_state")
+
+
 def maclab_get_state(h, rho, u):
     pr, wr = _ptr(rho)
     pu, wu = _ptr(u)
@@ -265,6 +280,22 @@ def maclab_diagnostics(h, raise_nonfinite=True):
         _check(s, "maclab_diagnostics")
     return {"mass": out[0], "kinetic": out[1], "momentum": list(out[2:5]), "residual": out[5],
             "max_u_lattice": out[6], "nonfinite": int(out[7]), "status": s}
+
+
+def maclab_diagnostics_sums(h):
+    out = (ctypes.c_double * 9)()
+    _check(lib().maclab_diagnostics_sums(h, out), "maclab_diagnostics_sums")
+    return list(out)
+
+
+def maclab_get_planes(h, p0, count, dst):
+    p, w = _ptr(dst)
+    return _check(lib().maclab_get_planes(h, int(p0), int(count), p, w), "maclab_get_planes")
+
+
+def maclab_set_planes(h, p0, count, src):
+    p, w = _ptr(src)
+    return _check(lib().maclab_set_planes(h, int(p0), int(count), p, w), "maclab_set_planes")
 
 
 def maclab_diagnostics_noalloc(lattice, precision, n_nodes, state, prev_state, exclude, out_sums,
@@ -454,6 +485,10 @@ class Solver:
 
     def set_state(self, rho, u):
         maclab_set_state(self.handle, rho, u)
+
+    def set_wall_state(self, rho, u):
+        """Per-node wall values (physical; fluid entries ignored)."""
+        maclab_set_wall_state(self.handle, rho, u)
 
     def get_state(self, dtype=np.float64):
         rho = np.empty(self.grid, dtype=dtype)
