@@ -353,6 +353,24 @@ maclab_status maclab_adjoint_bytes(maclab_handle h, size_t *bytes);
 maclab_status maclab_adjoint_step(maclab_handle h, const void *state_n, const void *state_np1,
                                   const void *lam_np1, void *lam_n, double *grad_force);
 
+/* The viscosity term of one reverse step: *acc (device, one double,
+ * accumulated) += sum over fluid nodes x of lam_np1(x) . D_n(x), where state_n
+ * is the raw state a maclab_step consumed and lam_np1 the adjoint of the state
+ * it produced.  nu enters a rollout only through the particle speed e = 6 nu
+ * / dx of Eq. (6) (initial and wall velocities u / e, force increment g dt / e,
+ * output u = e ut; the update of Eqs. (4)-(5) itself does not depend on e), and
+ * D_n is the defect of one step under that scaling: with ut'_nf = m' / rho'
+ * the output without the force F and J (0, ut) the step's derivative along the
+ * velocities, D_n = (ut'_nf - J (0, ut) - F, -J (0, ut) on drho).  Summed over
+ * the steps of a rollout, e dL/de = sum_n sum_x lam_(n+1) . D_n, so
+ * dL/dnu = (6 / dx) (1 / e) sum; each term is formed directly, without the
+ * near-cancellation of the end-point products that maclab_adjoint_finish
+ * subtracts (which loses accuracy in FP32 when the flow is nearly linear in u).
+ * Asynchronous on the handle's stream.  Errors: MACLAB_ERR_INVALID,
+ * MACLAB_ERR_CUDA. */
+maclab_status maclab_adjoint_nu_term(maclab_handle h, const void *state_n, const void *lam_np1,
+                                     double *acc);
+
 /* Seed the reverse pass: the gradients of the loss with respect to the
  * physical output fields rho (N values) and u (d * N values, logical order;
  * either may be NULL = zero) of dtype, for the raw final state state_T, give
@@ -439,6 +457,16 @@ maclab_status maclab_check_reciprocal(float lo, float hi, int32_t n, double *max
  * call.  Errors: MACLAB_ERR_INVALID (NULL tflops), MACLAB_ERR_OOM,
  * MACLAB_ERR_CUDA. */
 maclab_status maclab_measure_fp32_peak(double *tflops);
+
+/* Debug builds only (compiled with -DMACLAB_BOUNDS_CHECK, libmaclab_bounds.so):
+ * the number of out-of-bounds indices the checked kernels met on the current
+ * device since the last call (out[0]) and the first such index (out[1]); the
+ * log is cleared.  The checked kernels (the D3Q19 two-rows-per-thread step)
+ * compare every global and shared-memory index with the size of its buffer
+ * and skip a bad access instead of making it; nothing traps.  No paper
+ * counterpart (a verification aid).  Synchronises the device.  Errors:
+ * MACLAB_ERR_UNSUPPORTED in normal builds, MACLAB_ERR_INVALID, MACLAB_ERR_CUDA. */
+maclab_status maclab_debug_bounds(int64_t out[2]);
 
 /* Run the handle's stream to completion and report any CUDA error. */
 maclab_status maclab_sync(maclab_handle h);

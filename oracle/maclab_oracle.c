@@ -421,3 +421,67 @@ int oracle_adjoint_step_gather(int lattice, int64_t nx, int64_t ny, int64_t nz,
     free(lm);
     return ORACLE_OK;
 }
+
+/*
+ * The viscosity term of one reverse step.  Not in the paper: the chain rule of
+ * the particle speed of Eq. (6).  nu enters a rollout only through
+ * e = 6 nu / dx: initial and wall velocities are u / e in lattice units, the
+ * force increment is g dx / e^2, the output velocity is e ut, and Eqs. (4)-(5)
+ * themselves do not depend on e.  For one step from the state (rho, ut) this
+ * returns sum over fluid nodes x of
+ *     lam_rho_next(x) D_rho(x) + lam_u_next(x) . D_u(x),
+ *     D_rho = -drho',  D_u = m'/rho' - (dm'/rho' - m' drho' / rho'^2) - force,
+ * where rho', m' are the sums of Eqs. (4)-(5) and drho', dm' the same sums of
+ * dF_a = d/d(eps) f_a^eq(rho, (1 + eps) ut) at eps = 0
+ *      = w_a rho (3 c.ut + 9 (c.ut)^2 - 3 ut.ut).
+ * Summed over the steps of a rollout with lam_next the adjoint of the state the
+ * step produced, it gives e dL/de.  *status: ORACLE_OK or an error code.
+ */
+double oracle_nu_term(int lattice, int64_t nx, int64_t ny, int64_t nz, uint32_t periodic,
+                      const uint8_t *wall, const double *rho, const double *u, const double *force,
+                      const double *lam_rho_next, const double *lam_u_next, int *status) {
+    lattice_t L;
+    *status = ORACLE_OK;
+    if (get_lattice(lattice, &L) || nx < 1 || ny < 1 || nz < 1 || (L.d == 2 && nz != 1)) {
+        *status = ORACLE_BAD_ARG;
+        return 0.0;
+    }
+    const int64_t n[3] = {nx, ny, nz};
+    const int64_t N = nx * ny * nz;
+    double total = 0.0;
+    for (int64_t node = 0; node < N; ++node) {
+        if (wall && wall[node]) continue;
+        const int64_t x[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+        double r = 0.0, m[3] = {0.0, 0.0, 0.0}, dr = 0.0, dm[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < L.q; ++a) {
+            int64_t y[3] = {0, 0, 0};
+            for (int i = 0; i < 3; ++i) {
+                y[i] = upstream(x[i], L.c[a][i], n[i], (periodic >> i) & 1u);
+                if (y[i] < 0) { *status = ORACLE_OUTSIDE; return 0.0; }
+            }
+            const int64_t src = (y[2] * ny + y[1]) * nx + y[0];
+            double ut[3] = {0.0, 0.0, 0.0}, cu = 0.0, uu = 0.0;
+            for (int i = 0; i < L.d; ++i) {
+                ut[i] = u[i * N + src];
+                cu += (double)L.c[a][i] * ut[i];
+                uu += ut[i] * ut[i];
+            }
+            const double f = feq(&L, a, rho[src], ut);
+            const double df = L.w[a] * rho[src] * (3.0 * cu + 9.0 * cu * cu - 3.0 * uu);
+            r += f;
+            dr += df;
+            for (int i = 0; i < L.d; ++i) {
+                m[i] += (double)L.c[a][i] * f;
+                dm[i] += (double)L.c[a][i] * df;
+            }
+        }
+        double t = -lam_rho_next[node] * dr;
+        for (int i = 0; i < L.d; ++i) {
+            const double du = dm[i] / r - m[i] * dr / (r * r);
+            const double Du = m[i] / r - du - (force ? force[i] : 0.0);
+            t += lam_u_next[i * N + node] * Du;
+        }
+        total += t;
+    }
+    return total;
+}

@@ -70,6 +70,9 @@ def _load():
             lib.oracle_adjoint_step.restype = ctypes.c_int
             lib.oracle_adjoint_step_gather.argtypes = lib.oracle_adjoint_step.argtypes
             lib.oracle_adjoint_step_gather.restype = ctypes.c_int
+            lib.oracle_nu_term.argtypes = [ctypes.c_int, i64, i64, i64, u32, vp, dp, dp, dp, dp, dp,
+                                           ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_nu_term.restype = ctypes.c_double
             lib.oracle_set_threads.argtypes = [ctypes.c_int]
             lib.oracle_set_threads.restype = ctypes.c_int
             lib.oracle_lattice_table.argtypes = [ctypes.c_int, vp, vp]
@@ -180,6 +183,22 @@ def adjoint_step(lattice, rho, u, periodic, lam_rho_next, lam_u_next, wall=None,
             _ptr(lr1), _ptr(lu1), _ptr(lr), _ptr(lu), _ptr(gf))
     _check(rc, "adjoint_step")
     return lr, lu, gf
+
+
+def nu_term(lattice, rho, u, periodic, lam_rho_next, lam_u_next, wall=None, force=None):
+    """The viscosity term of one reverse step (see maclab_oracle.c): summed over
+    a rollout's steps it gives e dL/de (Eq. (6): nu enters only through e)."""
+    rho = _f64(rho)
+    d, nx, ny, nz = _shape(lattice, rho)
+    u = _f64(u)
+    lr, lu = _f64(lam_rho_next), _f64(lam_u_next)
+    wall_b = None if wall is None else np.ascontiguousarray(wall, dtype=np.uint8)
+    f = None if force is None else _f64(np.asarray(force, dtype=np.float64).reshape(d))
+    st = ctypes.c_int(0)
+    v = _load().oracle_nu_term(lattice, nx, ny, nz, int(periodic), _ptr(wall_b), _ptr(rho), _ptr(u),
+                               _ptr(f), _ptr(lr), _ptr(lu), ctypes.byref(st))
+    _check(st.value, "nu_term")
+    return v
 
 
 def rollout_adjoint(lattice, rho0, u0, periodic, nsteps, lam_rho_T, lam_u_T, wall=None,

@@ -32,8 +32,24 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every CUDA source of the library and link libmaclab.so."""
+BOUNDS_LIB = os.path.join(OUT_DIR, "libmaclab_bounds.so")
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=(), bounds_check: bool = False) -> str:
+    """Compile every CUDA source of the library and link libmaclab.so.
+
+    bounds_check: the debug build instead (-DMACLAB_BOUNDS_CHECK, objects in
+    _build/bounds, linked as libmaclab_bounds.so): the checked kernels record
+    and skip out-of-bounds indices (maclab_debug_bounds).
+    """
+    global OBJ_DIR, LIB
+    if bounds_check:
+        saved = OBJ_DIR, LIB
+        OBJ_DIR, LIB = os.path.join(saved[0], "bounds"), BOUNDS_LIB
+        try:
+            return build(force, verbose, tuple(extra_flags) + ("-DMACLAB_BOUNDS_CHECK",))
+        finally:
+            OBJ_DIR, LIB = saved
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(OBJ_DIR, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))

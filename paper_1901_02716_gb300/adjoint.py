@@ -11,7 +11,11 @@ library's kernels; this module only moves device buffers and calls the C ABI.
 Gradients are returned for the initial density and velocity (physical, zero on
 wall nodes), the wall velocities (one row per wall id) and the viscosity nu (at
 a fixed number of steps: e = 6 nu / dx changes the lattice velocities and the
-time step).
+time step).  dL/dnu is summed step by step during the reverse pass
+(maclab_adjoint_nu_term: the defect of each step under the e-scaling, dotted
+with the adjoint it produced), which keeps FP32 rollouts accurate where the
+end-point form (the difference of two nearly equal products, kept as
+``grads_extra["nu_endpoint"]``) loses digits.
 """
 from __future__ import annotations
 
@@ -71,6 +75,7 @@ class MacLABRollout(torch.autograd.Function):
         u_T = torch.empty_like(u0)
         s.get_state_into(rho_T, u_T)
         ctx.solver, ctx.ckpts, ctx.state_T, ctx.seg, ctx.n = s, ckpts, state_T, seg, n
+        ctx.dx = float(spec.dx)
         ctx.n_walls = n_walls
         ctx.d = u0.shape[0]
         ctx.wall_dtype = None if wall_u is None else wall_u.dtype
@@ -87,6 +92,7 @@ class MacLABRollout(torch.autograd.Function):
         dot_T = M.maclab_adjoint_seed(h, None if g_rho is None else g_rho.contiguous(),
                                       None if g_u is None else g_u.contiguous(), ctx.state_T, lam)
         gforce = torch.zeros(3, dtype=torch.float64, device="cuda")
+        nu_acc = torch.zeros(1, dtype=torch.float64, device="cuda")
         n, seg, ckpts = ctx.n, ctx.seg, ctx.ckpts
         bounds = [(i * seg, min((i + 1) * seg, n)) for i in range(len(ckpts))] if n else []
         for idx in range(len(bounds) - 1, -1, -1):
@@ -99,6 +105,7 @@ class MacLABRollout(torch.autograd.Function):
                 states.append(_raw(s))
             states.append(end_state)
             for k in range(b - a - 1, -1, -1):
+                M.maclab_adjoint_nu_term(h, states[k], lam, nu_acc)
                 M.maclab_adjoint_step(h, states[k], states[k + 1], lam, lam2, gforce)
                 lam, lam2 = lam2, lam
         ref = g_u if g_u is not None else g_rho
@@ -111,7 +118,12 @@ class MacLABRollout(torch.autograd.Function):
         if ctx.n_walls:
             grad_wall = torch.tensor([w[1:1 + ctx.d] for w in res["wall"]], dtype=ctx.wall_dtype,
                                      device="cuda")
-        grad_nu = torch.tensor(res["nu"], dtype=ctx.nu_dtype)
+        # e dL/de = sum of the step terms; dL/dnu = (de/dnu) dL/de, de/dnu = 6 / dx
+        e = s.params["e"]
+        grad_nu_steps = (6.0 / ctx.dx) * float(nu_acc.item()) / e
+        res["nu_endpoint"] = res["nu"]
+        res["nu"] = grad_nu_steps
+        grad_nu = torch.tensor(grad_nu_steps, dtype=ctx.nu_dtype)
         ctx.grads_extra = res
         return grad_rho0, grad_u0, grad_wall, grad_nu, None
 

@@ -192,6 +192,93 @@ __global__ void __launch_bounds__(256) adj_gather(Geometry g, const S* __restric
   }
 }
 
+// ------------------------------------------------------------------ the viscosity term
+//
+// nu enters a rollout only through e = 6 nu / dx (Eq. (6)): the initial and
+// wall velocities are u / e in lattice units, the force increment is
+// g dt / e = g dx / e^2, the output is u = e ut, and the lattice update itself
+// does not depend on e.  With the tangent tau_n = e d(state_n)/de and
+// s_n = tau_n + (0, ut_n) (zero at t = 0 and on wall nodes), s follows
+// s_(n+1) = J_n s_n + D_n with the defect of one step at a fluid node
+//   D_n^u   = ut'_nf - J (0, ut) |_u - F,        D_n^drho = -J (0, ut) |_drho,
+// where ut'_nf = m' / rho' is the step's output without the force F and
+// J (0, ut) the step's derivative along ut scaled by (1 + eps):
+//   dF_a = w_a rho (3 c.u + 9 (c.u)^2 - 3 u.u),  drho' = sum dF_a,
+//   dut' = (sum c dF_a - ut'_nf drho') / rho'.
+// Then e dL/de = lam_T . s_T = sum_n sum_x lam_(n+1)(x) . D_n(x): every term is
+// formed directly (ut'_nf - dut' = (m' - dm') / rho' + ut'_nf drho' / rho', with
+// m' - dm' = sum c w rho (1 - 9/2 (c.u)^2 + 3/2 u.u)), not as the difference of
+// the end-point products lam_T . ut_T and lam_0 . ut_0, which nearly cancel.
+// Sums use the integer weights 36 w_a and drop their constant parts exactly
+// (sum 36 w_a = 36, sum 36 w_a c_a = 0).
+template <int LAT, typename S>
+__global__ void __launch_bounds__(256) adj_nu_term(Geometry g, const S* __restrict__ state,
+                                                   const typename Store<S>::C* __restrict__ lam1,
+                                                   double f0, double f1, double f2,
+                                                   double* __restrict__ acc) {
+  using C = typename Store<S>::C;
+  using L = Lattice<LAT>;
+  constexpr int D = L::D;
+  const int64_t N = g.n;
+  const C force[3] = {C(f0), C(f1), C(f2)};
+  double sum = 0.0;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < N;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const int x = log_x(g, (int)(m % g.nx));
+    const int y = (int)((m / g.nx) % g.ny);
+    const int z = (int)(m / ((int64_t)g.nx * g.ny));
+    if (wall_at<LAT>(g, x, y, z, m)) continue;
+    C R = 0, dR = 0, M[3] = {0, 0, 0}, Md[3] = {0, 0, 0};  // all x 36
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+      int xs = x - L::c(a, 0), ys = y - L::c(a, 1), zs = D == 3 ? z - L::c(a, 2) : 0;
+      xs = xs < 0 ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
+      ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+      if (D == 3) zs = zs < 0 ? zs + g.nz : (zs >= g.nz ? zs - g.nz : zs);
+      const int64_t sidx = ((int64_t)zs * g.ny + ys) * g.nx + mem_x(g, xs);
+      const C dr = (C)Store<S>::from(state[sidx]);
+      const C rho = C(1) + dr;
+      C cu = 0, uu = 0;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const C u = (C)Store<S>::from(state[(1 + i) * N + sidx]);
+        cu += C(L::c(a, i)) * u;
+        uu += u * u;
+      }
+      const C w = C(L::w36(a));
+      const C p = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;   // f = w rho (1 + p)
+      const C q = C(1.5) * uu - C(4.5) * cu * cu;               // f - df = w rho (1 + q)
+      const C fv = w * (dr + rho * p);                          // f - w (the constant part)
+      const C gv = w * (dr + rho * q);                          // f - df - w
+      R += fv;
+      dR += w * rho * (C(3) * cu + C(9) * cu * cu - C(3) * uu);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        if (L::c(a, i) == 0) continue;
+        M[i] += C(L::c(a, i)) * fv;
+        Md[i] += C(L::c(a, i)) * gv;
+      }
+    }
+    const C R36 = C(36) + R;                 // 36 rho'
+    double t = -(double)lam1[m] * (double)(dR / C(36));
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const C unf = M[i] / R36;              // m' / rho'
+      const C du = Md[i] / R36 + unf * (dR / R36) - force[i];
+      t += (double)lam1[(1 + i) * N + m] * (double)du;
+    }
+    sum += t;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(acc, red[0]);
+}
+
 static unsigned grid256(int64_t n) {
   static int sms = 0;
   if (!sms) {
@@ -242,6 +329,37 @@ cudaError_t launch_adjoint_step(const Geometry& g, int precision, const void* st
                                   force_lat, grad_force, st)
              : adjoint_lat<kD3Q19>(g, precision, state_n, state_np1, lam_np1, lam_n, scratch,
                                    force_lat, grad_force, st);
+}
+
+template <int LAT>
+static cudaError_t nu_term_lat(const Geometry& g, int precision, const void* sn, const void* lam1,
+                               const double* f, double* acc, cudaStream_t st) {
+  switch (precision) {
+    case MACLAB_F64:
+      adj_nu_term<LAT, double><<<grid256(g.n), 256, 0, st>>>(g, (const double*)sn, (const double*)lam1, f[0], f[1],
+                                                            f[2], acc);
+      break;
+    case MACLAB_F32:
+      adj_nu_term<LAT, float><<<grid256(g.n), 256, 0, st>>>(g, (const float*)sn, (const float*)lam1, f[0], f[1],
+                                                           f[2], acc);
+      break;
+    case MACLAB_BF16_STORE:
+      adj_nu_term<LAT, __nv_bfloat16><<<grid256(g.n), 256, 0, st>>>(g, (const __nv_bfloat16*)sn, (const float*)lam1,
+                                                                   f[0], f[1], f[2], acc);
+      break;
+    case MACLAB_F16_STORE:
+      adj_nu_term<LAT, __half><<<grid256(g.n), 256, 0, st>>>(g, (const __half*)sn, (const float*)lam1, f[0], f[1],
+                                                            f[2], acc);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_nu_term(const Geometry& g, int precision, const void* state_n, const void* lam_np1,
+                                   const double force_lat[3], double* acc, cudaStream_t st) {
+  return g.lattice == kD2Q9 ? nu_term_lat<kD2Q9>(g, precision, state_n, lam_np1, force_lat, acc, st)
+                            : nu_term_lat<kD3Q19>(g, precision, state_n, lam_np1, force_lat, acc, st);
 }
 
 // ------------------------------------------------------------------ seeds and gradients

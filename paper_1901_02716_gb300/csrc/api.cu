@@ -85,6 +85,7 @@ void free_ctx(maclab_ctx* h) {
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   cudaFree(h->d_partial);
   cudaFree(h->d_diag);
+  if (h->h_diag) cudaFreeHost(h->h_diag);
   cudaFree(h->d_adj_scratch);
   cudaFree(h->d_adj_red);
   cudaFree(h->d_seg_inst);
@@ -304,7 +305,8 @@ maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {
   h->diag_nblocks = diag_blocks(N);
   if (cudaMalloc(&h->buf[0], sb) != cudaSuccess || cudaMalloc(&h->buf[1], sb) != cudaSuccess ||
       cudaMalloc(&h->d_partial, sizeof(double) * kDiagOut * h->diag_nblocks) != cudaSuccess ||
-      cudaMalloc(&h->d_diag, sizeof(double) * kDiagOut) != cudaSuccess) {
+      cudaMalloc(&h->d_diag, sizeof(double) * kDiagOut) != cudaSuccess ||
+      cudaHostAlloc(&h->h_diag, sizeof(double) * kDiagOut, cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     free_ctx(h);
     return fail(MACLAB_ERR_OOM, "state allocation failed");
@@ -725,6 +727,15 @@ maclab_status maclab_adjoint_step(maclab_handle h, const void* state_n, const vo
   return MACLAB_OK;
 }
 
+maclab_status maclab_adjoint_nu_term(maclab_handle h, const void* state_n, const void* lam_np1, double* acc) {
+  NvtxRange nvtx_range("maclab_adjoint_nu_term");
+  if (!h || !state_n || !lam_np1 || !acc) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  DeviceGuard dg(h->device);
+  CUDA_TRY(launch_adjoint_nu_term(h->g, h->precision, state_n, lam_np1, h->force_lat, acc, h->stream),
+           "adjoint nu term");
+  return MACLAB_OK;
+}
+
 maclab_status maclab_adjoint_seed(maclab_handle h, const void* grad_rho, const void* grad_u,
                                   int32_t dtype, const void* state_T, void* lam_T, double* dot_T) {
   if (!h || !state_T || !lam_T) return fail(MACLAB_ERR_INVALID, "NULL argument");
@@ -790,9 +801,11 @@ maclab_status maclab_diagnostics(maclab_handle h, double out[8]) {
                               h->prev_valid ? h->buf[h->cur ^ 1] : nullptr, h->d_partial,
                               h->diag_nblocks, h->d_diag, h->stream),
            "diagnostics kernel");
-  double r[kDiagOut];
-  CUDA_TRY(cudaMemcpyAsync(r, h->d_diag, sizeof(r), cudaMemcpyDeviceToHost, h->stream), "diagnostics D2H");
+  CUDA_TRY(cudaMemcpyAsync(h->h_diag, h->d_diag, kDiagOut * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+           "diagnostics D2H");
   CUDA_TRY(cudaStreamSynchronize(h->stream), "diagnostics sync");
+  double r[kDiagOut];
+  for (int k = 0; k < kDiagOut; ++k) r[k] = h->h_diag[k];
   const double nf = (double)h->n_fluid;
   out[0] = h->rho0 * (nf + r[0]);
   out[1] = 0.5 * h->rho0 * h->e * h->e * r[1];
@@ -814,9 +827,10 @@ maclab_status maclab_diagnostics_sums(maclab_handle h, double out[9]) {
                               h->prev_valid ? h->buf[h->cur ^ 1] : nullptr, h->d_partial,
                               h->diag_nblocks, h->d_diag, h->stream),
            "diagnostics kernel");
-  CUDA_TRY(cudaMemcpyAsync(out, h->d_diag, kDiagOut * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+  CUDA_TRY(cudaMemcpyAsync(h->h_diag, h->d_diag, kDiagOut * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
            "diagnostics D2H");
   CUDA_TRY(cudaStreamSynchronize(h->stream), "diagnostics sync");
+  for (int k = 0; k < kDiagOut; ++k) out[k] = h->h_diag[k];
   if (!h->prev_valid) out[5] = out[6] = -1.0;
   return MACLAB_OK;
 }
@@ -861,6 +875,51 @@ maclab_status maclab_set_planes(maclab_handle h, int64_t p0, int64_t count, cons
              "set_planes copy");
   if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "set_planes sync");
   return MACLAB_OK;
+}
+
+}  // extern "C"
+
+namespace maclab {
+BoundsLog* bounds_log() {
+#ifdef MACLAB_BOUNDS_CHECK
+  static std::mutex m;
+  static BoundsLog* logs[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(m);
+  if (!logs[dev]) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(BoundsLog)) != cudaSuccess || cudaMemset(p, 0, sizeof(BoundsLog)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    logs[dev] = static_cast<BoundsLog*>(p);
+  }
+  return logs[dev];
+#else
+  return nullptr;
+#endif
+}
+}  // namespace maclab
+
+extern "C" {
+
+maclab_status maclab_debug_bounds(int64_t out[2]) {
+  if (!out) return fail(MACLAB_ERR_INVALID, "NULL argument");
+#ifdef MACLAB_BOUNDS_CHECK
+  BoundsLog* log = bounds_log();
+  if (!log) return fail(MACLAB_ERR_CUDA, "bounds log unavailable");
+  BoundsLog h{};
+  CUDA_TRY(cudaDeviceSynchronize(), "debug_bounds sync");
+  CUDA_TRY(cudaMemcpy(&h, log, sizeof(h), cudaMemcpyDeviceToHost), "debug_bounds read");
+  CUDA_TRY(cudaMemset(log, 0, sizeof(h)), "debug_bounds clear");
+  out[0] = (int64_t)h.count;
+  out[1] = (int64_t)h.first;
+  return MACLAB_OK;
+#else
+  out[0] = out[1] = 0;
+  return fail(MACLAB_ERR_UNSUPPORTED, "library built without MACLAB_BOUNDS_CHECK");
+#endif
 }
 
 maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {

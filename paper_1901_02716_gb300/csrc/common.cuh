@@ -42,6 +42,30 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// ------------------------------------------------------------------ bounds checks
+// Debug builds (compiled with -DMACLAB_BOUNDS_CHECK; _build.build(bounds_check=True)
+// makes libmaclab_bounds.so): the kernels that take a BoundsLog check each
+// global and shared-memory index against the size of its buffer before the
+// access; a bad index is counted, the first one recorded, and the access
+// skipped (a load gives 0).  Nothing traps.  maclab_debug_bounds reads and
+// clears the log.  In normal builds bounds_ok is the constant true and the
+// checks compile away.
+struct BoundsLog {
+  unsigned long long count;
+  long long first;
+};
+#ifdef MACLAB_BOUNDS_CHECK
+__device__ __forceinline__ bool bounds_ok(BoundsLog* log, long long idx, long long limit) {
+  if (idx >= 0 && idx < limit) return true;
+  if (log && atomicAdd(&log->count, 1ull) == 0ull) log->first = idx;
+  return false;
+}
+#else
+__device__ __forceinline__ bool bounds_ok(BoundsLog*, long long, long long) { return true; }
+#endif
+// Device log of the current device (debug builds; nullptr otherwise).  Defined in api.cu.
+BoundsLog* bounds_log();
+
 // ------------------------------------------------------------------ storage
 
 template <typename S>
@@ -203,6 +227,9 @@ bool tiled_adjoint_supported(const Geometry& g, int precision);
 cudaError_t launch_tiled_adjoint(const Geometry& g, int precision, const void* state_n,
                                  const void* state_np1, const void* lam_np1, void* lam_n,
                                  const double force_lat[3], double* grad_force, cudaStream_t st);
+// sum over fluid x of lam_np1(x) . D_n(x), the viscosity term of one reverse step, into *acc
+cudaError_t launch_adjoint_nu_term(const Geometry& g, int precision, const void* state_n, const void* lam_np1,
+                                   const double force_lat[3], double* acc, cudaStream_t st);
 cudaError_t launch_adjoint_seed(const Geometry& g, int precision, const void* grho, const void* gu,
                                 int dtype, const void* state, double rho0, double e, void* lam,
                                 double* dot, cudaStream_t st);
@@ -268,6 +295,7 @@ struct maclab_ctx {
   bool prev_valid = false;         // buf[cur ^ 1] holds the state one step back
   double* d_partial = nullptr;     // diagnostics scratch (per-block partial sums)
   double* d_diag = nullptr;        // diagnostics result (kDiagOut doubles)
+  double* h_diag = nullptr;        // page-locked host copy of it
   int diag_nblocks = 0;
   // CUDA graphs of graph_steps steps, one per starting buffer
   int graph_steps = 32;

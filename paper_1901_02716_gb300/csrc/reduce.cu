@@ -1,8 +1,9 @@
 // reduce.cu -- FP64 diagnostics of the stored state.
 //
-// Sums over fluid nodes (walls excluded), accumulated in FP64 whatever the
+// Sums over fluid nodes (walls excluded), to FP64 accuracy whatever the
 // storage type (each node's products are formed in the storage's arithmetic
-// type, FP32 for FP32 and 16-bit storage, where FP64 arithmetic is slow):
+// type, FP32 for FP32 and 16-bit storage, and added in float-float within a
+// thread, where FP64 arithmetic is slow; FP64 across threads):
 //   slot 0  sum drho                      (mass = rho0 (n_fluid + slot 0))
 //   slot 1  sum rho |u|^2                 (kinetic energy = rho0 e^2 slot 1 / 2)
 //   slot 2..4  sum rho u_i                (momentum = rho0 e slot)
@@ -19,30 +20,79 @@
 
 #include "common.cuh"
 #include "lattice.cuh"
+#include "step_tiled.cuh"  // Quad<S>: four stored values in one vector load
 
 namespace maclab {
 
 constexpr int kDiagSlots = 9;
+
+// Running sum of one thread.  FP64 storage sums in FP64.  FP32 and 16-bit
+// storage form each node's products in FP32, and a thread adds them in
+// float-float: a pair (hi, lo) updated with Knuth's error-free two-sum, so the
+// rounding error of every FP32 addition is kept in lo and the pair carries
+// about 46 bits; it becomes one FP64 value at the end of the thread's loop.
+// All of this runs on the FP32 pipe (GB300's FP64 rate is a small fraction
+// of it), and the per-thread sums stay accurate to about 2^-46 of their size.
+template <typename C>
+struct DiagAcc;
+template <>
+struct DiagAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct DiagAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 template <typename S>
 __global__ void __launch_bounds__(256) diag_partial(Geometry g, const S* __restrict__ cur,
                                                     const S* __restrict__ prev,
                                                     double* __restrict__ partial) {
   using C = typename Store<S>::C;
-  double acc[kDiagSlots];
-#pragma unroll
-  for (int k = 0; k < kDiagSlots; ++k) acc[k] = 0.0;
+  DiagAcc<C> sum[kDiagSlots - 2];  // slots 0-6
+  float nonfinite = 0.f;
   C umax2 = C(0);
   const int64_t N = g.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // storage position (mx, y, z) of m, advanced by the stride without dividing
-  int64_t q = m / g.nx;
-  int mx = (int)(m - q * g.nx), y = (int)(q % g.ny);
-  int64_t z = q / g.ny;
-  const int64_t sq = stride / g.nx;
-  const int sx = (int)(stride - sq * g.nx), sy = (int)(sq % g.ny);
-  const int64_t sz = sq / g.ny;
+  // (32-bit divisions where the node count allows: 64-bit ones are emulated)
+  int64_t q, sq;
+  int mx, y, sx, sy;
+  int64_t z, sz;
+  if (N < (int64_t)INT32_MAX && stride < (int64_t)INT32_MAX) {
+    const unsigned nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+    const unsigned m32 = (unsigned)(m < N ? m : 0), q32 = m32 / nx, s32 = (unsigned)stride, sq32 = s32 / nx;
+    q = q32;
+    mx = (int)(m32 - q32 * nx);
+    y = (int)(q32 % ny);
+    z = q32 / ny;
+    sq = sq32;
+    sx = (int)(s32 - sq32 * nx);
+    sy = (int)(sq32 % ny);
+    sz = sq32 / ny;
+  } else {
+    q = m / g.nx;
+    mx = (int)(m - q * g.nx);
+    y = (int)(q % g.ny);
+    z = q / g.ny;
+    sq = stride / g.nx;
+    sx = (int)(stride - sq * g.nx);
+    sy = (int)(sq % g.ny);
+    sz = sq / g.ny;
+  }
+  (void)q;
+  (void)sq;
   for (; m < N; m += stride) {
     bool wall = false;
     if (g.wall_mode == kWallMask) {
@@ -63,29 +113,35 @@ __global__ void __launch_bounds__(256) diag_partial(Geometry g, const S* __restr
     }
     z += sz;
     if (wall) continue;
-    // per-node products in the storage's arithmetic type, sums in FP64
+    // per-node products in the storage's arithmetic type
     const C dr = Store<S>::from(cur[m]);
     const C rho = C(1) + dr;
     C uu = C(0), du = C(0);
     bool finite = isfinite(dr);
-    acc[0] += (double)dr;
-    for (int i = 0; i < g.d; ++i) {
+    sum[0].add(dr);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (i >= g.d) break;
       const C u = Store<S>::from(cur[(1 + i) * N + m]);
       finite = finite && isfinite(u);
       uu = fma(u, u, uu);
-      acc[2 + i] += (double)(rho * u);
+      sum[2 + i].add(rho * u);
       if (prev) {
         const C d = u - Store<S>::from(prev[(1 + i) * N + m]);
         du = fma(d, d, du);
       }
     }
-    acc[1] += (double)(rho * uu);
-    acc[5] += (double)du;
-    acc[6] += (double)uu;
+    sum[1].add(rho * uu);
+    sum[5].add(du);
+    sum[6].add(uu);
     umax2 = fmax(umax2, uu);  // max |u|^2 here, its root below (the root is monotonic)
-    if (!finite) acc[8] += 1.0;
+    if (!finite) nonfinite += 1.f;
   }
+  double acc[kDiagSlots];
+#pragma unroll
+  for (int k = 0; k < kDiagSlots - 2; ++k) acc[k] = sum[k].value();
   acc[7] = sqrt((double)umax2);
+  acc[8] = (double)nonfinite;
   // block reduction: warp shuffles, then one value per warp through shared memory
   __shared__ double red[kDiagSlots][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -113,26 +169,142 @@ __global__ void __launch_bounds__(256) diag_partial(Geometry g, const S* __restr
   }
 }
 
+// Rows of x (nx % 4 == 0): a warp takes whole rows, each lane 16-byte quads of
+// the four stored values of a node quad (vector loads, many in flight); rows on
+// a closed y or z boundary are wall rows and skipped as a whole, and in box
+// mode only the storage positions 0 and nx - 1 of a row (x = 0, nx - 1) are
+// x-walls.  Same per-node products and sums as diag_partial.
+template <typename S>
+__global__ void __launch_bounds__(256) diag_rows(Geometry g, const S* __restrict__ cur,
+                                                 const S* __restrict__ prev, double* __restrict__ partial) {
+  using C = typename Store<S>::C;
+  using P = typename Quad<S>::P;
+  DiagAcc<C> sum[kDiagSlots - 2];
+  float nonfinite = 0.f;
+  C umax2 = C(0);
+  const int64_t N = g.n;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t rows = N / g.nx;
+  const int quads = g.nx >> 2;
+  const bool xw = g.wall_mode == kWallBox && !(g.periodic & 1u);
+  const bool yw = g.wall_mode == kWallBox && !(g.periodic & 2u);
+  const bool zw = g.wall_mode == kWallBox && g.d == 3 && !(g.periodic & 4u);
+  for (int64_t row = warp; row < rows; row += nwarps) {
+    const int y = (int)(row % g.ny);
+    const int64_t z = row / g.ny;
+    if ((yw && (y == 0 || y == g.ny - 1)) || (zw && (z == 0 || z == g.nz - 1))) continue;
+    for (int q = lane; q < quads; q += 32) {
+      const int64_t m = row * g.nx + 4 * q;
+      bool wall[4] = {false, false, false, false};
+      if (g.wall_mode == kWallMask) {
+        const uchar4 mk = *reinterpret_cast<const uchar4*>(g.mask + m);
+        wall[0] = mk.x != 0; wall[1] = mk.y != 0; wall[2] = mk.z != 0; wall[3] = mk.w != 0;
+      } else if (xw) {
+        wall[0] = q == 0;
+        wall[3] = q == quads - 1;
+      }
+      P r[2], u[3][2], v[3][2];
+      Quad<S>::ld(cur + m, r[0], r[1]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i >= g.d) break;
+        Quad<S>::ld(cur + (1 + i) * N + m, u[i][0], u[i][1]);
+        if (prev) Quad<S>::ld(prev + (1 + i) * N + m, v[i][0], v[i][1]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (wall[k]) continue;
+        const int h = k >> 1;
+        const auto pick = [&](const P& p) { return (k & 1) ? p.y : p.x; };
+        const C dr = pick(r[h]);
+        const C rho = C(1) + dr;
+        C uu = C(0), du = C(0);
+        bool finite = isfinite(dr);
+        sum[0].add(dr);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          if (i >= g.d) break;
+          const C ui = pick(u[i][h]);
+          finite = finite && isfinite(ui);
+          uu = fma(ui, ui, uu);
+          sum[2 + i].add(rho * ui);
+          if (prev) {
+            const C d = ui - pick(v[i][h]);
+            du = fma(d, d, du);
+          }
+        }
+        sum[1].add(rho * uu);
+        sum[5].add(du);
+        sum[6].add(uu);
+        umax2 = fmax(umax2, uu);
+        if (!finite) nonfinite += 1.f;
+      }
+    }
+  }
+  double acc[kDiagSlots];
+#pragma unroll
+  for (int k = 0; k < kDiagSlots - 2; ++k) acc[k] = sum[k].value();
+  acc[7] = sqrt((double)umax2);
+  acc[8] = (double)nonfinite;
+  __shared__ double red[kDiagSlots][32];
+  const int wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kDiagSlots; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v, o);
+      v = k == 7 ? fmax(v, w) : v + w;
+    }
+    if (lane == 0) red[k][wid] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kDiagSlots; ++k) {
+      double v = lane < nw ? red[k][lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, v, o);
+        v = k == 7 ? fmax(v, w) : v + w;
+      }
+      if (lane == 0) partial[(int64_t)blockIdx.x * kDiagSlots + k] = v;
+    }
+  }
+}
+
+// One block folds the partials: strided sums per thread, then warp shuffles
+// and one value per warp through shared memory.
 __global__ void __launch_bounds__(256) diag_final(const double* __restrict__ partial, int nblocks,
                                                   double* __restrict__ out) {
-  __shared__ double red[kDiagSlots][256];
+  __shared__ double red[kDiagSlots][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
   for (int k = 0; k < kDiagSlots; ++k) {
     double v = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
       const double w = partial[(int64_t)b * kDiagSlots + k];
       v = k == 7 ? fmax(v, w) : v + w;
     }
-    red[k][threadIdx.x] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v, o);
+      v = k == 7 ? fmax(v, w) : v + w;
+    }
+    if (lane == 0) red[k][warp] = v;
   }
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int k = 0; k < kDiagSlots; ++k)
-        red[k][threadIdx.x] = k == 7 ? fmax(red[k][threadIdx.x], red[k][threadIdx.x + s])
-                                     : red[k][threadIdx.x] + red[k][threadIdx.x + s];
-    __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < kDiagSlots; ++k) {
+      double v = lane < 8 ? red[k][lane] : 0.0;
+      for (int o = 4; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, v, o);
+        v = k == 7 ? fmax(v, w) : v + w;
+      }
+      if (lane == 0) out[k] = v;
+    }
   }
-  if (threadIdx.x < kDiagSlots) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
 int diag_blocks(int64_t n) {
@@ -151,7 +323,10 @@ int diag_blocks(int64_t n) {
 template <typename S>
 static cudaError_t diag_t(const Geometry& g, const void* cur, const void* prev, double* partial,
                           int nblocks, double* out, cudaStream_t st) {
-  diag_partial<S><<<nblocks, 256, 0, st>>>(g, (const S*)cur, (const S*)prev, partial);
+  if (g.nx % 4 == 0)
+    diag_rows<S><<<nblocks, 256, 0, st>>>(g, (const S*)cur, (const S*)prev, partial);
+  else
+    diag_partial<S><<<nblocks, 256, 0, st>>>(g, (const S*)cur, (const S*)prev, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   diag_final<<<1, 256, 0, st>>>(partial, nblocks, out);

@@ -93,6 +93,7 @@ cudaError_t launch_rows2(const StepLaunch& sl, cudaStream_t stream, int ty, int 
   ta.mask = g.mask;
   for (int i = 0; i < 3; ++i) ta.force[i] = sl.force[i];
   ta.overlap = sl.overlap;
+  ta.bounds = bounds_log();
   return dispatch(sl.in, sl.out, dim3(ta.nzc, ytiles), nullptr);
 }
 

@@ -10,7 +10,10 @@
 //    of a tile of TY = 2 TYT rows.  Equilibria moving between its two rows
 //    stay in registers (or go to a neighbouring lane by a warp shuffle when
 //    they also move in x); only those leaving the thread's row pair in y go
-//    through shared memory: half the exchange of one row per thread.
+//    through shared memory: half the exchange of one row per thread.  The
+//    terms of one node pair are formed at a time, and each row's x-crossing
+//    values go by shuffle as soon as its two pairs are done, which keeps the
+//    register footprint near what two blocks per SM allow without spilling.
 //  * The y exchange is laid out for the receiver: for each direction and each
 //    receiving thread-row there is one 16-byte unit per column holding the two
 //    values its pairs a and b gather, so a receiver reads a direction with one
@@ -262,20 +265,34 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   const uint32_t halo_off = (uint32_t)(halo == 1 ? 0 : TY + 1) * BXC * QW;
   const uint32_t stage_sh = (uint32_t)__cvta_generic_to_shared(stage0);
   const int np = z1 - z0 + 2;  // planes z0 - 1 .. z1
+  // debug builds: a quad copy or load of 4 values at element offset e (from
+  // `in` or `out`) and a stage byte offset b (from stage0) must lie in bounds
+  const int64_t n4 = 4 * ta.n;
+  const int64_t stage_lim = (int64_t)Lay::stage_bytes - (int64_t)tx * QW;
+  auto quad_ok = [&](int64_t e, int64_t b) {
+    return bounds_ok(ta.bounds, e, n4 - 3) && bounds_ok(ta.bounds, b, stage_lim - QW + 1);
+  };
+  const int64_t in_off = row_off;  // ip[f] = in + f * n + in_off
   auto fetch = [&](int i) {
     const int p = z0 - 1 + i;
     if (i < np && active && plane_exists(p)) {
       const int64_t off = (int64_t)plane_mem(p) * ps;
-      const uint32_t sh = stage_sh + (uint32_t)(i & (kStages - 1)) * kSlotStride + own_off;
+      const uint32_t so = (uint32_t)(i & (kStages - 1)) * kSlotStride + own_off;
+      const uint32_t sh = stage_sh + so;
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        Quad<S>::copy(sh + f * kFieldStride, ip[f] + off);
-        Quad<S>::copy(sh + f * kFieldStride + BXC * QW, ip[f] + off + nx64);
+        if (quad_ok(f * ta.n + in_off + off, so + f * kFieldStride))
+          Quad<S>::copy(sh + f * kFieldStride, ip[f] + off);
+        if (quad_ok(f * ta.n + in_off + off + nx64, so + f * kFieldStride + BXC * QW))
+          Quad<S>::copy(sh + f * kFieldStride + BXC * QW, ip[f] + off + nx64);
       }
       if (halo != 0) {
-        const uint32_t hs = stage_sh + (uint32_t)(i & (kStages - 1)) * kSlotStride + halo_off;
+        const uint32_t ho = (uint32_t)(i & (kStages - 1)) * kSlotStride + halo_off;
+        const uint32_t hs = stage_sh + ho;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) Quad<S>::copy(hs + f * kFieldStride, ip[f] + off + halo_delta);
+        for (int f = 0; f < 4; ++f)
+          if (quad_ok(f * ta.n + in_off + off + halo_delta, ho + f * kFieldStride))
+            Quad<S>::copy(hs + f * kFieldStride, ip[f] + off + halo_delta);
       }
     }
     cp_async_commit();
@@ -291,7 +308,8 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        if (ok) {
+        const int64_t b = (int64_t)(slot_base - stage0) + own_off + j * BXC * QW + f * kFieldStride;
+        if (ok && bounds_ok(ta.bounds, b, stage_lim - QW + 1)) {
           Quad<S>::lds(reinterpret_cast<const S*>(slot_base + own_off + j * BXC * QW + f * kFieldStride),
                        st[j][f][0], st[j][f][1]);
         } else {
@@ -309,78 +327,113 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
     constexpr int A = decltype(dir)::value;
     constexpr int FY = F::fy(A), FX = F::fx(A);
     float4* const u = ybase + (FY == 1 ? 0 : Lay::SIGN_UNITS) + rows2_ykey(A) * Lay::DIR_UNITS + slot * YC;
+    auto unit_ok = [&](int c) { return bounds_ok(ta.bounds, (u + c) - Y, 2 * Lay::BUF_UNITS); };
     if constexpr (FX == 0) {
-      u[col] = make_float4(Ta.x, Ta.y, Tb.x, Tb.y);
+      if (unit_ok(col)) u[col] = make_float4(Ta.x, Ta.y, Tb.x, Tb.y);
     } else if constexpr (FX == 1) {
       // receiver column c gathers (left neighbour's b, own a)
-      reinterpret_cast<float2*>(u + col)[1] = Ta;
+      if (unit_ok(col)) reinterpret_cast<float2*>(u + col)[1] = Ta;
       const P b = seam_r ? O::swap(Tb) : Tb;
-      reinterpret_cast<float2*>(u + col_r)[0] = b;
+      if (unit_ok(col_r)) reinterpret_cast<float2*>(u + col_r)[0] = b;
     } else {
       // receiver column c gathers (own b, right neighbour's a)
-      reinterpret_cast<float2*>(u + col)[0] = Tb;
+      if (unit_ok(col)) reinterpret_cast<float2*>(u + col)[0] = Tb;
       const P a = seam_l ? O::swap(Ta) : Ta;
-      reinterpret_cast<float2*>(u + col_l)[1] = a;
+      if (unit_ok(col_l)) reinterpret_cast<float2*>(u + col_l)[1] = a;
     }
   };
 
+  // the value of one pair (q) of direction A into its half of the receiver's unit
+  auto publish_half = [&](float4* ybase, auto dir, auto qc, int slot, P T) {
+    constexpr int A = decltype(dir)::value;
+    constexpr int q = decltype(qc)::value;
+    constexpr int FY = F::fy(A), FX = F::fx(A);
+    float4* const u = ybase + (FY == 1 ? 0 : Lay::SIGN_UNITS) + rows2_ykey(A) * Lay::DIR_UNITS + slot * YC;
+    auto unit_ok = [&](int c) { return bounds_ok(ta.bounds, (u + c) - Y, 2 * Lay::BUF_UNITS); };
+    if constexpr (FX == 0) {
+      if (unit_ok(col)) reinterpret_cast<float2*>(u + col)[q] = T;
+    } else if constexpr (FX == 1) {
+      if constexpr (q == 0) {
+        if (unit_ok(col)) reinterpret_cast<float2*>(u + col)[1] = T;
+      } else {
+        const P b = seam_r ? O::swap(T) : T;
+        if (unit_ok(col_r)) reinterpret_cast<float2*>(u + col_r)[0] = b;
+      }
+    } else {
+      if constexpr (q == 1) {
+        if (unit_ok(col)) reinterpret_cast<float2*>(u + col)[0] = T;
+      } else {
+        const P a = seam_l ? O::swap(T) : T;
+        if (unit_ok(col_l)) reinterpret_cast<float2*>(u + col_l)[1] = a;
+      }
+    }
+  };
   auto update = [&](auto mode, P(&ap)[2][2][4], P(&ac)[2][2][4], P(&an)[2][2][4]) {
     constexpr int MODE = decltype(mode)::value;
-    float4* const ybase = Y + ybuf * Lay::BUF_UNITS;
+    const int ybuf_units = ybuf * Lay::BUF_UNITS;
+    float4* const ybase = Y + ybuf_units;
     ybuf ^= 1;
-    // x-crossing values per destination row: [row][k] +x (from pair b), -x (from pair a)
-    P xb[2][4], xa[2][4];
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) xb[j][k] = xa[j][k] = O::splat(C(0));
-    // ---- own rows
+    // one pair at a time (terms of one pair live at once); each row's x-crossing
+    // values go by shuffle as soon as the row is done
+    auto shuffle_in = [&](auto dir, auto jdc, P vb_or_va) {
+      constexpr int a = decltype(dir)::value;
+      constexpr int jd = decltype(jdc)::value;
+      constexpr int fx = F::fx(a), fz = F::fz(a);
+      auto& dst = pick<fz>(ap, ac, an)[jd];
+      if constexpr (fx == 1) {
+        P v = fold_shfl<BXC>(vb_or_va, src_l);
+        if (seam_l) v = O::swap(v);
+        accum3<C, a>(dst[0], v, wts);
+      } else {
+        P v = fold_shfl<BXC>(vb_or_va, src_r);
+        if (seam_r) v = O::swap(v);
+        accum3<C, a>(dst[1], v, wts);
+      }
+    };
     static_for<0, 2>([&](auto jc) {
       constexpr int j = decltype(jc)::value;
-      Terms3<C> t[2];
+      constexpr int jd = 1 - j;
+      P xb[4], xa[4];  // [k]: k < 3 own c_y = 0 directions, 3: the diagonal into row jd
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const P u[3] = {st[j][1][q], st[j][2][q], st[j][3][q]};
-        make_terms3<C>(st[j][0][q], u, t[q]);
-      }
+      for (int k = 0; k < 4; ++k) xb[k] = xa[k] = O::splat(C(0));
+      static_for<0, 2>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        Terms3<C> t;
+        {
+          const P u[3] = {st[j][1][q], st[j][2][q], st[j][3][q]};
+          make_terms3<C>(st[j][0][q], u, t);
+        }
+        static_for<0, L::Q>([&](auto I) {
+          constexpr int a = decltype(I)::value;
+          if constexpr (mode_allows<kD3Q19, MODE>(a)) {
+            constexpr int fx = F::fx(a), fy = F::fy(a), fz = F::fz(a);
+            const P T = term3<C, a>(t);
+            if constexpr (fy == 0) {
+              auto& dst = pick<fz>(ap, ac, an)[j];
+              constexpr int qd = q + fx;
+              if constexpr (qd >= 0 && qd < 2) accum3<C, a>(dst[qd], T, wts);
+              else if constexpr (fx == 1) xb[fold_xidx(a)] = T;
+              else xa[fold_xidx(a)] = T;
+            } else if constexpr ((j == 0 && fy == 1) || (j == 1 && fy == -1)) {
+              auto& dst = pick<fz>(ap, ac, an)[jd];
+              constexpr int qd = q + fx;
+              if constexpr (qd >= 0 && qd < 2) accum3<C, a>(dst[qd], T, wts);
+              else if constexpr (fx == 1) xb[3] = T;
+              else xa[3] = T;
+            } else {
+              publish_half(ybase, I, qc, j == 1 ? tr + 1 : tr, T);
+            }
+          }
+        });
+      });
       static_for<0, L::Q>([&](auto I) {
         constexpr int a = decltype(I)::value;
-        if constexpr (mode_allows<kD3Q19, MODE>(a)) {
-          constexpr int fx = F::fx(a), fy = F::fy(a), fz = F::fz(a);
-          const P T0 = term3<C, a>(t[0]), T1 = term3<C, a>(t[1]);
-          if constexpr (fy == 0) {
-            // within the row: a -> b (+x), b -> a (-x) in the thread; the rest by shuffles
-            auto& dst = pick<fz>(ap, ac, an)[j];
-            if constexpr (fx == 0) {
-              accum3<C, a>(dst[0], T0, wts);
-              accum3<C, a>(dst[1], T1, wts);
-            } else if constexpr (fx == 1) {
-              accum3<C, a>(dst[1], T0, wts);
-              xb[j][fold_xidx(a)] = T1;
-            } else {
-              accum3<C, a>(dst[0], T1, wts);
-              xa[j][fold_xidx(a)] = T0;
-            }
-          } else if constexpr ((j == 0 && fy == 1) || (j == 1 && fy == -1)) {
-            // to the thread's other row
-            constexpr int jd = 1 - j;
-            auto& dst = pick<fz>(ap, ac, an)[jd];
-            if constexpr (fx == 0) {
-              accum3<C, a>(dst[0], T0, wts);
-              accum3<C, a>(dst[1], T1, wts);
-            } else if constexpr (fx == 1) {  // c_z = 0 here
-              accum3<C, a>(dst[1], T0, wts);
-              xb[jd][3] = T1;
-            } else {
-              accum3<C, a>(dst[0], T1, wts);
-              xa[jd][3] = T0;
-            }
-          } else {
-            // leaving the row pair: row 1 up to thread-row tr + 1 (slot tr + 1 of
-            // the +y sign), row 0 down to thread-row tr - 1 (slot tr of -y)
-            publish(ybase, I, j == 1 ? tr + 1 : tr, T0, T1);
-          }
-        }
+        constexpr int fx = F::fx(a), fy = F::fy(a), fz = F::fz(a);
+        if constexpr (mode_allows<kD3Q19, MODE>(a) && fy == 0 && fx != 0)
+          shuffle_in(I, jc, fx == 1 ? xb[fold_xidx(a)] : xa[fold_xidx(a)]);
+        if constexpr (mode_allows<kD3Q19, MODE>(a) && fz == 0 && fx != 0 &&
+                      ((j == 0 && fy == 1) || (j == 1 && fy == -1)))
+          shuffle_in(I, std::integral_constant<int, jd>{}, fx == 1 ? xb[3] : xa[3]);
       });
     });
     // ---- halo row: its inward equilibria into the slot its neighbour reads
@@ -388,8 +441,12 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
       P hs[4][2];
       const unsigned char* hsrc = slot_base + halo_off;
 #pragma unroll
-      for (int f = 0; f < 4; ++f)
-        Quad<S>::lds(reinterpret_cast<const S*>(hsrc + f * kFieldStride), hs[f][0], hs[f][1]);
+      for (int f = 0; f < 4; ++f) {
+        if (bounds_ok(ta.bounds, (int64_t)(hsrc - stage0) + f * kFieldStride, stage_lim - QW + 1))
+          Quad<S>::lds(reinterpret_cast<const S*>(hsrc + f * kFieldStride), hs[f][0], hs[f][1]);
+        else
+          hs[f][0] = hs[f][1] = O::splat(C(0));
+      }
       Terms3<C> t[2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -410,31 +467,6 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
         });
       }
     }
-    // ---- x exchange by shuffles: +x into pair a from the left lane's b,
-    // -x into pair b from the right lane's a (lane-swapped across the seam)
-    static_for<0, 2>([&](auto jc) {
-      constexpr int j = decltype(jc)::value;
-      // c_y = 0 directions of row j, then the diagonal arriving from the other row
-      static_for<0, L::Q>([&](auto I) {
-        constexpr int a = decltype(I)::value;
-        constexpr int fx = F::fx(a), fy = F::fy(a), fz = F::fz(a);
-        constexpr bool own = fy == 0 && fx != 0;
-        constexpr bool diag = fz == 0 && fx != 0 && ((j == 1 && fy == 1) || (j == 0 && fy == -1));
-        if constexpr (mode_allows<kD3Q19, MODE>(a) && (own || diag)) {
-          constexpr int k = own ? fold_xidx(a) : 3;
-          auto& dst = pick<fz>(ap, ac, an)[j];
-          if constexpr (fx == 1) {
-            P v = fold_shfl<BXC>(xb[j][k], src_l);
-            if (seam_l) v = O::swap(v);
-            accum3<C, a>(dst[0], v, wts);
-          } else {
-            P v = fold_shfl<BXC>(xa[j][k], src_r);
-            if (seam_r) v = O::swap(v);
-            accum3<C, a>(dst[1], v, wts);
-          }
-        }
-      });
-    });
     __syncthreads();
     // ---- gather: row 0 the +y units of slot tr, row 1 the -y units of slot tr + 1
     static_for<0, L::Q>([&](auto I) {
@@ -443,7 +475,9 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
       if constexpr (mode_allows<kD3Q19, MODE>(a) && fy != 0) {
         constexpr int j = fy == 1 ? 0 : 1;
         const int slot = fy == 1 ? tr : tr + 1;
-        const float4 v = ybase[(fy == 1 ? 0 : Lay::SIGN_UNITS) + rows2_ykey(a) * Lay::DIR_UNITS + slot * YC + col];
+        const int64_t unit = (int64_t)ybuf_units + (fy == 1 ? 0 : Lay::SIGN_UNITS) + rows2_ykey(a) * Lay::DIR_UNITS +
+                             slot * YC + col;
+        const float4 v = bounds_ok(ta.bounds, unit, 2 * Lay::BUF_UNITS) ? Y[unit] : make_float4(0.f, 0.f, 0.f, 0.f);
         auto& dst = pick<fz>(ap, ac, an)[j];
         accum3<C, a>(dst[0], O::make(v.x, v.y), wts);
         accum3<C, a>(dst[1], O::make(v.z, v.w), wts);
@@ -467,8 +501,10 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
 #pragma unroll
       for (int j = 0; j < 2; ++j)
 #pragma unroll
-        for (int f = 0; f < 4; ++f)
-          wv[j][f] = xwall_lane ? Store<S>::from(wall_src[(int64_t)f * ta.n + (int64_t)q * ps + j * nx64]) : 0.f;
+        for (int f = 0; f < 4; ++f) {
+          const int64_t e = (int64_t)(wall_src - in) + (int64_t)f * ta.n + (int64_t)q * ps + j * nx64;
+          wv[j][f] = xwall_lane && bounds_ok(ta.bounds, e, n4) ? Store<S>::from(in[e]) : 0.f;
+        }
     }
   };
   auto store = [&](int q, P(&acc)[2][2][4]) {
@@ -495,7 +531,7 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
       for (int f = 0; f < 4; ++f) {
         v[f][0].x = x_lo_wall ? wv[j][f] : v[f][0].x;
         v[f][1].y = x_hi_wall ? wv[j][f] : v[f][1].y;
-        Quad<S>::st(op[f] + off, v[f][0], v[f][1]);
+        if (bounds_ok(ta.bounds, f * ta.n + in_off + off, n4 - 3)) Quad<S>::st(op[f] + off, v[f][0], v[f][1]);
       }
     }
   };

@@ -75,6 +75,7 @@ struct TiledArgs {
   const uint8_t* mask;     // node types in storage order (kWallMask)
   double force[3];
   int overlap;             // host side: launch with programmatic dependent launch
+  BoundsLog* bounds;       // debug builds: where bad indices are recorded (bounds_ok)
 };
 
 // ------------------------------------------------------------------ lane pairs

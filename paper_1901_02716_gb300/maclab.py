@@ -65,6 +65,8 @@ SIGNATURES = {
     "maclab_get_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
     "maclab_set_wall_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
     "maclab_diagnostics_sums": (_S, [_H, _VP]),
+    "maclab_debug_bounds": (_S, [_VP]),
+    "maclab_adjoint_nu_term": (_S, [_H, _VP, _VP, _VP]),
     "maclab_get_planes": (_S, [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int32]),
     "maclab_set_planes": (_S, [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int32]),
     "maclab_state_bytes": (_S, [_H, ctypes.POINTER(ctypes.c_size_t)]),
@@ -118,7 +120,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libmaclab.so of this package, or the file MACLAB_LIBRARY names (e.g. the
+    bounds-checked debug build, _build.build(bounds_check=True))."""
+    return os.environ.get("MACLAB_LIBRARY") or _build.LIB
 
 
 def lib(build_if_missing: bool = False):
@@ -282,6 +286,13 @@ def maclab_diagnostics(h, raise_nonfinite=True):
             "max_u_lattice": out[6], "nonfinite": int(out[7]), "status": s}
 
 
+def maclab_debug_bounds():
+    """(count, first index) of bad indices met by the checked kernels (debug builds)."""
+    out = (ctypes.c_int64 * 2)()
+    _check(lib().maclab_debug_bounds(out), "maclab_debug_bounds")
+    return out[0], out[1]
+
+
 def maclab_diagnostics_sums(h):
     out = (ctypes.c_double * 9)()
     _check(lib().maclab_diagnostics_sums(h, out), "maclab_diagnostics_sums")
@@ -317,6 +328,12 @@ def maclab_adjoint_step(h, state_n, state_np1, lam_np1, lam_n, grad_force=None):
     """Device pointers (ints) or tensors for every array argument."""
     p = [_dev(a) for a in (state_n, state_np1, lam_np1, lam_n, grad_force)]
     return _check(lib().maclab_adjoint_step(h, *p), "maclab_adjoint_step")
+
+
+def maclab_adjoint_nu_term(h, state_n, lam_np1, acc):
+    """acc (device double) += sum_x lam_np1 . D_n (see maclab.h)."""
+    p = [_dev(a) for a in (state_n, lam_np1, acc)]
+    return _check(lib().maclab_adjoint_nu_term(h, *p), "maclab_adjoint_nu_term")
 
 
 def maclab_adjoint_seed(h, grad_rho, grad_u, state_T, lam_T):

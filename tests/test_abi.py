@@ -96,3 +96,10 @@ def test_noalloc_diagnostics_refuses_host_buffers(lib):
                                      out.ctypes.data, None)
     assert ei.value.status == M.ERR_INVALID
     assert np.all(out == 3.0)
+
+
+def test_debug_bounds_unsupported_in_normal_build(lib):
+    """maclab_debug_bounds exists only in the bounds-checked debug build."""
+    with pytest.raises(M.MacLABError) as ei:
+        M.maclab_debug_bounds()
+    assert ei.value.status == M.ERR_UNSUPPORTED

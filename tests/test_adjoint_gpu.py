@@ -82,6 +82,36 @@ def test_adjoint_step_matches_oracle(torch, lat, dims, periodic, walls, precisio
                                                           abs=tol * scale_u)
 
 
+@pytest.mark.parametrize("lat,dims,periodic,walls", [
+    (D2, (24, 17), 0b11, "none"), (D2, (20, 15), 0b01, "mixed"), (D2, (17, 13), 0b00, "box"),
+    (D3, (8, 8, 6), 0b111, "none"), (D3, (12, 9, 8), 0b000, "box"), (D3, (9, 8, 7), 0b101, "mixed")])
+@pytest.mark.parametrize("precision", [M.F64, M.F32])
+def test_viscosity_term_matches_oracle(torch, lat, dims, periodic, walls, precision):
+    """maclab_adjoint_nu_term (one reverse step's share of e dL/de) against the
+    oracle's plain definition (pinned on the CPU by finite differences in e)."""
+    d = len(dims)
+    case = inputs.random_case(lat, dims, periodic, seed=74, u_amp=0.08, rho_amp=0.02, walls=walls,
+                              force=tuple([3e-4] * d))
+    s = M.Solver.from_case(case, precision)        # e = 1, rho0 = 1: physical == lattice
+    s0 = _raw(torch, s)
+    g = inputs.rng(75)
+    lr1 = g.standard_normal(case.rho.shape)
+    lu1 = g.standard_normal(case.u.shape)
+    dt = torch.float64
+    lam1 = torch.empty(s.adjoint_bytes(), dtype=torch.uint8, device="cuda")
+    s.step(1)
+    s1 = _raw(torch, s)
+    M.maclab_adjoint_seed(s.handle, torch.tensor(lr1, dtype=dt, device="cuda"),
+                          torch.tensor(lu1, dtype=dt, device="cuda"), s1, lam1)
+    acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    M.maclab_adjoint_nu_term(s.handle, s0, lam1, acc)
+    got = float(acc.item())
+    s.close()
+    ref = orc.nu_term(lat, case.rho, case.u, periodic, lr1, lu1, wall=case.wall_mask, force=case.force)
+    tol = 1e-10 if precision == M.F64 else 1e-4
+    assert got == pytest.approx(ref, rel=tol)
+
+
 def _cavity_problem(n=20, lid=0.08, dx=0.05, nu=0.02, precision=M.F64, steps=25, seg=0):
     from paper_1901_02716_gb300.adjoint import RolloutSpec
     case = inputs.cavity2d(n, lid=lid)

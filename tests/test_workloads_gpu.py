@@ -94,15 +94,14 @@ def test_tgv3d_96_adjoint_rollout_2000_steps(precision):
     plus a seeded Gaussian perturbation (sigma = 1e-3 e), 2,000 steps with
     sqrt(N) checkpointing; L = ||u(T) - u_target||^2 with u_target the
     analytic decayed field u0 exp(-3 nu k^2 T).  Against fourth-order central
-    differences of FP64 GPU rollouts: dL/du0 along a random direction to 1e-4
-    relative in FP32 (1e-7 in FP64).  dL/dnu is a near-cancellation: nu enters
-    only through e, and at this amplitude the lattice flow is nearly linear, so
-    the e-scalings of input and output almost cancel and what remains is the
-    small nonlinear part (dL/dnu ~ 1e-5 against end-point terms ~100 times
-    larger); in FP32 the 2,000-step reverse pass then holds it to 1e-2
-    relative (measured 3.8e-3), in FP64 to 1e-6.  (The FP64 CPU reverse pass is
-    the reference on small problems in test_adjoint_gpu.py; at this size it
-    would take about a quarter of an hour.)"""
+    differences of FP64 GPU rollouts: dL/du0 along a random direction and
+    dL/dnu to 1e-4 relative in FP32 (1e-7 and 1e-6 in FP64).  nu enters only
+    through e, and at this amplitude the lattice flow is nearly linear, so the
+    e-scalings of input and output almost cancel (dL/dnu ~ 1e-5 against
+    end-point products ~100 times larger): the end-point form held FP32 to
+    only 1e-2 (3.8e-3 measured).  dL/dnu is now the sum of each reverse step's
+    term (maclab_adjoint_nu_term), formed directly.  (dL/du0 is also checked
+    against the oracle's own reverse pass in test_long_oracle_gpu.py.)"""
     torch = pytest.importorskip("torch")
     from paper_1901_02716_gb300.adjoint import RolloutSpec, rollout
     n, steps, dx, nu = 96, 2000, 1.0, 1.0 / 6.0   # e = 6 nu / dx = 1, dt = 1
@@ -134,5 +133,5 @@ def test_tgv3d_96_adjoint_rollout_2000_steps(precision):
     g_v = float(np.sum(u0_t.grad.cpu().numpy() * v))
     err = (abs(float(loss.detach()) / l64 - 1), abs(g_v / fd_v - 1), abs(nu_t.grad.item() / fd_nu - 1))
     print("loss, dL/du0.v, dL/dnu relative errors", err)
-    tol = (1e-4, 1e-4, 1e-2) if precision == M.F32 else (1e-10, 1e-7, 1e-6)
+    tol = (1e-4, 1e-4, 1e-4) if precision == M.F32 else (1e-10, 1e-7, 1e-6)
     assert all(e <= t for e, t in zip(err, tol)), err
