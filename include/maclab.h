@@ -239,6 +239,13 @@ maclab_status maclab_diagnostics(maclab_handle h, double out[8]);
  * invariants of Eq. (15).  Synchronises the stream. */
 maclab_status maclab_diagnostics_sums(maclab_handle h, double out[9]);
 
+/* The same raw sums written to device memory (out: 9 doubles on the handle's
+ * device; out[5] and out[6] are the residual sums over the state one step
+ * back, meaningful only when that state is held), asynchronously on the
+ * handle's stream: no host round trip, so it can sit between steps of a
+ * running loop.  Errors: MACLAB_ERR_INVALID, MACLAB_ERR_CUDA. */
+maclab_status maclab_diagnostics_device(maclab_handle h, double *out);
+
 /* Raw planes of the march axis (z in 3D, y in 2D) of the current lattice
  * state, for decomposing a domain into slabs along that axis.  A slab is a
  * domain closed along the axis whose first and last planes are wall nodes

@@ -819,6 +819,17 @@ maclab_status maclab_diagnostics(maclab_handle h, double out[8]) {
   return MACLAB_OK;
 }
 
+maclab_status maclab_diagnostics_device(maclab_handle h, double* out) {
+  NvtxRange nvtx_range("maclab_diagnostics_device");
+  if (!h || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  DeviceGuard dg(h->device);
+  CUDA_TRY(launch_diagnostics(h->g, h->precision, h->buf[h->cur],
+                              h->prev_valid ? h->buf[h->cur ^ 1] : nullptr, h->d_partial,
+                              h->diag_nblocks, out, h->stream),
+           "diagnostics kernel");
+  return MACLAB_OK;
+}
+
 maclab_status maclab_diagnostics_sums(maclab_handle h, double out[9]) {
   NvtxRange nvtx_range("maclab_diagnostics_sums");
   if (!h || !out) return fail(MACLAB_ERR_INVALID, "NULL argument");

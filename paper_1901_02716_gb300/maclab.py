@@ -65,6 +65,7 @@ SIGNATURES = {
     "maclab_get_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
     "maclab_set_wall_state": (_S, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32]),
     "maclab_diagnostics_sums": (_S, [_H, _VP]),
+    "maclab_diagnostics_device": (_S, [_H, _VP]),
     "maclab_debug_bounds": (_S, [_VP]),
     "maclab_adjoint_nu_term": (_S, [_H, _VP, _VP, _VP]),
     "maclab_get_planes": (_S, [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int32]),
@@ -291,6 +292,11 @@ def maclab_debug_bounds():
     out = (ctypes.c_int64 * 2)()
     _check(lib().maclab_debug_bounds(out), "maclab_debug_bounds")
     return out[0], out[1]
+
+
+def maclab_diagnostics_device(h, out):
+    """Raw sums (9 doubles) into the device buffer out, asynchronously."""
+    return _check(lib().maclab_diagnostics_device(h, _dev(out)), "maclab_diagnostics_device")
 
 
 def maclab_diagnostics_sums(h):

@@ -102,3 +102,21 @@ def test_graph_stepping_is_bit_identical(lat, dims, periodic, walls):
         assert s.params["steps"] == 37
         s.close()
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+@pytest.mark.parametrize("lat,dims,periodic,walls", [
+    (D2, (40, 23), 0b01, "mixed"), (D3, (16, 12, 10), 0b000, "box")])
+def test_device_sums_equal_host_sums(lat, dims, periodic, walls):
+    """maclab_diagnostics_device leaves in device memory the same raw sums,
+    bit for bit, that maclab_diagnostics_sums returns to the host."""
+    import torch
+    case = inputs.random_case(lat, dims, periodic, seed=53, u_amp=0.08, rho_amp=0.02, walls=walls)
+    s = M.Solver.from_case(case, M.F32)
+    s.step(2)
+    host = np.asarray(M.maclab_diagnostics_sums(s.handle))
+    out = torch.full((9,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    M.maclab_diagnostics_device(s.handle, out)
+    s.sync()
+    assert np.array_equal(out.cpu().numpy(), host)
+    s.close()
