@@ -304,12 +304,18 @@ maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {
   const size_t sb = state_bytes(h);
   h->diag_nblocks = diag_blocks(N);
   if (cudaMalloc(&h->buf[0], sb) != cudaSuccess || cudaMalloc(&h->buf[1], sb) != cudaSuccess ||
-      cudaMalloc(&h->d_partial, sizeof(double) * kDiagOut * h->diag_nblocks) != cudaSuccess ||
+      cudaMalloc(&h->d_partial, sizeof(double) * (kDiagOut * h->diag_nblocks + 1)) != cudaSuccess ||
       cudaMalloc(&h->d_diag, sizeof(double) * kDiagOut) != cudaSuccess ||
       cudaHostAlloc(&h->h_diag, sizeof(double) * kDiagOut, cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     free_ctx(h);
     return fail(MACLAB_ERR_OOM, "state allocation failed");
+  }
+  // the diagnostics kernel's ticket counter (after the block records) starts at 0
+  if (cudaMemsetAsync(h->d_partial + kDiagOut * h->diag_nblocks, 0, sizeof(double), h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    free_ctx(h);
+    return fail(MACLAB_ERR_CUDA, "diagnostics scratch initialisation failed");
   }
   if (n_wall > 0) {
     if (cudaMalloc(&h->d_node_type, (size_t)N) != cudaSuccess ||
@@ -519,6 +525,11 @@ maclab_status maclab_set_lattice_state(maclab_handle h, const void* state, int32
   h->prev_valid = false;
   if (where == MACLAB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream), "set_lattice_state sync");
   return MACLAB_OK;
+}
+
+// The diagnostics kernel's ticket counter: the word after the handle's block records.
+static unsigned* diag_ticket(const maclab_ctx* h) {
+  return reinterpret_cast<unsigned*>(h->d_partial + kDiagOut * h->diag_nblocks);
 }
 
 static StepLaunch step_launch(const maclab_ctx* h, int from) {
@@ -799,7 +810,7 @@ maclab_status maclab_diagnostics(maclab_handle h, double out[8]) {
   DeviceGuard dg(h->device);
   CUDA_TRY(launch_diagnostics(h->g, h->precision, h->buf[h->cur],
                               h->prev_valid ? h->buf[h->cur ^ 1] : nullptr, h->d_partial,
-                              h->diag_nblocks, h->d_diag, h->stream),
+                              diag_ticket(h), h->diag_nblocks, h->d_diag, h->stream, h->overlap),
            "diagnostics kernel");
   CUDA_TRY(cudaMemcpyAsync(h->h_diag, h->d_diag, kDiagOut * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
            "diagnostics D2H");
@@ -825,7 +836,7 @@ maclab_status maclab_diagnostics_device(maclab_handle h, double* out) {
   DeviceGuard dg(h->device);
   CUDA_TRY(launch_diagnostics(h->g, h->precision, h->buf[h->cur],
                               h->prev_valid ? h->buf[h->cur ^ 1] : nullptr, h->d_partial,
-                              h->diag_nblocks, out, h->stream),
+                              diag_ticket(h), h->diag_nblocks, out, h->stream, h->overlap),
            "diagnostics kernel");
   return MACLAB_OK;
 }
@@ -836,7 +847,7 @@ maclab_status maclab_diagnostics_sums(maclab_handle h, double out[9]) {
   DeviceGuard dg(h->device);
   CUDA_TRY(launch_diagnostics(h->g, h->precision, h->buf[h->cur],
                               h->prev_valid ? h->buf[h->cur ^ 1] : nullptr, h->d_partial,
-                              h->diag_nblocks, h->d_diag, h->stream),
+                              diag_ticket(h), h->diag_nblocks, h->d_diag, h->stream, h->overlap),
            "diagnostics kernel");
   CUDA_TRY(cudaMemcpyAsync(h->h_diag, h->d_diag, kDiagOut * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
            "diagnostics D2H");

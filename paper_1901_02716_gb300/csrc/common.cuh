@@ -207,7 +207,8 @@ void record_error(const char* msg);
 constexpr int kDiagOut = 9;
 int diag_blocks(int64_t n);
 cudaError_t launch_diagnostics(const Geometry& g, int precision, const void* cur, const void* prev,
-                               double* partial, int nblocks, double* out, cudaStream_t st);
+                               double* partial, unsigned* ticket, int nblocks, double* out,
+                               cudaStream_t st, int overlap);
 
 // Defined in adjoint.cu.
 cudaError_t launch_adjoint_step(const Geometry& g, int precision, const void* state_n,

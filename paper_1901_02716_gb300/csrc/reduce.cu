@@ -27,72 +27,211 @@ namespace maclab {
 constexpr int kDiagSlots = 9;
 
 // Running sum of one thread.  FP64 storage sums in FP64.  FP32 and 16-bit
-// storage form each node's products in FP32, and a thread adds them in
-// float-float: a pair (hi, lo) updated with Knuth's error-free two-sum, so the
-// rounding error of every FP32 addition is kept in lo and the pair carries
-// about 46 bits; it becomes one FP64 value at the end of the thread's loop.
-// All of this runs on the FP32 pipe (GB300's FP64 rate is a small fraction
-// of it), and the per-thread sums stay accurate to about 2^-46 of their size.
+// storage form each node's products in FP32 and add them in float-float: a
+// pair (hi, lo) updated with Knuth's error-free two-sum, so the rounding error
+// of every FP32 addition is kept in lo and the pair carries about 46 bits.
+// Threads, warps and blocks combine their pairs the same way (two-sum of the
+// hi parts, the lo parts and that error added), and only the nine final
+// values become FP64.  All of this runs on the FP32 pipe: GB300's FP64 rate is
+// a small fraction of it, and a reduction that folded its partial sums in FP64
+// spent much of its time there.
 template <typename C>
 struct DiagAcc;
 template <>
 struct DiagAcc<double> {
   double v = 0.0;
   __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void merge(const DiagAcc& o) { v += o.v; }
+  __device__ __forceinline__ DiagAcc shfl_down(int o) const {
+    DiagAcc r;
+    r.v = __shfl_down_sync(0xffffffffu, v, o);
+    return r;
+  }
+  __device__ __forceinline__ void store(double* w) const { *w = v; }
+  template <bool kGlobal>
+  __device__ __forceinline__ static DiagAcc load(const double* w) {
+    DiagAcc r;
+    r.v = kGlobal ? __ldcg(w) : *w;
+    return r;
+  }
   __device__ __forceinline__ double value() const { return v; }
 };
 template <>
 struct DiagAcc<float> {
   float hi = 0.f, lo = 0.f;
+  // s + err == a + b exactly (Knuth's two-sum; no FMA contraction in these
+  // steps: each is an explicitly rounded add or subtract)
+  __device__ __forceinline__ static float two_sum(float a, float b, float* err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    *err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+  }
   __device__ __forceinline__ void add(float x) {
-    const float s = __fadd_rn(hi, x);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-    hi = s;
+    float err;
+    hi = two_sum(hi, x, &err);
     lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ void merge(const DiagAcc& o) {
+    float err;
+    hi = two_sum(hi, o.hi, &err);
+    lo = __fadd_rn(lo, __fadd_rn(o.lo, err));
+  }
+  __device__ __forceinline__ DiagAcc shfl_down(int o) const {
+    DiagAcc r;
+    r.hi = __shfl_down_sync(0xffffffffu, hi, o);
+    r.lo = __shfl_down_sync(0xffffffffu, lo, o);
+    return r;
+  }
+  // one 8-byte word of a record holds the pair
+  __device__ __forceinline__ void store(double* w) const { *reinterpret_cast<float2*>(w) = make_float2(hi, lo); }
+  template <bool kGlobal>
+  __device__ __forceinline__ static DiagAcc load(const double* w) {
+    const float2* p = reinterpret_cast<const float2*>(w);
+    const float2 v = kGlobal ? __ldcg(p) : *p;
+    DiagAcc r;
+    r.hi = v.x;
+    r.lo = v.y;
+    return r;
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Everything one thread, warp or block has gathered: the seven sums, the
+// largest |u|^2 and the count of non-finite nodes.  A record of it is nine
+// 8-byte words (the slots of the output; word 7 holds max |u|^2 in the
+// arithmetic type, word 8 the count as an unsigned 64-bit integer).
+template <typename C>
+struct DiagPart {
+  DiagAcc<C> sum[kDiagSlots - 2];
+  C umax2 = C(0);
+  unsigned nonfinite = 0;
+
+  __device__ __forceinline__ void merge(const DiagPart& o) {
+#pragma unroll
+    for (int k = 0; k < kDiagSlots - 2; ++k) sum[k].merge(o.sum[k]);
+    umax2 = fmax(umax2, o.umax2);
+    nonfinite += o.nonfinite;
+  }
+  __device__ __forceinline__ DiagPart shfl_down(int o) const {
+    DiagPart r;
+#pragma unroll
+    for (int k = 0; k < kDiagSlots - 2; ++k) r.sum[k] = sum[k].shfl_down(o);
+    r.umax2 = __shfl_down_sync(0xffffffffu, umax2, o);
+    r.nonfinite = __shfl_down_sync(0xffffffffu, nonfinite, o);
+    return r;
+  }
+  __device__ __forceinline__ void store(double* rec) const {
+#pragma unroll
+    for (int k = 0; k < kDiagSlots - 2; ++k) sum[k].store(rec + k);
+    *reinterpret_cast<C*>(rec + 7) = umax2;
+    *reinterpret_cast<unsigned long long*>(rec + 8) = nonfinite;
+  }
+  template <bool kGlobal>
+  __device__ __forceinline__ static DiagPart load(const double* rec) {
+    DiagPart r;
+#pragma unroll
+    for (int k = 0; k < kDiagSlots - 2; ++k) r.sum[k] = DiagAcc<C>::template load<kGlobal>(rec + k);
+    const C* m = reinterpret_cast<const C*>(rec + 7);
+    const unsigned long long* c = reinterpret_cast<const unsigned long long*>(rec + 8);
+    r.umax2 = kGlobal ? __ldcg(m) : *m;
+    r.nonfinite = (unsigned)(kGlobal ? __ldcg(c) : *c);
+    return r;
+  }
+  // the nine output values; the root of max |u|^2 is taken once, here
+  __device__ __forceinline__ void output(double* out) const {
+#pragma unroll
+    for (int k = 0; k < kDiagSlots - 2; ++k) out[k] = sum[k].value();
+    out[7] = sqrt((double)umax2);
+    out[8] = (double)nonfinite;
+  }
+};
+
+// Folds the parts of a block's threads (blockDim.x a multiple of 32, at most
+// 1024) into one, held by thread 0.  Warps fold by shuffles; one record per
+// warp goes through shared memory and warp 0 folds those.
+template <typename C>
+__device__ __forceinline__ DiagPart<C> block_fold(DiagPart<C> t) {
+  __shared__ double red[32][kDiagSlots];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t.merge(t.shfl_down(o));
+  if (lane == 0) t.store(red[warp]);
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    t = lane < nw ? DiagPart<C>::template load<false>(red[lane]) : DiagPart<C>();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t.merge(t.shfl_down(o));
+  }
+  __syncthreads();  // red may be reused by a second fold
+  return t;
+}
+
+// The end of a diagnostics kernel.  Each block writes its record to
+// partial[blockIdx.x]; the last block to finish (a ticket counter that the
+// last one also returns to zero, atomicInc wrapping at gridDim.x - 1) reads
+// all the records and writes the nine output values.  No block waits for
+// another.  ticket must hold 0 before the launch; every launch leaves it 0.
+template <typename C>
+__device__ __forceinline__ void grid_fold(const DiagPart<C>& mine, double* __restrict__ partial,
+                                          unsigned* __restrict__ ticket, double* __restrict__ out) {
+  __shared__ bool last;
+  const DiagPart<C> b = block_fold(mine);
+  if (threadIdx.x == 0) {
+    b.store(partial + (int64_t)blockIdx.x * kDiagSlots);
+    __threadfence();  // the record is visible to every block before the ticket is taken
+    last = atomicInc(ticket, gridDim.x - 1) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  DiagPart<C> t;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
+    t.merge(DiagPart<C>::template load<true>(partial + (int64_t)k * kDiagSlots));
+  t = block_fold(t);
+  if (threadIdx.x == 0) {
+    double v[kDiagSlots];
+    t.output(v);
+#pragma unroll
+    for (int k = 0; k < kDiagSlots; ++k) out[k] = v[k];
+  }
+}
+
 template <typename S>
 __global__ void __launch_bounds__(256) diag_partial(Geometry g, const S* __restrict__ cur,
                                                     const S* __restrict__ prev,
-                                                    double* __restrict__ partial) {
+                                                    double* __restrict__ partial,
+                                                    unsigned* __restrict__ ticket,
+                                                    double* __restrict__ out) {
   using C = typename Store<S>::C;
-  DiagAcc<C> sum[kDiagSlots - 2];  // slots 0-6
-  float nonfinite = 0.f;
-  C umax2 = C(0);
+  pdl_wait();  // the step before this kernel has completed and its writes are visible
+  DiagPart<C> t;
   const int64_t N = g.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // storage position (mx, y, z) of m, advanced by the stride without dividing
   // (32-bit divisions where the node count allows: 64-bit ones are emulated)
-  int64_t q, sq;
   int mx, y, sx, sy;
   int64_t z, sz;
   if (N < (int64_t)INT32_MAX && stride < (int64_t)INT32_MAX) {
     const unsigned nx = (unsigned)g.nx, ny = (unsigned)g.ny;
     const unsigned m32 = (unsigned)(m < N ? m : 0), q32 = m32 / nx, s32 = (unsigned)stride, sq32 = s32 / nx;
-    q = q32;
     mx = (int)(m32 - q32 * nx);
     y = (int)(q32 % ny);
     z = q32 / ny;
-    sq = sq32;
     sx = (int)(s32 - sq32 * nx);
     sy = (int)(sq32 % ny);
     sz = sq32 / ny;
   } else {
-    q = m / g.nx;
+    const int64_t q = m / g.nx, sq = stride / g.nx;
     mx = (int)(m - q * g.nx);
     y = (int)(q % g.ny);
     z = q / g.ny;
-    sq = stride / g.nx;
     sx = (int)(stride - sq * g.nx);
     sy = (int)(sq % g.ny);
     sz = sq / g.ny;
   }
-  (void)q;
-  (void)sq;
   for (; m < N; m += stride) {
     bool wall = false;
     if (g.wall_mode == kWallMask) {
@@ -118,70 +257,52 @@ __global__ void __launch_bounds__(256) diag_partial(Geometry g, const S* __restr
     const C rho = C(1) + dr;
     C uu = C(0), du = C(0);
     bool finite = isfinite(dr);
-    sum[0].add(dr);
+    t.sum[0].add(dr);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       if (i >= g.d) break;
       const C u = Store<S>::from(cur[(1 + i) * N + m]);
       finite = finite && isfinite(u);
       uu = fma(u, u, uu);
-      sum[2 + i].add(rho * u);
+      t.sum[2 + i].add(rho * u);
       if (prev) {
         const C d = u - Store<S>::from(prev[(1 + i) * N + m]);
         du = fma(d, d, du);
       }
     }
-    sum[1].add(rho * uu);
-    sum[5].add(du);
-    sum[6].add(uu);
-    umax2 = fmax(umax2, uu);  // max |u|^2 here, its root below (the root is monotonic)
-    if (!finite) nonfinite += 1.f;
+    t.sum[1].add(rho * uu);
+    t.sum[5].add(du);
+    t.sum[6].add(uu);
+    t.umax2 = fmax(t.umax2, uu);  // max |u|^2 here, its root at the end (the root is monotonic)
+    if (!finite) ++t.nonfinite;
   }
-  double acc[kDiagSlots];
-#pragma unroll
-  for (int k = 0; k < kDiagSlots - 2; ++k) acc[k] = sum[k].value();
-  acc[7] = sqrt((double)umax2);
-  acc[8] = (double)nonfinite;
-  // block reduction: warp shuffles, then one value per warp through shared memory
-  __shared__ double red[kDiagSlots][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kDiagSlots; ++k) {
-    double v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) {
-      const double w = __shfl_down_sync(0xffffffffu, v, o);
-      v = k == 7 ? fmax(v, w) : v + w;
-    }
-    if (lane == 0) red[k][warp] = v;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kDiagSlots; ++k) {
-      double v = lane < nw ? red[k][lane] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) {
-        const double w = __shfl_down_sync(0xffffffffu, v, o);
-        v = k == 7 ? fmax(v, w) : v + w;
-      }
-      if (lane == 0) partial[(int64_t)blockIdx.x * kDiagSlots + k] = v;
-    }
-  }
+  grid_fold(t, partial, ticket, out);
 }
 
 // Rows of x (nx % 4 == 0): a warp takes whole rows, each lane 16-byte quads of
 // the four stored values of a node quad (vector loads, many in flight); rows on
 // a closed y or z boundary are wall rows and skipped as a whole, and in box
 // mode only the storage positions 0 and nx - 1 of a row (x = 0, nx - 1) are
-// x-walls.  Same per-node products and sums as diag_partial.
+// x-walls.  The stored density deviations are exact inputs and enter the
+// float-float sum node by node, as in diag_partial.  The per-node products
+// (rho |u|^2, rho u_i, |u - u_prev|^2, |u|^2) are each rounded to the
+// arithmetic type already; a quad's four are added in that type first and the
+// quad's sum enters the float-float sum (one two-sum per quad and slot instead
+// of one per node: three more roundings of the same size per quad, not an
+// error that grows with the node count; the sums differ from diag_partial's by
+// at most 5 units of 2^-24 of the sum of the terms' magnitudes).  A quad whose
+// summed density and |u|^2 are not finite holds a non-finite value (or
+// overflows) and is checked node by node.
 template <typename S>
-__global__ void __launch_bounds__(256) diag_rows(Geometry g, const S* __restrict__ cur,
-                                                 const S* __restrict__ prev, double* __restrict__ partial) {
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 3) diag_rows(Geometry g, const S* __restrict__ cur,
+                                                    const S* __restrict__ prev,
+                                                    double* __restrict__ partial,
+                                                    unsigned* __restrict__ ticket,
+                                                    double* __restrict__ out) {
   using C = typename Store<S>::C;
   using P = typename Quad<S>::P;
-  DiagAcc<C> sum[kDiagSlots - 2];
-  float nonfinite = 0.f;
-  C umax2 = C(0);
+  pdl_wait();  // the step before this kernel has completed and its writes are visible
+  DiagPart<C> t;
   const int64_t N = g.n;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -191,10 +312,20 @@ __global__ void __launch_bounds__(256) diag_rows(Geometry g, const S* __restrict
   const bool xw = g.wall_mode == kWallBox && !(g.periodic & 1u);
   const bool yw = g.wall_mode == kWallBox && !(g.periodic & 2u);
   const bool zw = g.wall_mode == kWallBox && g.d == 3 && !(g.periodic & 4u);
+  // (y, z) of the warp's row, advanced by nwarps rows a turn without dividing
+  int y = (int)(warp % g.ny);
+  int64_t z = warp / g.ny;
+  const int dy = (int)(nwarps % g.ny);
+  const int64_t dz = nwarps / g.ny;
   for (int64_t row = warp; row < rows; row += nwarps) {
-    const int y = (int)(row % g.ny);
-    const int64_t z = row / g.ny;
-    if ((yw && (y == 0 || y == g.ny - 1)) || (zw && (z == 0 || z == g.nz - 1))) continue;
+    const bool wall_row = (yw && (y == 0 || y == g.ny - 1)) || (zw && (z == 0 || z == g.nz - 1));
+    y += dy;
+    z += dz;
+    if (y >= g.ny) {
+      y -= g.ny;
+      ++z;
+    }
+    if (wall_row) continue;
     for (int q = lane; q < quads; q += 32) {
       const int64_t m = row * g.nx + 4 * q;
       bool wall[4] = {false, false, false, false};
@@ -213,6 +344,10 @@ __global__ void __launch_bounds__(256) diag_rows(Geometry g, const S* __restrict
         Quad<S>::ld(cur + (1 + i) * N + m, u[i][0], u[i][1]);
         if (prev) Quad<S>::ld(prev + (1 + i) * N + m, v[i][0], v[i][1]);
       }
+      // the quad's sums: drho, rho |u|^2, rho u_i, |u - u_prev|^2, |u|^2
+      C qs[kDiagSlots - 2];
+#pragma unroll
+      for (int k = 0; k < kDiagSlots - 2; ++k) qs[k] = C(0);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (wall[k]) continue;
@@ -221,92 +356,51 @@ __global__ void __launch_bounds__(256) diag_rows(Geometry g, const S* __restrict
         const C dr = pick(r[h]);
         const C rho = C(1) + dr;
         C uu = C(0), du = C(0);
-        bool finite = isfinite(dr);
-        sum[0].add(dr);
+        t.sum[0].add(dr);
+        qs[0] += dr;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           if (i >= g.d) break;
           const C ui = pick(u[i][h]);
-          finite = finite && isfinite(ui);
           uu = fma(ui, ui, uu);
-          sum[2 + i].add(rho * ui);
+          qs[2 + i] = fma(rho, ui, qs[2 + i]);
           if (prev) {
             const C d = ui - pick(v[i][h]);
             du = fma(d, d, du);
           }
         }
-        sum[1].add(rho * uu);
-        sum[5].add(du);
-        sum[6].add(uu);
-        umax2 = fmax(umax2, uu);
-        if (!finite) nonfinite += 1.f;
+        qs[1] = fma(rho, uu, qs[1]);
+        qs[5] += du;
+        qs[6] += uu;
+        t.umax2 = fmax(t.umax2, uu);
+      }
+#pragma unroll
+      for (int k = 0; k < kDiagSlots - 2; ++k) {
+        if (k == 0 || (k >= 2 && k < 5 && k - 2 >= g.d)) continue;
+        t.sum[k].add(qs[k]);
+      }
+      if (!isfinite(qs[0] + qs[6])) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (wall[k]) continue;
+          const int h = k >> 1;
+          const auto pick = [&](const P& p) { return (k & 1) ? p.y : p.x; };
+          bool finite = isfinite(pick(r[h]));
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            if (i >= g.d) break;
+            finite = finite && isfinite(pick(u[i][h]));
+          }
+          if (!finite) ++t.nonfinite;
+        }
       }
     }
   }
-  double acc[kDiagSlots];
-#pragma unroll
-  for (int k = 0; k < kDiagSlots - 2; ++k) acc[k] = sum[k].value();
-  acc[7] = sqrt((double)umax2);
-  acc[8] = (double)nonfinite;
-  __shared__ double red[kDiagSlots][32];
-  const int wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kDiagSlots; ++k) {
-    double v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) {
-      const double w = __shfl_down_sync(0xffffffffu, v, o);
-      v = k == 7 ? fmax(v, w) : v + w;
-    }
-    if (lane == 0) red[k][wid] = v;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kDiagSlots; ++k) {
-      double v = lane < nw ? red[k][lane] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) {
-        const double w = __shfl_down_sync(0xffffffffu, v, o);
-        v = k == 7 ? fmax(v, w) : v + w;
-      }
-      if (lane == 0) partial[(int64_t)blockIdx.x * kDiagSlots + k] = v;
-    }
-  }
+  grid_fold(t, partial, ticket, out);
 }
 
-// One block folds the partials: strided sums per thread, then warp shuffles
-// and one value per warp through shared memory.
-__global__ void __launch_bounds__(256) diag_final(const double* __restrict__ partial, int nblocks,
-                                                  double* __restrict__ out) {
-  __shared__ double red[kDiagSlots][8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kDiagSlots; ++k) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-      const double w = partial[(int64_t)b * kDiagSlots + k];
-      v = k == 7 ? fmax(v, w) : v + w;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double w = __shfl_down_sync(0xffffffffu, v, o);
-      v = k == 7 ? fmax(v, w) : v + w;
-    }
-    if (lane == 0) red[k][warp] = v;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int k = 0; k < kDiagSlots; ++k) {
-      double v = lane < 8 ? red[k][lane] : 0.0;
-      for (int o = 4; o > 0; o >>= 1) {
-        const double w = __shfl_down_sync(0xffffffffu, v, o);
-        v = k == 7 ? fmax(v, w) : v + w;
-      }
-      if (lane == 0) out[k] = v;
-    }
-  }
-}
-
+// Blocks of one launch: three 256-thread blocks per SM (the row kernel keeps
+// to 85 registers for that with FP32 arithmetic), fewer on small grids.
 int diag_blocks(int64_t n) {
   static int sms = 0;
   if (!sms) {
@@ -316,31 +410,34 @@ int diag_blocks(int64_t n) {
       sms = 148;
   }
   int64_t b = (n + 255) / 256;
-  if (b > 2 * sms) b = 2 * sms;
+  if (b > 3 * sms) b = 3 * sms;
   return (int)(b < 1 ? 1 : b);
 }
 
 template <typename S>
 static cudaError_t diag_t(const Geometry& g, const void* cur, const void* prev, double* partial,
-                          int nblocks, double* out, cudaStream_t st) {
+                          unsigned* ticket, int nblocks, double* out, cudaStream_t st, int overlap) {
   if (g.nx % 4 == 0)
-    diag_rows<S><<<nblocks, 256, 0, st>>>(g, (const S*)cur, (const S*)prev, partial);
-  else
-    diag_partial<S><<<nblocks, 256, 0, st>>>(g, (const S*)cur, (const S*)prev, partial);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  diag_final<<<1, 256, 0, st>>>(partial, nblocks, out);
-  return cudaGetLastError();
+    return launch_kernel(diag_rows<S>, dim3(nblocks), dim3(256), 0, st, overlap, g, (const S*)cur,
+                         (const S*)prev, partial, ticket, out);
+  return launch_kernel(diag_partial<S>, dim3(nblocks), dim3(256), 0, st, overlap, g, (const S*)cur,
+                       (const S*)prev, partial, ticket, out);
 }
 
-// partial: scratch of nblocks * kDiagSlots doubles; out: kDiagSlots doubles (device).
+// One kernel: per-block records in partial (nblocks * kDiagSlots doubles), the
+// last block's fold into out (kDiagSlots doubles, device).  ticket: one
+// counter on the device that holds 0 and that no other launch uses at the
+// same time; the launch leaves it 0.  overlap: launched with programmatic
+// dependent launch after a step kernel.
 cudaError_t launch_diagnostics(const Geometry& g, int precision, const void* cur, const void* prev,
-                               double* partial, int nblocks, double* out, cudaStream_t st) {
+                               double* partial, unsigned* ticket, int nblocks, double* out,
+                               cudaStream_t st, int overlap) {
   switch (precision) {
-    case MACLAB_F64: return diag_t<double>(g, cur, prev, partial, nblocks, out, st);
-    case MACLAB_F32: return diag_t<float>(g, cur, prev, partial, nblocks, out, st);
-    case MACLAB_BF16_STORE: return diag_t<__nv_bfloat16>(g, cur, prev, partial, nblocks, out, st);
-    case MACLAB_F16_STORE: return diag_t<__half>(g, cur, prev, partial, nblocks, out, st);
+    case MACLAB_F64: return diag_t<double>(g, cur, prev, partial, ticket, nblocks, out, st, overlap);
+    case MACLAB_F32: return diag_t<float>(g, cur, prev, partial, ticket, nblocks, out, st, overlap);
+    case MACLAB_BF16_STORE:
+      return diag_t<__nv_bfloat16>(g, cur, prev, partial, ticket, nblocks, out, st, overlap);
+    case MACLAB_F16_STORE: return diag_t<__half>(g, cur, prev, partial, ticket, nblocks, out, st, overlap);
   }
   return cudaErrorInvalidValue;
 }
@@ -349,13 +446,13 @@ cudaError_t launch_diagnostics(const Geometry& g, int precision, const void* cur
 //
 // For callers that cannot allocate device memory while they run (for example a
 // host loop that reserved all device memory for its own pool up front, or code
-// that may not block on an allocation): the same two kernels, with the
-// per-block partial sums in a fixed array that the module holds, instead of a
-// buffer owned by a handle.
+// that may not block on an allocation): the same kernels, with the per-block
+// records and the ticket counter in a fixed array that the module holds,
+// instead of a buffer owned by a handle.
 //
 // A call launches ceil(n / kNoAllocNodesPerBlock) blocks, so each block folds
 // about kNoAllocNodesPerBlock nodes (interleaved with the other blocks' by the
-// grid stride); the array holds kNoAllocMaxBlocks partials, which bounds one
+// grid stride); the array holds kNoAllocMaxBlocks records, which bounds one
 // call to kNoAllocMaxNodes nodes.
 
 constexpr int64_t kNoAllocMaxBlocks = 4096;
@@ -363,10 +460,13 @@ constexpr int64_t kNoAllocNodesPerBlock = 8192;
 constexpr int64_t kNoAllocMaxNodes = kNoAllocMaxBlocks * kNoAllocNodesPerBlock;  // 33,554,432
 
 // Held by every GPU that loads this module, until the process exits
-// (4096 x 9 doubles = 288 KiB).  Every call overwrites the entries it reads
-// before reading them, so nothing here has to start at zero; calls that
-// overlap on the GPU share it and race.
-static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * kDiagSlots];
+// (4096 x 9 records and one word for the ticket: 288 KiB).  Every call
+// overwrites the records it reads before reading them and sets the ticket to
+// 0 before its reduction starts, so nothing here has to start at zero; calls
+// that overlap on the GPU share it and race.
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * kDiagSlots + 1];
+
+__global__ void diag_ticket_reset(unsigned* ticket) { *ticket = 0u; }
 
 namespace {
 using CtxGetCurrent = int (*)(void**);  // cuCtxGetCurrent(CUcontext*), through the runtime
@@ -409,7 +509,9 @@ static cudaError_t noalloc_scratch(double** out) {
     cudaFuncAttributes fa{};
     const void* kernels[] = {(const void*)diag_partial<double>, (const void*)diag_partial<float>,
                              (const void*)diag_partial<__nv_bfloat16>, (const void*)diag_partial<__half>,
-                             (const void*)diag_final};
+                             (const void*)diag_rows<double>, (const void*)diag_rows<float>,
+                             (const void*)diag_rows<__nv_bfloat16>, (const void*)diag_rows<__half>,
+                             (const void*)diag_ticket_reset};
     for (const void* k : kernels) {
       e = cudaFuncGetAttributes(&fa, k);
       if (e != cudaSuccess) return e;
@@ -482,8 +584,12 @@ extern "C" maclab_status maclab_diagnostics_noalloc(int32_t lattice, int32_t pre
   g.wall_mode = exclude ? kWallMask : kWallNone;
   g.mask = exclude;
   const int nblocks = (int)((n_nodes + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock);
-  e = launch_diagnostics(g, precision, state, prev_state, partials, nblocks, out_sums,
-                         (cudaStream_t)stream);
+  unsigned* ticket = reinterpret_cast<unsigned*>(partials + kNoAllocMaxBlocks * kDiagSlots);
+  diag_ticket_reset<<<1, 1, 0, (cudaStream_t)stream>>>(ticket);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = launch_diagnostics(g, precision, state, prev_state, partials, ticket, nblocks, out_sums,
+                           (cudaStream_t)stream, 0);
   if (e != cudaSuccess) return err(MACLAB_ERR_CUDA, cudaGetErrorString(e));
   return MACLAB_OK;
 }

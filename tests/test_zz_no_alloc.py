@@ -96,15 +96,26 @@ def test_noalloc_matches_handle_diagnostics(label, make, precision):
                                      out.data_ptr(), stream)
         torch.cuda.synchronize()
         results.append(out.cpu().numpy().copy())
-    # momentum sums cancel: their rounding is bounded by n |u|max, not by the sum
-    mom_abs = 1e-12 * n * max(ref["max_u_lattice"], 1e-30)
+    # The stored density deviations are summed node by node on both paths
+    # (float-float, or FP64): mass agrees to 1e-12.  The per-node products
+    # (rho |u|^2, rho u_i, the residual's squares) are rounded to the arithmetic
+    # type on both paths, but the handle's row kernel adds a quad's four in that
+    # type before its float-float sum, and fuses the product into that add: with
+    # FP32 arithmetic (FP32 and 16-bit storage) each term differs by at most 5
+    # units of 2^-24 of its magnitude, so the sums differ by at most
+    # 5 * 2^-24 * sum |term|; with FP64 storage the same count of 2^-53 units.
+    rel = 5 * 2.0 ** -24 if precision != M.F64 else 1e-12
+    # momentum sums cancel: their rounding is bounded by the sum of |rho u_i|,
+    # at most n (1 + max |drho|) |u|max, not by the sum itself
+    mom_abs = max(rel, 1e-12) * n * 1.1 * max(ref["max_u_lattice"], 1e-30)
     for sums in results:
         assert np.all(np.isfinite(sums))
         assert n_fluid + sums[0] == pytest.approx(ref["mass"], rel=1e-12)
-        assert 0.5 * sums[1] == pytest.approx(ref["kinetic"], rel=1e-12)
+        assert 0.5 * sums[1] == pytest.approx(ref["kinetic"], rel=rel)
         for i in range(case.d):
             assert sums[2 + i] == pytest.approx(ref["momentum"][i], rel=1e-10, abs=mom_abs)
-        assert math.sqrt(sums[5] / sums[6]) == pytest.approx(ref["residual"], rel=1e-12)
+        # the residual's ratio: each of its two sums within rel
+        assert math.sqrt(sums[5] / sums[6]) == pytest.approx(ref["residual"], rel=rel)
         assert sums[7] == pytest.approx(ref["max_u_lattice"], rel=1e-15)
         assert sums[8] == ref["nonfinite"] == 0
     assert np.array_equal(results[0], results[1])
