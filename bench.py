@@ -436,8 +436,10 @@ def e2e_leg(M, case, prec, args, stream):
 
 
 def adjoint_leg(M, case, prec, args, stream):
-    """Time of one reverse step (maclab_adjoint_step, states already stored)
-    against one forward step, same workload and storage type."""
+    """Time of one reverse step of a rollout (maclab_adjoint_step_nu: the
+    reverse step with its viscosity term; states already stored) against one
+    forward step, same workload and storage type; beside it the reverse step
+    without the term and the per-node viscosity kernel alone."""
     import torch
     s = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
     nb = s.state_bytes()
@@ -464,11 +466,14 @@ def adjoint_leg(M, case, prec, args, stream):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / k
 
+    nu_acc = torch.zeros(1, dtype=torch.float64, device="cuda")
     t_fwd = timed(lambda i=0: s.step(1))
     t_adj = timed(lambda i=0: M.maclab_adjoint_step(s.handle, s0, s1, lam[i & 1], lam[(i + 1) & 1], gf))
+    t_nu = timed(lambda i=0: M.maclab_adjoint_nu_term(s.handle, s0, lam[i & 1], nu_acc))
     s.close()
     return {"forward_ms": t_fwd, "adjoint_ms": t_adj, "ratio": t_adj / t_fwd,
-            "adjoint_launches_per_step": 1}
+            "adjoint_launches_per_step": 1, "nu_term_ms": t_nu,
+            "ratio_with_nu_gradient": (t_adj + t_nu) / t_fwd}
 
 
 def diagnostics_leg(M, case, prec, stream):

@@ -15,7 +15,9 @@ time step).  dL/dnu is summed step by step during the reverse pass
 (maclab_adjoint_nu_term: the defect of each step under the e-scaling, dotted
 with the adjoint it produced), which keeps FP32 rollouts accurate where the
 end-point form (the difference of two nearly equal products, kept as
-``grads_extra["nu_endpoint"]``) loses digits.
+``grads_extra["nu_endpoint"]``) loses digits.  That term is a pass of its own
+per reverse step, so it is formed only when the viscosity's gradient is
+requested (nu.requires_grad).
 """
 from __future__ import annotations
 
@@ -93,6 +95,8 @@ class MacLABRollout(torch.autograd.Function):
                                       None if g_u is None else g_u.contiguous(), ctx.state_T, lam)
         gforce = torch.zeros(3, dtype=torch.float64, device="cuda")
         nu_acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+        # the viscosity term costs a pass per reverse step: only when dL/dnu is asked for
+        need_nu = bool(ctx.needs_input_grad[3])
         n, seg, ckpts = ctx.n, ctx.seg, ctx.ckpts
         bounds = [(i * seg, min((i + 1) * seg, n)) for i in range(len(ckpts))] if n else []
         for idx in range(len(bounds) - 1, -1, -1):
@@ -105,7 +109,8 @@ class MacLABRollout(torch.autograd.Function):
                 states.append(_raw(s))
             states.append(end_state)
             for k in range(b - a - 1, -1, -1):
-                M.maclab_adjoint_nu_term(h, states[k], lam, nu_acc)
+                if need_nu:
+                    M.maclab_adjoint_nu_term(h, states[k], lam, nu_acc)
                 M.maclab_adjoint_step(h, states[k], states[k + 1], lam, lam2, gforce)
                 lam, lam2 = lam2, lam
         ref = g_u if g_u is not None else g_rho
@@ -120,10 +125,12 @@ class MacLABRollout(torch.autograd.Function):
                                      device="cuda")
         # e dL/de = sum of the step terms; dL/dnu = (de/dnu) dL/de, de/dnu = 6 / dx
         e = s.params["e"]
-        grad_nu_steps = (6.0 / ctx.dx) * float(nu_acc.item()) / e
         res["nu_endpoint"] = res["nu"]
-        res["nu"] = grad_nu_steps
-        grad_nu = torch.tensor(grad_nu_steps, dtype=ctx.nu_dtype)
+        grad_nu = None
+        if need_nu:
+            grad_nu_steps = (6.0 / ctx.dx) * float(nu_acc.item()) / e
+            res["nu"] = grad_nu_steps
+            grad_nu = torch.tensor(grad_nu_steps, dtype=ctx.nu_dtype)
         ctx.grads_extra = res
         return grad_rho0, grad_u0, grad_wall, grad_nu, None
 

@@ -211,6 +211,30 @@ __global__ void __launch_bounds__(256) adj_gather(Geometry g, const S* __restric
 // the end-point products lam_T . ut_T and lam_0 . ut_0, which nearly cancel.
 // Sums use the integer weights 36 w_a and drop their constant parts exactly
 // (sum 36 w_a = 36, sum 36 w_a c_a = 0).
+// Running sum of one thread: FP64 for FP64 storage; float-float (Knuth's
+// two-sum, the error of every FP32 addition kept in lo) otherwise, so the
+// per-node terms, formed in FP32, are added without FP64 arithmetic.
+template <typename C>
+struct NuAcc {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct NuAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// One thread per node along the grid stride; the node's storage coordinates
+// advance with the stride (no division per node), and the storage offsets of
+// its 3 x 3 x 3 upstream neighbourhood are formed once per node.
 template <int LAT, typename S>
 __global__ void __launch_bounds__(256) adj_nu_term(Geometry g, const S* __restrict__ state,
                                                    const typename Store<S>::C* __restrict__ lam1,
@@ -221,21 +245,65 @@ __global__ void __launch_bounds__(256) adj_nu_term(Geometry g, const S* __restri
   constexpr int D = L::D;
   const int64_t N = g.n;
   const C force[3] = {C(f0), C(f1), C(f2)};
-  double sum = 0.0;
-  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < N;
-       m += (int64_t)gridDim.x * blockDim.x) {
-    const int x = log_x(g, (int)(m % g.nx));
-    const int y = (int)((m / g.nx) % g.ny);
-    const int z = (int)(m / ((int64_t)g.nx * g.ny));
-    if (wall_at<LAT>(g, x, y, z, m)) continue;
+  NuAcc<C> sum;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int mx, y, sx, sy;
+  int64_t z, sz;
+  if (N < (int64_t)INT32_MAX && stride < (int64_t)INT32_MAX) {
+    const unsigned nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+    const unsigned m32 = (unsigned)(m < N ? m : 0), q32 = m32 / nx, s32 = (unsigned)stride, sq32 = s32 / nx;
+    mx = (int)(m32 - q32 * nx);
+    y = (int)(q32 % ny);
+    z = q32 / ny;
+    sx = (int)(s32 - sq32 * nx);
+    sy = (int)(sq32 % ny);
+    sz = sq32 / ny;
+  } else {
+    const int64_t q = m / g.nx, sq = stride / g.nx;
+    mx = (int)(m - q * g.nx);
+    y = (int)(q % g.ny);
+    z = q / g.ny;
+    sx = (int)(stride - sq * g.nx);
+    sy = (int)(sq % g.ny);
+    sz = sq / g.ny;
+  }
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  for (; m < N; m += stride) {
+    const int x = log_x(g, mx);
+    const int yy = y;
+    const int64_t zz = z;
+    mx += sx;
+    const int carry = mx >= g.nx ? 1 : 0;
+    mx -= carry * g.nx;
+    y += sy + carry;
+    if (y >= g.ny) {
+      y -= g.ny;
+      z += 1;
+    }
+    z += sz;
+    if (wall_at<LAT>(g, x, yy, (int)zz, m)) continue;
+    // storage offsets of the source x - c: index k = c + 1 along each axis
+    int xo[3];
+    int64_t yo[3], zo[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      int xs = x - (k - 1), ys = yy - (k - 1);
+      xs = xs < 0 ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
+      ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+      xo[k] = mem_x(g, xs);
+      yo[k] = (int64_t)ys * g.nx;
+      int64_t zs = zz;
+      if (D == 3) {
+        zs = zz - (k - 1);
+        zs = zs < 0 ? zs + g.nz : (zs >= g.nz ? zs - g.nz : zs);
+      }
+      zo[k] = zs * plane;
+    }
     C R = 0, dR = 0, M[3] = {0, 0, 0}, Md[3] = {0, 0, 0};  // all x 36
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-      int xs = x - L::c(a, 0), ys = y - L::c(a, 1), zs = D == 3 ? z - L::c(a, 2) : 0;
-      xs = xs < 0 ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
-      ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
-      if (D == 3) zs = zs < 0 ? zs + g.nz : (zs >= g.nz ? zs - g.nz : zs);
-      const int64_t sidx = ((int64_t)zs * g.ny + ys) * g.nx + mem_x(g, xs);
+      const int64_t sidx = zo[(D == 3 ? L::c(a, 2) : 0) + 1] + yo[L::c(a, 1) + 1] + xo[L::c(a, 0) + 1];
       const C dr = (C)Store<S>::from(state[sidx]);
       const C rho = C(1) + dr;
       C cu = 0, uu = 0;
@@ -260,23 +328,42 @@ __global__ void __launch_bounds__(256) adj_nu_term(Geometry g, const S* __restri
       }
     }
     const C R36 = C(36) + R;                 // 36 rho'
-    double t = -(double)lam1[m] * (double)(dR / C(36));
+    C t = -lam1[m] * (dR / C(36));
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       const C unf = M[i] / R36;              // m' / rho'
       const C du = Md[i] / R36 + unf * (dR / R36) - force[i];
-      t += (double)lam1[(1 + i) * N + m] * (double)du;
+      t += lam1[(1 + i) * N + m] * du;
     }
-    sum += t;
+    sum.add(t);
   }
-  __shared__ double red[256];
-  red[threadIdx.x] = sum;
+  // block sum: warp shuffles, one value per warp, one FP64 atomic per block
+  double v = sum.value();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __shared__ double red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
   __syncthreads();
-  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
-    if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s2 += red[w];
+    atomicAdd(acc, s2);
   }
-  if (threadIdx.x == 0) atomicAdd(acc, red[0]);
+}
+
+// Blocks of the viscosity-term kernel: four 256-thread blocks per SM at most.
+static unsigned nu_blocks(int64_t n) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 148;
+  }
+  int64_t b = (n + 255) / 256;
+  if (b > 4 * sms) b = 4 * sms;
+  return (unsigned)(b < 1 ? 1 : b);
 }
 
 static unsigned grid256(int64_t n) {
@@ -336,19 +423,19 @@ static cudaError_t nu_term_lat(const Geometry& g, int precision, const void* sn,
                                const double* f, double* acc, cudaStream_t st) {
   switch (precision) {
     case MACLAB_F64:
-      adj_nu_term<LAT, double><<<grid256(g.n), 256, 0, st>>>(g, (const double*)sn, (const double*)lam1, f[0], f[1],
+      adj_nu_term<LAT, double><<<nu_blocks(g.n), 256, 0, st>>>(g, (const double*)sn, (const double*)lam1, f[0], f[1],
                                                             f[2], acc);
       break;
     case MACLAB_F32:
-      adj_nu_term<LAT, float><<<grid256(g.n), 256, 0, st>>>(g, (const float*)sn, (const float*)lam1, f[0], f[1],
+      adj_nu_term<LAT, float><<<nu_blocks(g.n), 256, 0, st>>>(g, (const float*)sn, (const float*)lam1, f[0], f[1],
                                                            f[2], acc);
       break;
     case MACLAB_BF16_STORE:
-      adj_nu_term<LAT, __nv_bfloat16><<<grid256(g.n), 256, 0, st>>>(g, (const __nv_bfloat16*)sn, (const float*)lam1,
+      adj_nu_term<LAT, __nv_bfloat16><<<nu_blocks(g.n), 256, 0, st>>>(g, (const __nv_bfloat16*)sn, (const float*)lam1,
                                                                    f[0], f[1], f[2], acc);
       break;
     case MACLAB_F16_STORE:
-      adj_nu_term<LAT, __half><<<grid256(g.n), 256, 0, st>>>(g, (const __half*)sn, (const float*)lam1, f[0], f[1],
+      adj_nu_term<LAT, __half><<<nu_blocks(g.n), 256, 0, st>>>(g, (const __half*)sn, (const float*)lam1, f[0], f[1],
                                                             f[2], acc);
       break;
     default: return cudaErrorInvalidValue;

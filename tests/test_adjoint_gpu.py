@@ -133,6 +133,31 @@ def _oracle_loss(case, dx, nu, rho0, u0, wall_u, target, steps):
     return float(np.sum((u * e - target) ** 2))
 
 
+@pytest.mark.parametrize("precision", [M.F64, M.F32])
+def test_rollout_without_viscosity_gradient(torch, precision):
+    """With nu not differentiated the reverse pass skips the viscosity term:
+    no gradient for nu, and the other gradients those of a rollout that also
+    differentiates nu (the term only reads the adjoint): the initial field's
+    bit for bit, the wall ids' to 1e-12 (their sums over wall nodes are FP64
+    atomics, whose order varies from run to run)."""
+    from paper_1901_02716_gb300.adjoint import rollout
+    dx, nu, steps = 0.05, 0.02, 12
+    case, spec, rho0, u0, wall_u, target, e = _cavity_problem(dx=dx, nu=nu, precision=precision,
+                                                             steps=steps, seg=5)
+    dt = torch.float64
+    grads = []
+    for nu_grad in (True, False):
+        u0_t = torch.tensor(u0, dtype=dt, device="cuda", requires_grad=True)
+        wall_t = torch.tensor(wall_u, dtype=dt, device="cuda", requires_grad=True)
+        nu_t = torch.tensor(nu, dtype=dt, requires_grad=nu_grad)
+        r_T, u_T = rollout(torch.tensor(rho0, dtype=dt, device="cuda"), u0_t, wall_t, nu_t, spec)
+        ((u_T - torch.tensor(target, dtype=dt, device="cuda")) ** 2).sum().backward()
+        grads.append((u0_t.grad.clone(), wall_t.grad.clone(), nu_t.grad))
+    assert grads[0][2] is not None and grads[1][2] is None
+    assert torch.equal(grads[0][0], grads[1][0])
+    assert torch.allclose(grads[0][1], grads[1][1], rtol=1e-12, atol=0.0)
+
+
 @pytest.mark.parametrize("precision,tol", [(M.F64, 1e-7), (M.F32, 1e-4)])
 def test_rollout_gradients(torch, precision, tol):
     from paper_1901_02716_gb300.adjoint import rollout
