@@ -469,7 +469,7 @@ def adjoint_leg(M, case, prec, args, stream):
     nu_acc = torch.zeros(1, dtype=torch.float64, device="cuda")
     t_fwd = timed(lambda i=0: s.step(1))
     t_adj = timed(lambda i=0: M.maclab_adjoint_step(s.handle, s0, s1, lam[i & 1], lam[(i + 1) & 1], gf))
-    t_nu = timed(lambda i=0: M.maclab_adjoint_nu_term(s.handle, s0, lam[i & 1], nu_acc))
+    t_nu = timed(lambda i=0: M.maclab_adjoint_nu_term(s.handle, s0, lam[i & 1], nu_acc, s1))
     s.close()
     return {"forward_ms": t_fwd, "adjoint_ms": t_adj, "ratio": t_adj / t_fwd,
             "adjoint_launches_per_step": 1, "nu_term_ms": t_nu,

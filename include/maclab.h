@@ -373,10 +373,16 @@ maclab_status maclab_adjoint_step(maclab_handle h, const void *state_n, const vo
  * dL/dnu = (6 / dx) (1 / e) sum; each term is formed directly, without the
  * near-cancellation of the end-point products that maclab_adjoint_finish
  * subtracts (which loses accuracy in FP32 when the flow is nearly linear in u).
+ * state_np1 (optional, may be NULL): the raw state that step produced.  With
+ * it, on FP32 storage where the two-rows-per-thread D3Q19 step is built, the
+ * term is one tiled pass: it gathers the moments of
+ * g_a = w_a (drho + rho (3/2 u.u - 9/2 (c.u)^2)) and takes rho' and m' / rho'
+ * from state_np1 (J (0, ut) on drho = R - sum g, with R = 36 drho').  Without
+ * it (or elsewhere) a per-node kernel gathers the 19 neighbours of every node.
  * Asynchronous on the handle's stream.  Errors: MACLAB_ERR_INVALID,
  * MACLAB_ERR_CUDA. */
-maclab_status maclab_adjoint_nu_term(maclab_handle h, const void *state_n, const void *lam_np1,
-                                     double *acc);
+maclab_status maclab_adjoint_nu_term(maclab_handle h, const void *state_n, const void *state_np1,
+                                     const void *lam_np1, double *acc);
 
 /* Seed the reverse pass: the gradients of the loss with respect to the
  * physical output fields rho (N values) and u (d * N values, logical order;

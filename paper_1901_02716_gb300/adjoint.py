@@ -110,7 +110,7 @@ class MacLABRollout(torch.autograd.Function):
             states.append(end_state)
             for k in range(b - a - 1, -1, -1):
                 if need_nu:
-                    M.maclab_adjoint_nu_term(h, states[k], lam, nu_acc)
+                    M.maclab_adjoint_nu_term(h, states[k], lam, nu_acc, states[k + 1])
                 M.maclab_adjoint_step(h, states[k], states[k + 1], lam, lam2, gforce)
                 lam, lam2 = lam2, lam
         ref = g_u if g_u is not None else g_rho

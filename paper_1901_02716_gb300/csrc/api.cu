@@ -738,10 +738,17 @@ maclab_status maclab_adjoint_step(maclab_handle h, const void* state_n, const vo
   return MACLAB_OK;
 }
 
-maclab_status maclab_adjoint_nu_term(maclab_handle h, const void* state_n, const void* lam_np1, double* acc) {
+maclab_status maclab_adjoint_nu_term(maclab_handle h, const void* state_n, const void* state_np1,
+                                     const void* lam_np1, double* acc) {
   NvtxRange nvtx_range("maclab_adjoint_nu_term");
   if (!h || !state_n || !lam_np1 || !acc) return fail(MACLAB_ERR_INVALID, "NULL argument");
   DeviceGuard dg(h->device);
+  if (state_np1 && h->kernel != MACLAB_KERNEL_REFERENCE && rows2_nu_supported(h->g, h->precision)) {
+    CUDA_TRY(launch_rows2_nu(h->g, state_n, state_np1, static_cast<const float*>(lam_np1), h->force_lat, acc,
+                             h->stream),
+             "adjoint nu term (two-rows kernel)");
+    return MACLAB_OK;
+  }
   CUDA_TRY(launch_adjoint_nu_term(h->g, h->precision, state_n, lam_np1, h->force_lat, acc, h->stream),
            "adjoint nu term");
   return MACLAB_OK;

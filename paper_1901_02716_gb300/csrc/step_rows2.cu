@@ -97,4 +97,38 @@ cudaError_t launch_rows2(const StepLaunch& sl, cudaStream_t stream, int ty, int 
   return dispatch(sl.in, sl.out, dim3(ta.nzc, ytiles), nullptr);
 }
 
+bool rows2_nu_supported(const Geometry& g, int precision) {
+  Rows2Shape s;
+  return precision == MACLAB_F32 && rows2_shape(g, precision, 0, &s);
+}
+
+cudaError_t launch_rows2_nu(const Geometry& g, const void* state_n, const void* state_np1, const float* lam,
+                            const double force[3], double* acc, cudaStream_t stream) {
+  Rows2Shape s;
+  if (!rows2_nu_supported(g, MACLAB_F32) || !rows2_shape(g, MACLAB_F32, 0, &s)) return cudaErrorInvalidValue;
+  TiledArgs ta{};
+  ta.nx = g.nx;
+  ta.ny = g.ny;
+  ta.nplanes = g.nz;
+  ta.n = g.n;
+  ta.plane_stride = (int64_t)g.nx * g.ny;
+  ta.ty = 2 * s.tyt;
+  const int ytiles = g.ny / ta.ty;
+  int resident = 0;
+  cudaError_t e = rows2_nu_dispatch(s.bxc, s.tyt, ta, nullptr, nullptr, stream, dim3(), &resident);
+  if (e != cudaSuccess) return e;
+  ta.nzc = fold_chunks(ta.nplanes, ytiles, 0, resident);
+  ta.px = (g.periodic & 1u) ? 1 : 0;
+  ta.py = (g.periodic & 2u) ? 1 : 0;
+  ta.pz = (g.periodic & 4u) ? 1 : 0;
+  ta.wall_mode = g.wall_mode;
+  ta.mask = g.mask;
+  for (int i = 0; i < 3; ++i) ta.force[i] = force[i];
+  ta.overlap = 0;
+  ta.bounds = bounds_log();
+  ta.lam = lam;
+  ta.nu_acc = acc;
+  return rows2_nu_dispatch(s.bxc, s.tyt, ta, state_n, state_np1, stream, dim3(ta.nzc, ytiles), nullptr);
+}
+
 }  // namespace maclab

@@ -38,6 +38,16 @@
 //
 // Requires: D3Q19, FP32 arithmetic (FP32, BF16 or FP16 storage), nx % 4 == 0,
 // nx / 4 <= BXC, ny % TY == 0, TYT >= 2.
+//
+// Viscosity-term mode (NU, FP32 storage): the same march and exchanges gather
+// the moments of g_a = w_a (drho + rho (3/2 u.u - 9/2 (c.u)^2)) (the
+// equilibrium less its derivative along u and its constant: Eq. (2) with no
+// linear part and the quadratic part negated) instead of Eq. (2) itself, and
+// the store becomes a sum: with R and u' of the stored state after the step,
+// drho' along u is dR = R - G0, and each fluid node adds
+//   lam_rho (-dR / 36) + sum_i lam_u_i (Md_i / (36 + R) + (u'_i - F_i) dR / (36 + R) - F_i),
+// Md = the first moments of g, into the accumulator (the term of
+// maclab_adjoint_nu_term, per node as in adj_nu_term).
 
 #pragma once
 #include "step_fold.cuh"
@@ -91,8 +101,43 @@ __device__ __forceinline__ void make_terms3(typename Pair<C>::P r, const typenam
     }
 }
 
+// Terms of g_a / w_a = drho + rho (3/2 u.u - 9/2 (c.u)^2) in the same slots:
+// A = drho + 3/2 rho u.u, S_i = A - 9/2 rho u_i^2, and for the pair (i, j)
+// Ep = S_i - 9/2 rho u_j^2 - 9 rho u_i u_j, Em = ... + 9 rho u_i u_j; no B, O.
+template <typename C>
+__device__ __forceinline__ void make_terms3_nu(typename Pair<C>::P r, const typename Pair<C>::P (&u)[3],
+                                               Terms3<C>& t) {
+  using O = Pair<C>;
+  using P = typename O::P;
+  const P g = O::fma(r, O::splat(C(3)), O::splat(C(3)));  // 3 (1 + drho)
+  P B[3], Pd[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    B[i] = O::mul(g, u[i]);
+    Pd[i] = O::mul(O::mul(B[i], u[i]), O::splat(C(1.5)));  // 9/2 rho u_i^2
+  }
+  const P psum = O::add(O::add(Pd[0], Pd[1]), Pd[2]);
+  t.A = O::fma(psum, O::splat(C(1.0 / 3.0)), r);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t.S[i] = O::sub(t.A, Pd[i]);
+  const P B30 = O::mul(B[0], O::splat(C(3)));
+  const P B31 = O::mul(B[1], O::splat(C(3)));
+  const P nu1 = O::sub(O::splat(C(0)), u[1]);
+  const P nu2 = O::sub(O::splat(C(0)), u[2]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 3; ++j) {
+      const int k = pair_index(i, j);
+      const P base = O::sub(t.S[i], Pd[j]);
+      const P b3 = i == 0 ? B30 : B31;
+      t.Ep[k] = O::fma(b3, j == 1 ? nu1 : nu2, base);
+      t.Em[k] = O::fma(b3, u[j], base);
+    }
+}
+
 // T_a of both lanes (axis directions undoubled: they carry the weight 2)
-template <typename C, int A>
+template <typename C, int A, bool NU = false>
 __device__ __forceinline__ typename Pair<C>::P term3(const Terms3<C>& t) {
   using L = Lattice<kD3Q19>;
   using O = Pair<C>;
@@ -101,12 +146,15 @@ __device__ __forceinline__ typename Pair<C>::P term3(const Terms3<C>& t) {
   if constexpr (nzc == 0) {
     return t.A;
   } else if constexpr (nzc == 1) {
-    if constexpr (L::c(A, i0) > 0) return O::add(t.S[i0], t.B[i0]);
+    if constexpr (NU) return t.S[i0];
+    else if constexpr (L::c(A, i0) > 0) return O::add(t.S[i0], t.B[i0]);
     else return O::sub(t.S[i0], t.B[i0]);
   } else {
     constexpr int k = pair_index(i0, i1);
     constexpr int s0 = L::c(A, i0), s1 = L::c(A, i1);
-    if constexpr (s0 == s1) {
+    if constexpr (NU) {
+      return s0 == s1 ? t.Ep[k] : t.Em[k];
+    } else if constexpr (s0 == s1) {
       if constexpr (s0 > 0) return O::add(t.Ep[k], t.Op[k]);
       else return O::sub(t.Ep[k], t.Op[k]);
     } else {
@@ -180,7 +228,21 @@ struct Rows2Layout {
 
 // ------------------------------------------------------------------ kernel
 
-template <typename S, int BXC, int TYT>
+// Running float-float sum of one thread (viscosity-term mode): Knuth's two-sum
+// keeps the rounding error of every FP32 addition.
+struct Rows2Sum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+    hi = s;
+  }
+};
+
+// NU: viscosity-term mode (see the top of this file); `out` is then the state
+// after the step, read only.
+template <typename S, int BXC, int TYT, bool NU = false>
 __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCKS)
     step_rows2(TiledArgs ta, const S* __restrict__ in, S* __restrict__ out) {
   using Lay = Rows2Layout<S, BXC, TYT>;
@@ -401,13 +463,14 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
         Terms3<C> t;
         {
           const P u[3] = {st[j][1][q], st[j][2][q], st[j][3][q]};
-          make_terms3<C>(st[j][0][q], u, t);
+          if constexpr (NU) make_terms3_nu<C>(st[j][0][q], u, t);
+          else make_terms3<C>(st[j][0][q], u, t);
         }
         static_for<0, L::Q>([&](auto I) {
           constexpr int a = decltype(I)::value;
           if constexpr (mode_allows<kD3Q19, MODE>(a)) {
             constexpr int fx = F::fx(a), fy = F::fy(a), fz = F::fz(a);
-            const P T = term3<C, a>(t);
+            const P T = term3<C, a, NU>(t);
             if constexpr (fy == 0) {
               auto& dst = pick<fz>(ap, ac, an)[j];
               constexpr int qd = q + fx;
@@ -451,19 +514,20 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const P u[3] = {hs[1][q], hs[2][q], hs[3][q]};
-        make_terms3<C>(hs[0][q], u, t[q]);
+        if constexpr (NU) make_terms3_nu<C>(hs[0][q], u, t[q]);
+        else make_terms3<C>(hs[0][q], u, t[q]);
       }
       if (halo == 1) {
         static_for<0, L::Q>([&](auto I) {
           constexpr int a = decltype(I)::value;
           if constexpr (mode_allows<kD3Q19, MODE>(a) && F::fy(a) == 1)
-            publish(ybase, I, 0, term3<C, a>(t[0]), term3<C, a>(t[1]));
+            publish(ybase, I, 0, term3<C, a, NU>(t[0]), term3<C, a, NU>(t[1]));
         });
       } else {
         static_for<0, L::Q>([&](auto I) {
           constexpr int a = decltype(I)::value;
           if constexpr (mode_allows<kD3Q19, MODE>(a) && F::fy(a) == -1)
-            publish(ybase, I, TYT, term3<C, a>(t[0]), term3<C, a>(t[1]));
+            publish(ybase, I, TYT, term3<C, a, NU>(t[0]), term3<C, a, NU>(t[1]));
         });
       }
     }
@@ -497,7 +561,7 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   // node (x = 0 or nx - 1, row0) of field 0: in bounds for every lane
   const S* const wall_src = in + (int64_t)row0 * ta.nx + (x_hi_wall ? ta.nx - 1 : 0);
   auto load_walls = [&](int q) {
-    if (box_x && q >= 0 && q < ta.nplanes) {
+    if (!NU && box_x && q >= 0 && q < ta.nplanes) {
 #pragma unroll
       for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -507,8 +571,54 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
         }
     }
   };
+  Rows2Sum nus;  // viscosity-term mode: this thread's sum
   auto store = [&](int q, P(&acc)[2][2][4]) {
     const bool zskip = zwall && (q == 0 || q == ta.nplanes - 1);
+    if constexpr (NU) {
+      // the viscosity term of the fluid nodes of the two rows: R and u' from the
+      // stored state after the step, lam from ta.lam
+      const float* const lam = ta.lam;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (!active || row_wall[j] || zskip) continue;
+        const int64_t off = (int64_t)q * ps + j * nx64;
+        P sn[4][2], lm[4][2];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const int64_t e = f * ta.n + in_off + off;
+          if (bounds_ok(ta.bounds, e, n4 - 3)) {
+            Quad<S>::ld(out + e, sn[f][0], sn[f][1]);
+            Quad<float>::ld(lam + e, lm[f][0], lm[f][1]);
+          } else {
+            sn[f][0] = sn[f][1] = lm[f][0] = lm[f][1] = O::splat(C(0));
+          }
+        }
+        // fluid lanes: (pair a.x, a.y, b.x, b.y) = storage positions 4 tx .. 4 tx + 3
+        bool fl[4] = {!x_lo_wall, true, true, !x_hi_wall};
+        if (ta.wall_mode == kWallMask) {
+          const uchar4 mk = *reinterpret_cast<const uchar4*>(mrow + off);
+          fl[0] = mk.x == 0; fl[1] = mk.y == 0; fl[2] = mk.z == 0; fl[3] = mk.w == 0;
+        }
+        float part = 0.f;
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+          const P R = O::mul(sn[0][qq], O::splat(C(36)));
+          const P inv = O::rcp(O::add(O::splat(C(36)), R));
+          const P dR = O::sub(R, acc[j][qq][0]);
+          const P dRi = O::mul(dR, inv);
+          P t = O::mul(lm[0][qq], O::mul(dR, O::splat(C(-1.0 / 36.0))));
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const P unf = O::sub(sn[1 + i][qq], force[i]);
+            const P du = O::sub(O::fma(unf, dRi, O::mul(acc[j][qq][1 + i], inv)), force[i]);
+            t = O::fma(lm[1 + i][qq], du, t);
+          }
+          part += (fl[2 * qq] ? t.x : 0.f) + (fl[2 * qq + 1] ? t.y : 0.f);
+        }
+        nus.add(part);
+      }
+      return;
+    }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const bool skip = !active || row_wall[j] || zskip;
@@ -590,6 +700,21 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
     store(z1 - 1, R0);
   }
   cp_async_wait<0>();
+  if constexpr (NU) {
+    // block sum: warp shuffles, one value per warp, one FP64 atomic per block
+    double v = (double)nus.hi + (double)nus.lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __shared__ double red[32];
+    const int lid = tr * BXC + tx;
+    if ((lid & 31) == 0) red[lid >> 5] = v;
+    __syncthreads();
+    if (lid == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < (BXC * TYT) / 32; ++w) sum += red[w];
+      atomicAdd(ta.nu_acc, sum);
+    }
+  }
 }
 
 // Launch of the instance (bxc, tyt) for storage type S (FP32 instances in
@@ -597,13 +722,16 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
 template <typename S>
 cudaError_t rows2_dispatch(int bxc, int tyt, const TiledArgs& ta, const void* in, void* out,
                            cudaStream_t st, dim3 grid, int* resident);
+// The viscosity-term mode, FP32 storage (instances in step_rows2_nu.cu).
+cudaError_t rows2_nu_dispatch(int bxc, int tyt, const TiledArgs& ta, const void* in, const void* out,
+                              cudaStream_t st, dim3 grid, int* resident);
 
 // Launch one instance.  With resident_out set,
 // only report the blocks of this shape one SM holds.
-template <typename S, int BXC, int TYT>
+template <typename S, int BXC, int TYT, bool NU = false>
 cudaError_t launch_rows2_shape(const TiledArgs& ta, const void* in, void* out, cudaStream_t stream,
                                dim3 grid, int* resident_out) {
-  auto kern = step_rows2<S, BXC, TYT>;
+  auto kern = step_rows2<S, BXC, TYT, NU>;
   constexpr size_t smem = Rows2Layout<S, BXC, TYT>::smem;
   static int resident_dev[64] = {};
   int dev = 0;

@@ -76,6 +76,8 @@ struct TiledArgs {
   double force[3];
   int overlap;             // host side: launch with programmatic dependent launch
   BoundsLog* bounds;       // debug builds: where bad indices are recorded (bounds_ok)
+  const float* lam;        // viscosity-term launches: the adjoint of the state after the step
+  double* nu_acc;          // viscosity-term launches: the sum's accumulator (one double)
 };
 
 // ------------------------------------------------------------------ lane pairs

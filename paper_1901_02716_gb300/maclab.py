@@ -67,7 +67,7 @@ SIGNATURES = {
     "maclab_diagnostics_sums": (_S, [_H, _VP]),
     "maclab_diagnostics_device": (_S, [_H, _VP]),
     "maclab_debug_bounds": (_S, [_VP]),
-    "maclab_adjoint_nu_term": (_S, [_H, _VP, _VP, _VP]),
+    "maclab_adjoint_nu_term": (_S, [_H, _VP, _VP, _VP, _VP]),
     "maclab_get_planes": (_S, [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int32]),
     "maclab_set_planes": (_S, [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int32]),
     "maclab_state_bytes": (_S, [_H, ctypes.POINTER(ctypes.c_size_t)]),
@@ -336,9 +336,10 @@ def maclab_adjoint_step(h, state_n, state_np1, lam_np1, lam_n, grad_force=None):
     return _check(lib().maclab_adjoint_step(h, *p), "maclab_adjoint_step")
 
 
-def maclab_adjoint_nu_term(h, state_n, lam_np1, acc):
-    """acc (device double) += sum_x lam_np1 . D_n (see maclab.h)."""
-    p = [_dev(a) for a in (state_n, lam_np1, acc)]
+def maclab_adjoint_nu_term(h, state_n, lam_np1, acc, state_np1=None):
+    """acc (device double) += sum_x lam_np1 . D_n (see maclab.h); state_np1, the
+    state after the step, selects the tiled pass where it is built."""
+    p = [_dev(a) for a in (state_n, state_np1, lam_np1, acc)]
     return _check(lib().maclab_adjoint_nu_term(h, *p), "maclab_adjoint_nu_term")
 
 

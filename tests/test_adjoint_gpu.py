@@ -84,11 +84,17 @@ def test_adjoint_step_matches_oracle(torch, lat, dims, periodic, walls, precisio
 
 @pytest.mark.parametrize("lat,dims,periodic,walls", [
     (D2, (24, 17), 0b11, "none"), (D2, (20, 15), 0b01, "mixed"), (D2, (17, 13), 0b00, "box"),
-    (D3, (8, 8, 6), 0b111, "none"), (D3, (12, 9, 8), 0b000, "box"), (D3, (9, 8, 7), 0b101, "mixed")])
+    (D3, (8, 8, 6), 0b111, "none"), (D3, (12, 9, 8), 0b000, "box"), (D3, (9, 8, 7), 0b101, "mixed"),
+    # shapes of the two-rows kernel's viscosity mode (FP32): rows of 2 to 32 quads,
+    # idle lanes, obstacle masks, box walls, every periodicity
+    (D3, (16, 8, 7), 0b101, "mixed"), (D3, (32, 16, 9), 0b000, "box"), (D3, (128, 8, 6), 0b010, "box"),
+    (D3, (4, 16, 5), 0b000, "box"), (D3, (40, 8, 12), 0b111, "none")])
 @pytest.mark.parametrize("precision", [M.F64, M.F32])
 def test_viscosity_term_matches_oracle(torch, lat, dims, periodic, walls, precision):
     """maclab_adjoint_nu_term (one reverse step's share of e dL/de) against the
-    oracle's plain definition (pinned on the CPU by finite differences in e)."""
+    oracle's plain definition (pinned on the CPU by finite differences in e):
+    the per-node kernel (no state after the step given) and, given that state,
+    the tiled pass where it is built."""
     d = len(dims)
     case = inputs.random_case(lat, dims, periodic, seed=74, u_amp=0.08, rho_amp=0.02, walls=walls,
                               force=tuple([3e-4] * d))
@@ -104,12 +110,15 @@ def test_viscosity_term_matches_oracle(torch, lat, dims, periodic, walls, precis
     M.maclab_adjoint_seed(s.handle, torch.tensor(lr1, dtype=dt, device="cuda"),
                           torch.tensor(lu1, dtype=dt, device="cuda"), s1, lam1)
     acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    acc_t = torch.zeros(1, dtype=torch.float64, device="cuda")
     M.maclab_adjoint_nu_term(s.handle, s0, lam1, acc)
-    got = float(acc.item())
+    M.maclab_adjoint_nu_term(s.handle, s0, lam1, acc_t, s1)
+    got, got_t = float(acc.item()), float(acc_t.item())
     s.close()
     ref = orc.nu_term(lat, case.rho, case.u, periodic, lr1, lu1, wall=case.wall_mask, force=case.force)
     tol = 1e-10 if precision == M.F64 else 1e-4
     assert got == pytest.approx(ref, rel=tol)
+    assert got_t == pytest.approx(ref, rel=tol)
 
 
 def _cavity_problem(n=20, lid=0.08, dx=0.05, nu=0.02, precision=M.F64, steps=25, seg=0):
