@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
         }
         // fluid lanes: (pair a.x, a.y, b.x, b.y) = storage positions 4 tx .. 4 tx + 3
         bool fl[4] = {!x_lo_wall, true, true, !x_hi_wall};
-        if (ta.wall_mode == kWallMask) {
+        if (ta.wall_mode == kWallMask && bounds_ok(ta.bounds, in_off + off, ta.n - 3)) {
           const uchar4 mk = *reinterpret_cast<const uchar4*>(mrow + off);
           fl[0] = mk.x == 0; fl[1] = mk.y == 0; fl[2] = mk.z == 0; fl[3] = mk.w == 0;
         }
