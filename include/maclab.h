@@ -481,7 +481,10 @@ maclab_status maclab_measure_fp32_peak(double *tflops);
  * MACLAB_ERR_UNSUPPORTED in normal builds, MACLAB_ERR_INVALID, MACLAB_ERR_CUDA. */
 maclab_status maclab_debug_bounds(int64_t out[2]);
 
-/* Run the handle's stream to completion and report any CUDA error. */
+/* Run the handle's stream to completion and report any CUDA error.  Also
+ * reads and clears the device's status word: MACLAB_ERR_TIMEOUT if, since the
+ * last check, a step kernel's bounded wait for a tile copy ran out (the
+ * kernel then finished with undefined values in the state it wrote). */
 maclab_status maclab_sync(maclab_handle h);
 
 /* Name of a status code (static string). */

@@ -311,6 +311,11 @@ maclab_status maclab_create(const maclab_config* cfg, maclab_handle* out) {
     free_ctx(h);
     return fail(MACLAB_ERR_OOM, "state allocation failed");
   }
+  // the step kernels' status word exists before any launch or graph capture
+  if (!step_status()) {
+    free_ctx(h);
+    return fail(MACLAB_ERR_OOM, "status word allocation failed");
+  }
   // the diagnostics kernel's ticket counter (after the block records) starts at 0
   if (cudaMemsetAsync(h->d_partial + kDiagOut * h->diag_nblocks, 0, sizeof(double), h->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -743,7 +748,9 @@ maclab_status maclab_adjoint_nu_term(maclab_handle h, const void* state_n, const
   NvtxRange nvtx_range("maclab_adjoint_nu_term");
   if (!h || !state_n || !lam_np1 || !acc) return fail(MACLAB_ERR_INVALID, "NULL argument");
   DeviceGuard dg(h->device);
-  if (state_np1 && h->kernel != MACLAB_KERNEL_REFERENCE && rows2_nu_supported(h->g, h->precision)) {
+  auto aligned = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+  if (state_np1 && h->kernel != MACLAB_KERNEL_REFERENCE && rows2_nu_supported(h->g, h->precision) &&
+      aligned(state_n) && aligned(state_np1) && aligned(lam_np1)) {
     CUDA_TRY(launch_rows2_nu(h->g, state_n, state_np1, static_cast<const float*>(lam_np1), h->force_lat, acc,
                              h->stream),
              "adjoint nu term (two-rows kernel)");
@@ -909,6 +916,23 @@ maclab_status maclab_set_planes(maclab_handle h, int64_t p0, int64_t count, cons
 }  // extern "C"
 
 namespace maclab {
+unsigned* step_status() {
+  static std::mutex m;
+  static unsigned* words[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(m);
+  if (!words[dev]) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(unsigned)) != cudaSuccess || cudaMemset(p, 0, sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    words[dev] = static_cast<unsigned*>(p);
+  }
+  return words[dev];
+}
+
 BoundsLog* bounds_log() {
 #ifdef MACLAB_BOUNDS_CHECK
   static std::mutex m;
@@ -1015,6 +1039,14 @@ maclab_status maclab_sync(maclab_handle h) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   DeviceGuard dg(h->device);
   CUDA_TRY(cudaStreamSynchronize(h->stream), "sync");
+  if (unsigned* st = step_status()) {
+    unsigned v = 0;
+    CUDA_TRY(cudaMemcpy(&v, st, sizeof(v), cudaMemcpyDeviceToHost), "sync status read");
+    if (v) {
+      CUDA_TRY(cudaMemset(st, 0, sizeof(v)), "sync status clear");
+      return fail(MACLAB_ERR_TIMEOUT, "a step kernel's bounded wait for a tile copy ran out");
+    }
+  }
   return MACLAB_OK;
 }
 

@@ -2,6 +2,7 @@
 // CUDA translation units of libmaclab.  Internal: not part of the C ABI.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -42,6 +43,52 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// ------------------------------------------------------------------ bulk tensor copies
+// One thread issues a TMA copy of a tile of a tensor map into shared memory;
+// its completion is counted in bytes on an mbarrier that the consumers wait
+// on.  Waits are bounded: a wait that runs out returns false (the caller
+// records it in the device status word, step_status(), and carries on, so no
+// thread leaves the block's barriers early).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// mbarrier initialisation visible to the copy engine before the first copy
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// shared memory the block has read made safe to overwrite by the copy engine
+__device__ __forceinline__ void proxy_async_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before a wait gives up
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// tile at coordinates (x, y, z, w) of a 4-D tensor map into shared memory at dst
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* map, int x, int y, int z, int w,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+      : "memory");
+}
+
 // ------------------------------------------------------------------ bounds checks
 // Debug builds (compiled with -DMACLAB_BOUNDS_CHECK; _build.build(bounds_check=True)
 // makes libmaclab_bounds.so): the kernels that take a BoundsLog check each
@@ -65,6 +112,10 @@ __device__ __forceinline__ bool bounds_ok(BoundsLog*, long long, long long) { re
 #endif
 // Device log of the current device (debug builds; nullptr otherwise).  Defined in api.cu.
 BoundsLog* bounds_log();
+// Defined in api.cu: the device status word of the current device (bit 0: a
+// bounded wait on a copy ran out), allocated and zeroed on first use;
+// maclab_sync reads and clears it.
+unsigned* step_status();
 
 // ------------------------------------------------------------------ storage
 

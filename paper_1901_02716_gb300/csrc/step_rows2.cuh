@@ -217,8 +217,18 @@ struct Rows2Layout {
   static constexpr int SIGN_UNITS = 5 * DIR_UNITS;
   static constexpr int BUF_UNITS = 2 * SIGN_UNITS;
   static constexpr size_t y_bytes = (size_t)2 * BUF_UNITS * 16;  // two buffers of 16-byte units
-  static constexpr size_t stage_bytes = (size_t)kStages * 4 * RS * BXC * Quad<S>::BYTES;
-  static constexpr size_t smem = y_bytes + stage_bytes;
+  // a stage slot: the TY own rows [4 fields][TY][row], then the halo rows
+  // below and above, [4 fields][row] each, as the tile copies lay them out
+  // (a row is nx stored values); offsets are multiples of 128 bytes
+  static constexpr size_t QB = (size_t)BXC * Quad<S>::BYTES;  // the widest row
+  static constexpr size_t slot_bytes = 4 * RS * QB;
+  static constexpr size_t halo_lo = 4 * TY * QB;
+  static constexpr size_t halo_hi = halo_lo + 4 * QB;
+  static constexpr size_t stage_bytes = (size_t)kStages * slot_bytes;
+  static constexpr size_t mbar_off = stage_bytes;        // one mbarrier per slot
+  static constexpr size_t y_off = stage_bytes + 16;
+  // + 128: the base is rounded up to a 128-byte boundary at run time
+  static constexpr size_t smem = 128 + y_off + y_bytes;
   static constexpr int THREADS = BXC * TYT;
   // at least eight warps per SM where shared memory allows
   static constexpr int SMEM_BLOCKS = (int)((220 * 1024) / smem) < 1 ? 1 : (int)((220 * 1024) / smem);
@@ -242,9 +252,13 @@ struct Rows2Sum {
 
 // NU: viscosity-term mode (see the top of this file); `out` is then the state
 // after the step, read only.
+// Tile copies: tm_own maps the state as [4 fields][nz][ny][nx] with a box of the
+// tile's TY own rows of every field; tm_halo the same tensor with a box of one
+// row of every field.
 template <typename S, int BXC, int TYT, bool NU = false>
 __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCKS)
-    step_rows2(TiledArgs ta, const S* __restrict__ in, S* __restrict__ out) {
+    step_rows2(TiledArgs ta, const S* __restrict__ in, S* __restrict__ out,
+               const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_halo) {
   using Lay = Rows2Layout<S, BXC, TYT>;
   using C = float;
   using O = Pair<C>;
@@ -254,14 +268,25 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   constexpr int TY = Lay::TY;
   constexpr int RS = Lay::RS;
   constexpr int YC = Lay::YC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  // stage slots at a 128-byte boundary (tile copies land on it), then the
+  // mbarriers, then the y exchange
+  unsigned char* const smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+  const int tx = threadIdx.x, tr = threadIdx.y;
+  const bool leader = tx == 0 && tr == 0;  // issues the tile copies
+  const uint32_t mbar0 = smem_u32(smem_raw + Lay::mbar_off);
+  if (leader) {
+    mbar_init(mbar0, 1);
+    mbar_init(mbar0 + 8, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
   pdl_wait();  // the previous step's writes are visible from here on
   pdl_launch_next();
 
-  const int tx = threadIdx.x, tr = threadIdx.y;
   const int bxr = ta.nx >> 2;  // threads per row actually used
   const bool active = tx < bxr;
-  float4* const Y = reinterpret_cast<float4*>(smem_raw);
+  float4* const Y = reinterpret_cast<float4*>(smem_raw + Lay::y_off);
 
   // columns: own, the right neighbour's (the unit a +x diagonal value goes to)
   // and the left one's (-x); idle lanes write into the spare column BXC
@@ -275,31 +300,27 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   const int src_r = tx == bxr - 1 ? 0 : tx + 1;
 
   // rows: own rows 2 tr, 2 tr + 1 of the tile; the first thread-row also
-  // stages the row below the tile, the last one the row above
+  // forms the equilibria of the row below the tile, the last one those of the
+  // row above (staged with the tile)
   const int row0 = blockIdx.y * TY + 2 * tr;
   int halo = tr == 0 ? 1 : (tr == TYT - 1 ? -1 : 0);
-  int hrow = halo == 1 ? row0 - 1 : row0 + 2;
-  if (halo != 0 && (hrow < 0 || hrow >= ta.ny)) {
-    if (ta.py) hrow = (hrow + ta.ny) % ta.ny;
-    else halo = 0;  // beyond a closed y boundary: the row next to it is a wall row
+  {
+    const int hrow = halo == 1 ? row0 - 1 : row0 + 2;
+    if (halo != 0 && (hrow < 0 || hrow >= ta.ny) && !ta.py)
+      halo = 0;  // beyond a closed y boundary: the row next to it is a wall row
   }
   bool row_wall[2];
   row_wall[0] = !ta.py && row0 == 0;
   row_wall[1] = !ta.py && row0 + 1 == ta.ny - 1;
   const int64_t row_off = (int64_t)row0 * ta.nx + 4 * tx;
-  const int64_t halo_delta = (int64_t)(hrow - row0) * ta.nx;
   const bool x_lo_wall = ta.wall_mode == kWallBox && !ta.px && tx == 0;
   const bool x_hi_wall = ta.wall_mode == kWallBox && !ta.px && tx == bxr - 1;
   const bool box_x = ta.wall_mode == kWallBox && !ta.px;
   const bool per_node_store = ta.wall_mode == kWallMask || (x_lo_wall && x_hi_wall);
 
-  const S* ip[4];
   S* op[4];
 #pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    ip[f] = in + (int64_t)f * ta.n + row_off;
-    op[f] = out + (int64_t)f * ta.n + row_off;
-  }
+  for (int f = 0; f < 4; ++f) op[f] = out + (int64_t)f * ta.n + row_off;
   const uint8_t* mrow = ta.wall_mode == kWallMask ? ta.mask + row_off : nullptr;
   P force[3];
 #pragma unroll
@@ -317,63 +338,69 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   auto plane_mem = [&](int p) { return p < 0 ? p + ta.nplanes : (p >= ta.nplanes ? p - ta.nplanes : p); };
   const bool zwall = !ta.pz;
 
-  // stage [kStages][4 fields][RS rows][BXC] quads; own row j at staged row
-  // 2 tr + 1 + j, the halo at 0 (below) or TY + 1 (above)
+  // stage slots (Lay): own row j of this thread at row 2 tr + j of the own
+  // block, the halo row below or above in its block; rows are nx values
+  // (rowB bytes) as the tile copies write them
   constexpr int QW = Quad<S>::BYTES;
-  constexpr uint32_t kFieldStride = RS * BXC * QW;
-  constexpr uint32_t kSlotStride = 4 * kFieldStride;
-  unsigned char* const stage0 = smem_raw + Lay::y_bytes + (size_t)tx * QW;
-  const uint32_t own_off = (uint32_t)(2 * tr + 1) * BXC * QW;
-  const uint32_t halo_off = (uint32_t)(halo == 1 ? 0 : TY + 1) * BXC * QW;
-  const uint32_t stage_sh = (uint32_t)__cvta_generic_to_shared(stage0);
+  static_assert(kStages == 2, "two stage slots, two mbarriers");
+  const uint32_t rowB = (uint32_t)bxr * QW;
+  const uint32_t fieldB = (uint32_t)TY * rowB;  // own block: [4 fields][TY rows]
+  const uint32_t own_off = (uint32_t)(2 * tr) * rowB + (uint32_t)tx * QW;
+  const uint32_t halo_off = (uint32_t)(halo == 1 ? Lay::halo_lo : Lay::halo_hi) + (uint32_t)tx * QW;
+  const uint32_t stage_sh = smem_u32(smem_raw);
   const int np = z1 - z0 + 2;  // planes z0 - 1 .. z1
+  // halo rows of the tile (wrapped on a periodic y axis; none beyond a closed one)
+  const int tile_row0 = blockIdx.y * TY;
+  int lo_row = tile_row0 - 1, hi_row = tile_row0 + TY;
+  bool lo_ok = true, hi_ok = true;
+  if (lo_row < 0) {
+    if (ta.py) lo_row += ta.ny;
+    else lo_ok = false;
+  }
+  if (hi_row >= ta.ny) {
+    if (ta.py) hi_row -= ta.ny;
+    else hi_ok = false;
+  }
+  const uint32_t tile_bytes = 4 * fieldB + (lo_ok ? 4 * rowB : 0u) + (hi_ok ? 4 * rowB : 0u);
   // debug builds: a quad copy or load of 4 values at element offset e (from
-  // `in` or `out`) and a stage byte offset b (from stage0) must lie in bounds
+  // `in` or `out`) and a stage byte offset b must lie in bounds
   const int64_t n4 = 4 * ta.n;
-  const int64_t stage_lim = (int64_t)Lay::stage_bytes - (int64_t)tx * QW;
-  auto quad_ok = [&](int64_t e, int64_t b) {
-    return bounds_ok(ta.bounds, e, n4 - 3) && bounds_ok(ta.bounds, b, stage_lim - QW + 1);
-  };
-  const int64_t in_off = row_off;  // ip[f] = in + f * n + in_off
+  const int64_t in_off = row_off;
+  // plane z0 - 1 + i into slot i & 1: one thread copies the tile's own rows
+  // and its halo rows of the four fields; a plane that does not exist (beyond
+  // a closed march axis) completes the slot's phase with no bytes
   auto fetch = [&](int i) {
+    if (!leader || i >= np) return;
     const int p = z0 - 1 + i;
-    if (i < np && active && plane_exists(p)) {
-      const int64_t off = (int64_t)plane_mem(p) * ps;
-      const uint32_t so = (uint32_t)(i & (kStages - 1)) * kSlotStride + own_off;
-      const uint32_t sh = stage_sh + so;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        if (quad_ok(f * ta.n + in_off + off, so + f * kFieldStride))
-          Quad<S>::copy(sh + f * kFieldStride, ip[f] + off);
-        if (quad_ok(f * ta.n + in_off + off + nx64, so + f * kFieldStride + BXC * QW))
-          Quad<S>::copy(sh + f * kFieldStride + BXC * QW, ip[f] + off + nx64);
-      }
-      if (halo != 0) {
-        const uint32_t ho = (uint32_t)(i & (kStages - 1)) * kSlotStride + halo_off;
-        const uint32_t hs = stage_sh + ho;
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-          if (quad_ok(f * ta.n + in_off + off + halo_delta, ho + f * kFieldStride))
-            Quad<S>::copy(hs + f * kFieldStride, ip[f] + off + halo_delta);
-      }
+    const uint32_t s = (uint32_t)(i & 1);
+    const uint32_t bar = mbar0 + 8 * s;
+    const uint32_t dst = stage_sh + s * (uint32_t)Lay::slot_bytes;
+    if (plane_exists(p)) {
+      const int pm = plane_mem(p);
+      proxy_async_fence();  // the block's reads of this slot (before its last barrier) come first
+      mbar_arrive_expect_tx(bar, tile_bytes);
+      tma_load_4d(dst, &tm_own, 0, tile_row0, pm, 0, bar);
+      if (lo_ok) tma_load_4d(dst + (uint32_t)Lay::halo_lo, &tm_halo, 0, lo_row, pm, 0, bar);
+      if (hi_ok) tma_load_4d(dst + (uint32_t)Lay::halo_hi, &tm_halo, 0, hi_row, pm, 0, bar);
+    } else {
+      mbar_arrive(bar);
     }
-    cp_async_commit();
   };
   P st[2][4][2];
-  const unsigned char* slot_base = stage0;
+  const unsigned char* slot_base = smem_raw;
   auto take = [&](int i) {
-    cp_async_wait<kStages - 1>();
     const int p = z0 - 1 + i;
+    const uint32_t s = (uint32_t)(i & 1);
+    if (!mbar_wait(mbar0 + 8 * s, (uint32_t)(i >> 1) & 1u) && ta.status) atomicOr(ta.status, 1u);
     const bool ok = active && plane_exists(p);
-    slot_base = stage0 + (size_t)(i & (kStages - 1)) * kSlotStride;
+    slot_base = smem_raw + (size_t)s * Lay::slot_bytes;
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        const int64_t b = (int64_t)(slot_base - stage0) + own_off + j * BXC * QW + f * kFieldStride;
-        if (ok && bounds_ok(ta.bounds, b, stage_lim - QW + 1)) {
-          Quad<S>::lds(reinterpret_cast<const S*>(slot_base + own_off + j * BXC * QW + f * kFieldStride),
-                       st[j][f][0], st[j][f][1]);
+        const int64_t b = (int64_t)s * Lay::slot_bytes + own_off + j * rowB + f * fieldB;
+        if (ok && bounds_ok(ta.bounds, b, (int64_t)Lay::stage_bytes - QW + 1)) {
+          Quad<S>::lds(reinterpret_cast<const S*>(smem_raw + b), st[j][f][0], st[j][f][1]);
         } else {
           st[j][f][0] = st[j][f][1] = O::splat(C(0));
         }
@@ -502,11 +529,11 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
     // ---- halo row: its inward equilibria into the slot its neighbour reads
     if (halo != 0) {  // idle lanes publish into their own or the spare column
       P hs[4][2];
-      const unsigned char* hsrc = slot_base + halo_off;
+      const int64_t hb = (int64_t)(slot_base - smem_raw) + halo_off;
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        if (bounds_ok(ta.bounds, (int64_t)(hsrc - stage0) + f * kFieldStride, stage_lim - QW + 1))
-          Quad<S>::lds(reinterpret_cast<const S*>(hsrc + f * kFieldStride), hs[f][0], hs[f][1]);
+        if (bounds_ok(ta.bounds, hb + f * rowB, (int64_t)Lay::stage_bytes - QW + 1))
+          Quad<S>::lds(reinterpret_cast<const S*>(smem_raw + hb + f * rowB), hs[f][0], hs[f][1]);
         else
           hs[f][0] = hs[f][1] = O::splat(C(0));
       }
@@ -664,7 +691,10 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   // first (halo) plane z0 - 1: only the equilibria moving up the march axis
   fetch(kStages - 1);
   take(0);
+  // (the barrier inside update, or this one, keeps slot 0's next copy behind
+  // every thread's wait for its current one)
   if (plane_exists(z0 - 1)) update(std::integral_constant<int, kFirst>{}, R0, R2, R1);
+  else __syncthreads();
 
   // full planes: R0, R1, R2 hold the sums of planes p - 1, p, p + 1; after
   // plane p, p - 1 is complete and the sums move down by one plane.  The
@@ -699,7 +729,6 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
     if (plane_exists(z1)) update(std::integral_constant<int, kLast>{}, R0, R1, R1);
     store(z1 - 1, R0);
   }
-  cp_async_wait<0>();
   if constexpr (NU) {
     // block sum: warp shuffles, one value per warp, one FP64 atomic per block
     double v = (double)nus.hi + (double)nus.lo;
@@ -721,16 +750,18 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
 // step_rows2.cu, 16-bit storage in step_rows2_s16.cu).
 template <typename S>
 cudaError_t rows2_dispatch(int bxc, int tyt, const TiledArgs& ta, const void* in, void* out,
-                           cudaStream_t st, dim3 grid, int* resident);
+                           const CUtensorMap& tm_own, const CUtensorMap& tm_halo, cudaStream_t st, dim3 grid,
+                           int* resident);
 // The viscosity-term mode, FP32 storage (instances in step_rows2_nu.cu).
 cudaError_t rows2_nu_dispatch(int bxc, int tyt, const TiledArgs& ta, const void* in, const void* out,
-                              cudaStream_t st, dim3 grid, int* resident);
+                              const CUtensorMap& tm_own, const CUtensorMap& tm_halo, cudaStream_t st, dim3 grid,
+                              int* resident);
 
 // Launch one instance.  With resident_out set,
 // only report the blocks of this shape one SM holds.
 template <typename S, int BXC, int TYT, bool NU = false>
-cudaError_t launch_rows2_shape(const TiledArgs& ta, const void* in, void* out, cudaStream_t stream,
-                               dim3 grid, int* resident_out) {
+cudaError_t launch_rows2_shape(const TiledArgs& ta, const void* in, void* out, const CUtensorMap& tm_own,
+                               const CUtensorMap& tm_halo, cudaStream_t stream, dim3 grid, int* resident_out) {
   auto kern = step_rows2<S, BXC, TYT, NU>;
   constexpr size_t smem = Rows2Layout<S, BXC, TYT>::smem;
   static int resident_dev[64] = {};
@@ -753,7 +784,7 @@ cudaError_t launch_rows2_shape(const TiledArgs& ta, const void* in, void* out, c
     return cudaSuccess;
   }
   return launch_kernel(kern, grid, dim3(BXC, TYT), smem, stream, ta.overlap, ta, static_cast<const S*>(in),
-                       static_cast<S*>(out));
+                       static_cast<S*>(out), tm_own, tm_halo);
 }
 
 }  // namespace maclab

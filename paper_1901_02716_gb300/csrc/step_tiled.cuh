@@ -78,6 +78,7 @@ struct TiledArgs {
   BoundsLog* bounds;       // debug builds: where bad indices are recorded (bounds_ok)
   const float* lam;        // viscosity-term launches: the adjoint of the state after the step
   double* nu_acc;          // viscosity-term launches: the sum's accumulator (one double)
+  unsigned* status;        // bit 0 set when a bounded wait on a copy ran out (step_status())
 };
 
 // ------------------------------------------------------------------ lane pairs

@@ -61,6 +61,7 @@ def _run(case, precision, steps, ty=0, kernel=M.KERNEL_ROWS2):
         s.set_tile(ty, 0)
     assert s.kernel_info()["kernel"] == kernel
     s.step(steps)
+    s.sync()  # raises if a bounded wait for a tile copy ran out (MACLAB_ERR_TIMEOUT)
     out = s.get_state()
     s.close()
     return out
