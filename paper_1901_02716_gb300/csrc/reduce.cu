@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(256) diag_partial(Geometry g, const S* __restr
                                                     double* __restrict__ out) {
   using C = typename Store<S>::C;
   pdl_wait();  // the step before this kernel has completed and its writes are visible
+  pdl_launch_next();  // the next step may be scheduled; it waits for this kernel before writing
   DiagPart<C> t;
   const int64_t N = g.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 3) diag_rows(Geometr
   using C = typename Store<S>::C;
   using P = typename Quad<S>::P;
   pdl_wait();  // the step before this kernel has completed and its writes are visible
+  pdl_launch_next();  // the next step may be scheduled; it waits for this kernel before writing
   DiagPart<C> t;
   const int64_t N = g.n;
   const int lane = threadIdx.x & 31;

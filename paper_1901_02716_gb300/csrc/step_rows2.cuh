@@ -599,27 +599,41 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
     }
   };
   Rows2Sum nus;  // viscosity-term mode: this thread's sum
+  // viscosity-term mode: the stored state after the step and lam of the plane
+  // q the next store sums, loaded early so their latency overlaps the update
+  P nsn[2][4][2], nlm[2][4][2];
+  auto nu_prefetch = [&](int q) {
+    if constexpr (NU) {
+      const bool zskip = zwall && (q == 0 || q == ta.nplanes - 1);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const bool skip = !active || row_wall[j] || zskip || q < 0 || q >= ta.nplanes;
+        const int64_t off = (int64_t)q * ps + j * nx64;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const int64_t e = f * ta.n + in_off + off;
+          if (!skip && bounds_ok(ta.bounds, e, n4 - 3)) {
+            Quad<S>::ld(out + e, nsn[j][f][0], nsn[j][f][1]);
+            Quad<float>::ld(ta.lam + e, nlm[j][f][0], nlm[j][f][1]);
+          } else {
+            nsn[j][f][0] = nsn[j][f][1] = nlm[j][f][0] = nlm[j][f][1] = O::splat(C(0));
+          }
+        }
+      }
+    }
+  };
   auto store = [&](int q, P(&acc)[2][2][4]) {
     const bool zskip = zwall && (q == 0 || q == ta.nplanes - 1);
     if constexpr (NU) {
-      // the viscosity term of the fluid nodes of the two rows: R and u' from the
-      // stored state after the step, lam from ta.lam
-      const float* const lam = ta.lam;
+      // the viscosity term of the fluid nodes of the two rows: R and u' of the
+      // stored state after the step and lam, loaded by nu_prefetch(q) before
+      // the plane update that precedes this store
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         if (!active || row_wall[j] || zskip) continue;
         const int64_t off = (int64_t)q * ps + j * nx64;
-        P sn[4][2], lm[4][2];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int64_t e = f * ta.n + in_off + off;
-          if (bounds_ok(ta.bounds, e, n4 - 3)) {
-            Quad<S>::ld(out + e, sn[f][0], sn[f][1]);
-            Quad<float>::ld(lam + e, lm[f][0], lm[f][1]);
-          } else {
-            sn[f][0] = sn[f][1] = lm[f][0] = lm[f][1] = O::splat(C(0));
-          }
-        }
+        const P(&sn)[4][2] = nsn[j];
+        const P(&lm)[4][2] = nlm[j];
         // fluid lanes: (pair a.x, a.y, b.x, b.y) = storage positions 4 tx .. 4 tx + 3
         bool fl[4] = {!x_lo_wall, true, true, !x_hi_wall};
         if (ta.wall_mode == kWallMask && bounds_ok(ta.bounds, in_off + off, ta.n - 3)) {
@@ -706,6 +720,7 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
     const int i = p - z0 + 1;
     fetch(i + kStages - 1);
     load_walls(p - 1);
+    nu_prefetch(p - 1);
     take(i);
     update(std::integral_constant<int, kMid>{}, R0, R1, R2);
     if (p - 1 >= z0) store(p - 1, R0);
@@ -725,6 +740,7 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
     const int i = np - 1;
     fetch(i + kStages - 1);
     load_walls(z1 - 1);
+    nu_prefetch(z1 - 1);
     take(i);
     if (plane_exists(z1)) update(std::integral_constant<int, kLast>{}, R0, R1, R1);
     store(z1 - 1, R0);
