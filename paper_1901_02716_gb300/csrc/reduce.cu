@@ -1,9 +1,6 @@
 // reduce.cu -- FP64 diagnostics of the stored state.
 //
-// Sums over fluid nodes (walls excluded), to FP64 accuracy whatever the
-// storage type (each node's products are formed in the storage's arithmetic
-// type, FP32 for FP32 and 16-bit storage, and added in float-float within a
-// thread, where FP64 arithmetic is slow; FP64 across threads):
+// Sums over fluid nodes (walls excluded), in nine slots:
 //   slot 0  sum drho                      (mass = rho0 (n_fluid + slot 0))
 //   slot 1  sum rho |u|^2                 (kinetic energy = rho0 e^2 slot 1 / 2)
 //   slot 2..4  sum rho u_i                (momentum = rho0 e slot)
@@ -11,10 +8,13 @@
 //   slot 6  sum |u|^2                     (steady residual denominator)
 //   slot 7  max |u|                       (lattice Mach number of the fastest node)
 //   slot 8  number of non-finite values
+// Each node's products are formed in the storage's arithmetic type (FP32 for
+// FP32 and 16-bit storage) and added in float-float (FP64 for FP64 storage)
+// by threads, warps, blocks and the grid; only the nine results become FP64.
 // Mass and momentum are the quantities the equilibrium conserves (Eq. (15));
 // the residual ||u^n - u^(n-1)||_2 / ||u^n||_2 is the steady-state measure.
-// Two kernels: per-block partials into a scratch array, then one block folds
-// the partials.
+// One kernel: block records into a scratch array, folded by the last block to
+// finish.
 
 #include <mutex>
 

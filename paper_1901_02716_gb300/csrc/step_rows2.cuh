@@ -786,10 +786,10 @@ cudaError_t launch_rows2_shape(const TiledArgs& ta, const void* in, void* out, c
   if (e != cudaSuccess) return e;
   int& resident = resident_dev[dev & 63];
   if (!resident) {
-    if (smem > 48 * 1024) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
+    // set whatever the size: static shared memory counts against the 48 KB
+    // default as well
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BXC * TYT, smem);
     if (e != cudaSuccess) return e;
