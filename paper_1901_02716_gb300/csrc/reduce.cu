@@ -286,22 +286,24 @@ __global__ void __launch_bounds__(256) diag_partial(Geometry g, const S* __restr
 // mode only the storage positions 0 and nx - 1 of a row (x = 0, nx - 1) are
 // x-walls.  The stored density deviations are exact inputs and enter the
 // float-float sum node by node, as in diag_partial.  The per-node products
-// (rho |u|^2, rho u_i, |u - u_prev|^2, |u|^2) are each rounded to the
-// arithmetic type already; a quad's four are added in that type first and the
-// quad's sum enters the float-float sum (one two-sum per quad and slot instead
-// of one per node: three more roundings of the same size per quad, not an
-// error that grows with the node count; the sums differ from diag_partial's by
-// at most 5 units of 2^-24 of the sum of the terms' magnitudes).  A quad whose
-// summed density and |u|^2 are not finite holds a non-finite value (or
-// overflows) and is checked node by node.
+// (rho |u|^2, rho u_i, |u - u_prev|^2, |u|^2) are formed on the quad's two node
+// pairs with paired arithmetic, each rounded to the arithmetic type; a quad's
+// four are added in that type and the quad's sum enters the float-float sum
+// (one two-sum per quad and slot instead of one per node: three more
+// roundings of the same size per quad, not an error that grows with the node
+// count; the sums differ from diag_partial's by at most 5 units of 2^-24 of
+// the sum of the terms' magnitudes).  Wall nodes of a quad enter as zeros.  A
+// quad whose summed density and |u|^2 are not finite holds a non-finite value
+// (or overflows) and is checked node by node.
 template <typename S>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 3) diag_rows(Geometry g, const S* __restrict__ cur,
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 2) diag_rows(Geometry g, const S* __restrict__ cur,
                                                     const S* __restrict__ prev,
                                                     double* __restrict__ partial,
                                                     unsigned* __restrict__ ticket,
                                                     double* __restrict__ out) {
   using C = typename Store<S>::C;
   using P = typename Quad<S>::P;
+  using O = Pair<C>;
   pdl_wait();  // the step before this kernel has completed and its writes are visible
   pdl_launch_next();  // the next step may be scheduled; it waits for this kernel before writing
   DiagPart<C> t;
@@ -346,42 +348,58 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 3) diag_rows(Geometr
         Quad<S>::ld(cur + (1 + i) * N + m, u[i][0], u[i][1]);
         if (prev) Quad<S>::ld(prev + (1 + i) * N + m, v[i][0], v[i][1]);
       }
-      // the quad's sums: drho, rho |u|^2, rho u_i, |u - u_prev|^2, |u|^2
-      C qs[kDiagSlots - 2];
+      // wall nodes of the quad enter as zeros (their values are not summed)
+      if (wall[0] | wall[1] | wall[2] | wall[3]) {
 #pragma unroll
-      for (int k = 0; k < kDiagSlots - 2; ++k) qs[k] = C(0);
+        for (int h = 0; h < 2; ++h) {
+          const bool w0 = wall[2 * h], w1 = wall[2 * h + 1];
+          r[h].x = w0 ? C(0) : r[h].x;
+          r[h].y = w1 ? C(0) : r[h].y;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (wall[k]) continue;
-        const int h = k >> 1;
-        const auto pick = [&](const P& p) { return (k & 1) ? p.y : p.x; };
-        const C dr = pick(r[h]);
-        const C rho = C(1) + dr;
-        C uu = C(0), du = C(0);
-        t.sum[0].add(dr);
-        qs[0] += dr;
+          for (int i = 0; i < 3; ++i) {
+            if (i >= g.d) break;
+            u[i][h].x = w0 ? C(0) : u[i][h].x;
+            u[i][h].y = w1 ? C(0) : u[i][h].y;
+            v[i][h].x = w0 ? C(0) : v[i][h].x;
+            v[i][h].y = w1 ? C(0) : v[i][h].y;
+          }
+        }
+      }
+      // the quad's sums on its two node pairs: drho, rho |u|^2, rho u_i,
+      // |u - u_prev|^2, |u|^2; the density deviations also node by node
+      P qs[kDiagSlots - 2];
+#pragma unroll
+      for (int k = 0; k < kDiagSlots - 2; ++k) qs[k] = O::splat(C(0));
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const P dr = r[h];
+        t.sum[0].add(dr.x);
+        t.sum[0].add(dr.y);
+        const P rho = O::add(O::splat(C(1)), dr);
+        P uu = O::splat(C(0)), du = O::splat(C(0));
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           if (i >= g.d) break;
-          const C ui = pick(u[i][h]);
-          uu = fma(ui, ui, uu);
-          qs[2 + i] = fma(rho, ui, qs[2 + i]);
+          const P ui = u[i][h];
+          uu = O::fma(ui, ui, uu);
+          qs[2 + i] = O::fma(rho, ui, qs[2 + i]);
           if (prev) {
-            const C d = ui - pick(v[i][h]);
-            du = fma(d, d, du);
+            const P dd = O::sub(ui, v[i][h]);
+            du = O::fma(dd, dd, du);
           }
         }
-        qs[1] = fma(rho, uu, qs[1]);
-        qs[5] += du;
-        qs[6] += uu;
-        t.umax2 = fmax(t.umax2, uu);
+        qs[0] = O::add(qs[0], dr);
+        qs[1] = O::fma(rho, uu, qs[1]);
+        qs[5] = O::add(qs[5], du);
+        qs[6] = O::add(qs[6], uu);
+        t.umax2 = fmax(t.umax2, fmax(uu.x, uu.y));
       }
 #pragma unroll
-      for (int k = 0; k < kDiagSlots - 2; ++k) {
-        if (k == 0 || (k >= 2 && k < 5 && k - 2 >= g.d)) continue;
-        t.sum[k].add(qs[k]);
+      for (int k = 1; k < kDiagSlots - 2; ++k) {
+        if (k >= 2 && k < 5 && k - 2 >= g.d) continue;
+        t.sum[k].add(qs[k].x + qs[k].y);
       }
-      if (!isfinite(qs[0] + qs[6])) {
+      if (!isfinite(qs[0].x + qs[0].y + qs[6].x + qs[6].y)) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (wall[k]) continue;
@@ -401,8 +419,9 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 3) diag_rows(Geometr
   grid_fold(t, partial, ticket, out);
 }
 
-// Blocks of one launch: three 256-thread blocks per SM (the row kernel keeps
-// to 85 registers for that with FP32 arithmetic), fewer on small grids.
+// Blocks of one launch: two 256-thread blocks per SM (the row kernel's paired
+// sums need more than the 85 registers three blocks would leave), fewer on
+// small grids.
 int diag_blocks(int64_t n) {
   static int sms = 0;
   if (!sms) {
@@ -412,7 +431,7 @@ int diag_blocks(int64_t n) {
       sms = 148;
   }
   int64_t b = (n + 255) / 256;
-  if (b > 3 * sms) b = 3 * sms;
+  if (b > 2 * sms) b = 2 * sms;
   return (int)(b < 1 ? 1 : b);
 }
 
