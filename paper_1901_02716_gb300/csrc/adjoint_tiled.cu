@@ -82,8 +82,9 @@ cudaError_t tiled_dispatch(const AdjShape& s, const AdjArgs& A, const void* sn, 
 template <int LAT, typename S>
 cudaError_t tiled_adjoint_t(const Geometry& g, const AdjShape& s, const void* sn, const void* sn1,
                             const void* lam1, void* lam0, const double* force, double* gf,
-                            cudaStream_t st) {
+                            int overlap, cudaStream_t st) {
   AdjArgs A{};
+  A.overlap = overlap;
   A.nx = g.nx;
   A.ny = g.d == 3 ? g.ny : 1;
   A.nplanes = g.d == 3 ? g.nz : g.ny;
@@ -121,17 +122,17 @@ bool tiled_adjoint_supported(const Geometry& g, int precision) {
 
 cudaError_t launch_tiled_adjoint(const Geometry& g, int precision, const void* state_n,
                                  const void* state_np1, const void* lam_np1, void* lam_n,
-                                 const double force_lat[3], double* grad_force, cudaStream_t st) {
+                                 const double force_lat[3], double* grad_force, int overlap, cudaStream_t st) {
   AdjShape s;
   if (!adj_shape(g, precision, &s)) return cudaErrorInvalidValue;
   if (g.lattice == kD2Q9) {
     if (precision == MACLAB_F64)
-      return tiled_adjoint_t<kD2Q9, double>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, st);
-    return tiled_adjoint_t<kD2Q9, float>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, st);
+      return tiled_adjoint_t<kD2Q9, double>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, overlap, st);
+    return tiled_adjoint_t<kD2Q9, float>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, overlap, st);
   }
   if (precision == MACLAB_F64)
-    return tiled_adjoint_t<kD3Q19, double>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, st);
-  return tiled_adjoint_t<kD3Q19, float>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, st);
+    return tiled_adjoint_t<kD3Q19, double>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, overlap, st);
+  return tiled_adjoint_t<kD3Q19, float>(g, s, state_n, state_np1, lam_np1, lam_n, force_lat, grad_force, overlap, st);
 }
 
 }  // namespace maclab

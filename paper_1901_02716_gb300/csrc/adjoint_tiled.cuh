@@ -36,6 +36,7 @@ struct AdjArgs {
   int wall_mode;
   const uint8_t* mask;
   double force[3];
+  int overlap;           // host side: launch with programmatic dependent launch
 };
 
 // a - b as fma(b, -1, a): the same correctly rounded difference, written
@@ -107,6 +108,8 @@ __global__ void __launch_bounds__(BXC * RY, (AdjTile<LAT, S, BXC, RY>::MIN_BLOCK
   using F = Frame<LAT>;
   constexpr int D = T::D, K = T::K, G = T::G, NU = T::NU;
   extern __shared__ __align__(16) uint4 units[];
+  pdl_wait();  // the previous kernel's writes are visible from here on
+  pdl_launch_next();
   const int tx = threadIdx.x, r = threadIdx.y;
   const int bxr = A.nx >> 2;
   const bool active = tx < bxr;
@@ -396,10 +399,9 @@ cudaError_t launch_adj_tiled(const AdjArgs& A, const void* in_state, const void*
     *resident_out = resident;
     return cudaSuccess;
   }
-  kern<<<dim3(A.nzc, ytiles), dim3(BXC, RY), smem, st>>>(
-      A, static_cast<const S*>(in_state), static_cast<const S*>(out_state), static_cast<const C*>(lam1),
-      static_cast<C*>(lam0), grad_force);
-  return cudaGetLastError();
+  return launch_kernel(kern, dim3(A.nzc, ytiles), dim3(BXC, RY), smem, st, A.overlap, A,
+                       static_cast<const S*>(in_state), static_cast<const S*>(out_state),
+                       static_cast<const C*>(lam1), static_cast<C*>(lam0), grad_force);
 }
 
 }  // namespace maclab

@@ -733,7 +733,7 @@ maclab_status maclab_adjoint_step(maclab_handle h, const void* state_n, const vo
   if (s != MACLAB_OK) return s;
   if (tiled) {
     CUDA_TRY(launch_tiled_adjoint(h->g, h->precision, state_n, state_np1, lam_np1, lam_n,
-                                  h->force_lat, grad_force, h->stream),
+                                  h->force_lat, grad_force, h->overlap, h->stream),
              "adjoint step");
   } else {
     CUDA_TRY(launch_adjoint_step(h->g, h->precision, state_n, state_np1, lam_np1, lam_n,

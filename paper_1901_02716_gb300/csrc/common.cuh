@@ -283,7 +283,7 @@ cudaError_t launch_fp32_peak(int blocks, int threads, int iters, float2* sink, c
 bool tiled_adjoint_supported(const Geometry& g, int precision);
 cudaError_t launch_tiled_adjoint(const Geometry& g, int precision, const void* state_n,
                                  const void* state_np1, const void* lam_np1, void* lam_n,
-                                 const double force_lat[3], double* grad_force, cudaStream_t st);
+                                 const double force_lat[3], double* grad_force, int overlap, cudaStream_t st);
 // sum over fluid x of lam_np1(x) . D_n(x), the viscosity term of one reverse step, into *acc
 cudaError_t launch_adjoint_nu_term(const Geometry& g, int precision, const void* state_n, const void* lam_np1,
                                    const double force_lat[3], double* acc, cudaStream_t st);
