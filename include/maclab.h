@@ -207,7 +207,11 @@ maclab_status maclab_get_launch_overlap(maclab_handle h, int32_t *on);
  * block (3D only) and tz planes of the slowest axis per block.  Segment kernel:
  * ty time steps per launch (1 or 2; 2 needs FP32 or FP64 storage and nx >= 8,
  * and a run of n steps then ends with a one-step launch so that the previous
- * state is step n - 1) and tz rows per work item.  0 keeps the library's
+ * state is step n - 1) and tz rows per work item; ty = 3 runs the two-step
+ * launches of one maclab_step call as the sweeps of a single persistent
+ * cooperative launch, each block waiting between sweeps (bounded, see
+ * maclab_set_wait_limit) only for the blocks that own rows within two of its
+ * own; the results are bit-identical with ty = 2.  0 keeps the library's
  * default (for the segment kernel it depends on the grid's size).  MACLAB_ERR_UNSUPPORTED if no built instance has that shape for this
  * domain (the previous shape is kept). */
 maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz);
@@ -483,9 +487,19 @@ maclab_status maclab_debug_bounds(int64_t out[2]);
 
 /* Run the handle's stream to completion and report any CUDA error.  Also
  * reads and clears the device's status word: MACLAB_ERR_TIMEOUT if, since the
- * last check, a step kernel's bounded wait for a tile copy ran out (the
- * kernel then finished with undefined values in the state it wrote). */
+ * last check, a step kernel's bounded wait (for a tile copy, or for another
+ * block of a persistent launch) ran out (the kernel then finished with
+ * undefined values in the state it wrote). */
 maclab_status maclab_sync(maclab_handle h);
+
+/* Budget of the bounded waits between blocks of the persistent segment launch
+ * (maclab_set_tile ty = 3): polls of a neighbouring block's counter before the
+ * wait gives up.  polls < 0 restores the default (2^22); 0 makes every such
+ * wait give up at once, so that the next maclab_sync returns
+ * MACLAB_ERR_TIMEOUT and the state is undefined until the next set_state.  A
+ * verification aid: with every block resident the waits always end.  No paper
+ * counterpart.  Errors: MACLAB_ERR_INVALID (NULL handle, polls > 2^32 - 1). */
+maclab_status maclab_set_wait_limit(maclab_handle h, int64_t polls);
 
 /* Name of a status code (static string). */
 const char *maclab_status_string(maclab_status s);

@@ -90,6 +90,8 @@ void free_ctx(maclab_ctx* h) {
   cudaFree(h->d_adj_red);
   cudaFree(h->d_seg_inst);
   cudaFree(h->d_seg_items);
+  cudaFree(h->d_seg_deps);
+  cudaFree(h->d_seg_done);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->d_node_type);
@@ -613,6 +615,30 @@ static maclab_status segment_prepare(maclab_ctx* h) {
   const int want = (h->seg_n_items + warps - 1) / warps;
   h->seg_blocks = want < per_sm * device_sms() ? (want > 0 ? want : 1) : per_sm * device_sms();
   drop_graphs(h);
+  // the persistent form (two steps per sweep): as many blocks as fit at once,
+  // each with the list of blocks it waits for between sweeps
+  cudaFree(h->d_seg_deps);
+  cudaFree(h->d_seg_done);
+  h->d_seg_deps = nullptr;
+  h->d_seg_done = nullptr;
+  h->seg_persist_blocks = 0;
+  int capacity = 0;
+  if (depth == 2 && batch_persist_capacity(h->precision, &capacity) == cudaSuccess && capacity > 0) {
+    const int pb = want < capacity ? (want > 0 ? want : 1) : capacity;
+    std::vector<int> deps;
+    batch_persist_deps(items, h->g.ny, (h->g.periodic & 2u) != 0, pb, deps);
+    if (cudaMalloc(&h->d_seg_deps, deps.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->d_seg_done, (size_t)pb * sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MACLAB_ERR_OOM, "persistent segment lists allocation failed");
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->d_seg_deps, deps.data(), deps.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             h->stream),
+             "persistent segment lists upload");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "persistent segment lists sync");
+    h->seg_persist_blocks = pb;
+  }
+  cudaGetLastError();
   return MACLAB_OK;
 }
 
@@ -657,7 +683,20 @@ maclab_status maclab_step(maclab_handle h, int64_t n) {
   const int launches = h->graph_steps / k;
   const int64_t gsteps = (int64_t)launches * k;
   int64_t done = 0;
-  while (gsteps > 0 && bulk - done >= gsteps) {
+  // the persistent segment form (ty 3): the bulk's step pairs in one
+  // cooperative launch per call instead of graphs of launches
+  const bool persist = h->kernel == MACLAB_KERNEL_SEGMENT && h->ty == 3 && k == 2 && h->seg_persist_blocks > 0;
+  for (int64_t pairs = persist ? bulk / 2 : 0; pairs > 0;) {
+    const int sweeps = pairs > (1 << 30) ? (1 << 30) : (int)pairs;
+    CUDA_TRY(launch_batch_step2_persist(h->precision, h->d_seg_inst, h->d_seg_items, h->seg_n_items, h->cur,
+                                        h->seg_persist_blocks, sweeps, h->d_seg_deps, h->d_seg_done,
+                                        step_status(), h->wait_limit, h->stream),
+             "persistent step launch");
+    if (sweeps & 1) h->cur ^= 1;
+    done += 2 * (int64_t)sweeps;
+    pairs -= sweeps;
+  }
+  while (!persist && gsteps > 0 && bulk - done >= gsteps) {
     if (!h->graph_exec[h->cur]) {
       maclab_status s = build_graph(h, h->cur);
       if (s != MACLAB_OK) return s;
@@ -1044,9 +1083,16 @@ maclab_status maclab_sync(maclab_handle h) {
     CUDA_TRY(cudaMemcpy(&v, st, sizeof(v), cudaMemcpyDeviceToHost), "sync status read");
     if (v) {
       CUDA_TRY(cudaMemset(st, 0, sizeof(v)), "sync status clear");
-      return fail(MACLAB_ERR_TIMEOUT, "a step kernel's bounded wait for a tile copy ran out");
+      return fail(MACLAB_ERR_TIMEOUT, "a step kernel's bounded wait (for a tile copy or another block) ran out");
     }
   }
+  return MACLAB_OK;
+}
+
+maclab_status maclab_set_wait_limit(maclab_handle h, int64_t polls) {
+  if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
+  if (polls > (int64_t)0xffffffffu) return fail(MACLAB_ERR_INVALID, "wait limit above 2^32 - 1");
+  h->wait_limit = polls < 0 ? kWaitLimit : (unsigned)polls;
   return MACLAB_OK;
 }
 
@@ -1553,7 +1599,7 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
   for (int kernel : {MACLAB_KERNEL_TILED, MACLAB_KERNEL_FOLDED})
     for (int a = 0; a < n_ty; ++a)
       for (int tz : tzs) cands.push_back(Cand{kernel, h->g.d == 3 ? tys3[a] : 0, tz});
-  for (int ty : {1, 2})
+  for (int ty : {1, 2, 3})  // 3: two steps per sweep, runs in one persistent launch
     for (int tz : {2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_SEGMENT, ty, tz});
   if (h->g.d == 3)
     for (int ty : {4, 8})
@@ -1566,9 +1612,20 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
     if (segment_prepare(h) != MACLAB_OK) continue;
     // per time step; graphs of 64 launches where 8 take under 0.5 ms, so that
     // the launch of the graph itself does not decide between close shapes
-    float ms = graph_ms(8);
-    if (ms < 0.5f) ms = graph_ms(64) / 8.f;
-    ms /= 8 * launch_depth(h);
+    float ms;
+    if (c.kernel == MACLAB_KERNEL_SEGMENT && c.ty == 3) {
+      // the persistent form: one launch of 32 sweeps (64 steps)
+      if (h->seg_persist_blocks < 1 || h->seg_depth != 2) continue;
+      ms = time_ms(h->stream, 1, [&]() {
+             launch_batch_step2_persist(h->precision, h->d_seg_inst, h->d_seg_items, h->seg_n_items, h->cur,
+                                        h->seg_persist_blocks, 32, h->d_seg_deps, h->d_seg_done, step_status(),
+                                        kWaitLimit, h->stream);
+           }) / 64.f;
+    } else {
+      ms = graph_ms(8);
+      if (ms < 0.5f) ms = graph_ms(64) / 8.f;
+      ms /= 8 * launch_depth(h);
+    }
     if (ms < best) {
       best = ms;
       bkernel = c.kernel;

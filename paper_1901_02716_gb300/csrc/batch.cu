@@ -22,6 +22,7 @@
 //  * The three destination rows of momentum sums live in registers, as in
 //    step_tiled.
 
+#include <algorithm>
 #include <vector>
 
 #include "step_tiled.cuh"
@@ -372,23 +373,17 @@ __device__ __forceinline__ void zero_sums(P (&a)[2][3]) {
     for (int k = 0; k < 3; ++k) a[q][k] = P{0, 0};
 }
 
-// FP32: three blocks per SM; FP64 needs more registers (two blocks)
+// Two updates of every work item, reading buffer cur and writing cur ^ 1:
+// the work of one launch of batch_step2_d2q9 (and of one sweep of the
+// persistent kernel below).
 template <typename S>
-__global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(const BatchInst* __restrict__ insts,
-                                                           const BatchItem* __restrict__ items,
-                                                           int n_items, int cur) {
+__device__ __forceinline__ void batch2_sweep(const BatchInst* __restrict__ insts,
+                                             const BatchItem* __restrict__ items, int n_items, int cur,
+                                             const RowRing<S, 3>& ring, int lane, int warp, int nwarps) {
   using C = typename Store<S>::C;
   using O = Pair<C>;
   using P = typename O::P;
   constexpr int K = 3;
-  extern __shared__ __align__(16) unsigned char batch_smem[];
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const RowRing<S, K> ring(batch_smem, threadIdx.x >> 5, lane);
-  pdl_wait();  // the previous step's writes are visible from here on
-  pdl_launch_next();
-
   for (int it = warp; it < n_items; it += nwarps) {
     const BatchItem item = items[it];
     const BatchInst& I = insts[item.inst];
@@ -560,6 +555,80 @@ __global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(
   }
 }
 
+// FP32: three blocks per SM; FP64 needs more registers (two blocks)
+template <typename S>
+__global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3) batch_step2_d2q9(const BatchInst* __restrict__ insts,
+                                                           const BatchItem* __restrict__ items,
+                                                           int n_items, int cur) {
+  extern __shared__ __align__(16) unsigned char batch_smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const RowRing<S, 3> ring(batch_smem, threadIdx.x >> 5, lane);
+  pdl_wait();  // the previous step's writes are visible from here on
+  pdl_launch_next();
+  batch2_sweep<S>(insts, items, n_items, cur, ring, lane, warp, nwarps);
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Persistent form for small domains: `sweeps` launches' worth of
+// batch_step2_d2q9 (2 sweeps steps) in one cooperative launch, the buffers
+// alternating.  Between sweeps a block waits only for the blocks that own rows
+// within two of its own (deps[deps[b] .. deps[b + 1]), block b's list): after
+// sweep k it sets done[b] = k + 1 and starts sweep k + 1 once those blocks'
+// counters reach k + 1.  Their new rows are then written (its input) and their
+// reads of its rows ended (its output overwrites them).  All blocks are
+// resident, so every wait ends; each is bounded all the same (wait_limit polls),
+// and one that runs out sets bit 1 of *status and ends the block's sweeps (its
+// neighbours' waits then run out in turn).  The state is read through the row ring only
+// (cp.async.cg, from L2), so a block never sees another block's stale values.
+template <typename S>
+__global__ void __launch_bounds__(128, sizeof(S) == 8 ? 2 : 3)
+    batch_step2_persist(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items, int n_items,
+                        int cur, int sweeps, const int* __restrict__ deps, unsigned* __restrict__ done,
+                        unsigned* __restrict__ status, unsigned wait_limit) {
+  extern __shared__ __align__(16) unsigned char batch_smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const RowRing<S, 3> ring(batch_smem, threadIdx.x >> 5, lane);
+  const int d0 = deps[blockIdx.x], d1 = deps[blockIdx.x + 1];
+  for (int k = 0; k < sweeps; ++k) {
+    batch2_sweep<S>(insts, items, n_items, cur ^ (k & 1), ring, lane, warp, nwarps);
+    if (k + 1 == sweeps) break;
+    cp_async_wait<0>();  // no row copy of this sweep lands after the next one starts
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this block's stores are visible before its counter
+      st_release_gpu(&done[blockIdx.x], (unsigned)(k + 1));
+    }
+    int ok = 1;
+    for (int j = d0 + (int)threadIdx.x; ok && j < d1; j += blockDim.x) {
+      const unsigned* f = &done[deps[j]];
+      ok = 0;
+      for (uint32_t it = 0; it < wait_limit; ++it) {
+        if (ld_acquire_gpu(f) >= (unsigned)(k + 1)) {
+          ok = 1;
+          break;
+        }
+      }
+    }
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0 && status) atomicOr(status, 2u);
+      break;
+    }
+  }
+}
+
 template <typename S>
 static cudaError_t launch_batch2_t(const BatchInst* insts, const BatchItem* items, int n_items,
                                    int cur, int blocks, cudaStream_t st, int overlap) {
@@ -599,6 +668,112 @@ cudaError_t launch_batch_step2(int precision, const void* insts, const void* ite
     case MACLAB_F32: return launch_batch2_t<float>(I, T, n_items, cur, blocks, st, overlap);
   }
   return cudaErrorInvalidValue;
+}
+
+template <typename S>
+static cudaError_t persist_setup(int* capacity) {
+  constexpr size_t smem = 4 * RowRing<S, 3>::warp_bytes;  // 4 warps
+  auto kern = batch_step2_persist<S>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  *capacity = per_sm * sms;
+  return cudaSuccess;
+}
+
+// Blocks of the persistent launch that can be resident at once (its limit).
+cudaError_t batch_persist_capacity(int precision, int* capacity) {
+  *capacity = 0;
+  switch (precision) {
+    case MACLAB_F64: return persist_setup<double>(capacity);
+    case MACLAB_F32: return persist_setup<float>(capacity);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename S>
+static cudaError_t launch_batch2_persist_t(const BatchInst* insts, const BatchItem* items, int n_items, int cur,
+                                           int blocks, int sweeps, const int* deps, unsigned* done,
+                                           unsigned* status, unsigned wait_limit, cudaStream_t st) {
+  constexpr size_t smem = 4 * RowRing<S, 3>::warp_bytes;
+  int capacity = 0;
+  cudaError_t e = persist_setup<S>(&capacity);
+  if (e != cudaSuccess) return e;
+  // a cooperative launch: every block resident at once (the waits need it);
+  // the dependency lists were built for exactly this block count
+  if (blocks < 1 || blocks > capacity) return cudaErrorCooperativeLaunchTooLarge;
+  if ((e = cudaMemsetAsync(done, 0, (size_t)blocks * sizeof(unsigned), st)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_step2_persist<S>, insts, items, n_items, cur, sweeps, deps, done, status,
+                            wait_limit);
+}
+
+// `sweeps` two-step launches in one persistent cooperative launch (FP32 and
+// FP64 storage).  deps: the lists of batch_persist_deps for `blocks` blocks;
+// done: `blocks` counters (zeroed here); wait_limit: polls before a wait gives up.
+cudaError_t launch_batch_step2_persist(int precision, const void* insts, const void* items, int n_items, int cur,
+                                       int blocks, int sweeps, const int* deps, unsigned* done, unsigned* status,
+                                       unsigned wait_limit, cudaStream_t st) {
+  const BatchInst* I = static_cast<const BatchInst*>(insts);
+  const BatchItem* T = static_cast<const BatchItem*>(items);
+  if (sweeps < 1 || !deps || !done) return cudaErrorInvalidValue;
+  switch (precision) {
+    case MACLAB_F64:
+      return launch_batch2_persist_t<double>(I, T, n_items, cur, blocks, sweeps, deps, done, status, wait_limit, st);
+    case MACLAB_F32:
+      return launch_batch2_persist_t<float>(I, T, n_items, cur, blocks, sweeps, deps, done, status, wait_limit, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The wait lists of the persistent launch: with `blocks` blocks of four warps,
+// warp w takes the items w, w + 4 blocks, ...; item (y0, y1) reads rows
+// y0 - 2 .. y1 + 1 (wrapped where y is periodic) of every x segment and
+// writes rows y0 .. y1 - 1.  Block b waits for every other block owning a row
+// that one of its items reads; the relation is symmetric, so these are also
+// the blocks that read b's rows.  out: blocks + 1 offsets (relative to the
+// array's start), then the lists.
+void batch_persist_deps(const std::vector<int>& items4, int ny, bool py, int blocks, std::vector<int>& out) {
+  const int n = (int)(items4.size() / 4), nwarps = 4 * blocks;
+  std::vector<std::vector<int>> owners(ny);  // blocks owning row y (ascending, no repeats)
+  for (int i = 0; i < n; ++i) {
+    const int b = (i % nwarps) / 4;
+    for (int y = items4[4 * i + 2]; y < items4[4 * i + 3]; ++y)
+      if (owners[y].empty() || owners[y].back() != b) owners[y].push_back(b);
+  }
+  std::vector<std::vector<int>> dep(blocks);
+  for (int i = 0; i < n; ++i) {
+    const int b = (i % nwarps) / 4;
+    for (int y = items4[4 * i + 2] - 2; y < items4[4 * i + 3] + 2; ++y) {
+      int r = y;
+      if (r < 0 || r >= ny) {
+        if (!py) continue;
+        r = ((r % ny) + ny) % ny;
+      }
+      for (int c : owners[r])
+        if (c != b) dep[b].push_back(c);
+    }
+  }
+  out.assign(blocks + 1, 0);
+  for (int b = 0; b < blocks; ++b) {
+    std::sort(dep[b].begin(), dep[b].end());
+    dep[b].erase(std::unique(dep[b].begin(), dep[b].end()), dep[b].end());
+    out[b] = (int)out.size();
+    out.insert(out.end(), dep[b].begin(), dep[b].end());
+  }
+  out[blocks] = (int)out.size();
 }
 
 size_t batch_inst_bytes() { return sizeof(BatchInst); }

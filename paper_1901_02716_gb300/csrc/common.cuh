@@ -227,6 +227,16 @@ struct KernelInfo {
 };
 bool step_kernel_supported(const Geometry& g, int precision, int kernel);
 int segment_depth(const Geometry& g, int precision, int ty);
+// Defined in batch.cu: `sweeps` two-step launches of the segment kernel in one
+// persistent cooperative launch of `blocks` blocks, each waiting between sweeps
+// (at most wait_limit polls; status bit 1 on a timeout) for the blocks on its
+// list in deps (from batch_persist_deps); done: `blocks` device counters.
+// batch_persist_capacity: the most blocks that can be resident at once.
+cudaError_t launch_batch_step2_persist(int precision, const void* insts, const void* items, int n_items, int cur,
+                                       int blocks, int sweeps, const int* deps, unsigned* done, unsigned* status,
+                                       unsigned wait_limit, cudaStream_t st);
+cudaError_t batch_persist_capacity(int precision, int* capacity);
+void batch_persist_deps(const std::vector<int>& items4, int ny, bool py, int blocks, std::vector<int>& out);
 int segment_rows(const Geometry& g, int tz);
 int pick_step_kernel(const Geometry& g, int precision);
 KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, int ty, int tz);
@@ -361,7 +371,10 @@ struct maclab_ctx {
   // segment kernel (a batch of this one domain): descriptor, work list
   void* d_seg_inst = nullptr;
   void* d_seg_items = nullptr;
-  int seg_n_items = 0, seg_blocks = 0, seg_rows = 0, seg_depth = 1;
+  int* d_seg_deps = nullptr;       // persistent segment launches: each block's wait list
+  unsigned* d_seg_done = nullptr;  // and the blocks' finished-sweep counters
+  int seg_n_items = 0, seg_blocks = 0, seg_rows = 0, seg_depth = 1, seg_persist_blocks = 0;
+  unsigned wait_limit = maclab::kWaitLimit;  // polls before a wait between blocks gives up
   void* d_adj_scratch = nullptr;   // reference adjoint: (L_r, L_m) at every node
   double* d_adj_red = nullptr;     // adjoint: reductions (1 + 4 * n_wall_ids doubles)
 };

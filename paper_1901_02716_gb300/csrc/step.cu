@@ -126,7 +126,7 @@ static cudaError_t launch_naive_lat(const StepLaunch& s, cudaStream_t stream) {
 int segment_depth(const Geometry& g, int precision, int ty) {
   const bool two_ok = (precision == MACLAB_F32 || precision == MACLAB_F64) && g.nx >= 8;
   if (ty == 0) return two_ok && (int64_t)(g.nx / 4) * g.ny < 200000 ? 2 : 1;
-  return ty == 2 && two_ok ? 2 : 1;
+  return (ty == 2 || ty == 3) && two_ok ? 2 : 1;  // 3: two steps, runs in one persistent launch
 }
 
 int segment_rows(const Geometry& g, int tz) {

@@ -75,6 +75,7 @@ SIGNATURES = {
     "maclab_set_lattice_state": (_S, [_H, _VP, ctypes.c_int32]),
     "maclab_step": (_S, [_H, ctypes.c_int64]),
     "maclab_sync": (_S, [_H]),
+    "maclab_set_wait_limit": (_S, [_H, ctypes.c_int64]),
     "maclab_set_kernel": (_S, [_H, ctypes.c_int32]),
     "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "maclab_set_launch_overlap": (_S, [_H, ctypes.c_int32]),
@@ -260,6 +261,10 @@ def maclab_step(h, n):
 
 def maclab_sync(h):
     return _check(lib().maclab_sync(h), "maclab_sync")
+
+
+def maclab_set_wait_limit(h, polls):
+    return _check(lib().maclab_set_wait_limit(h, int(polls)), "maclab_set_wait_limit")
 
 
 def maclab_set_kernel(h, kernel):
@@ -581,6 +586,10 @@ class Solver:
 
     def sync(self):
         maclab_sync(self.handle)
+
+    def set_wait_limit(self, polls=-1):
+        """Polls before a wait between blocks of a persistent launch gives up (-1: default)."""
+        maclab_set_wait_limit(self.handle, polls)
 
 
 class _Member(Solver):

@@ -287,6 +287,61 @@ def test_segment_two_steps_per_launch(precision, steps, dims, periodic, walls):
     t.close()
 
 
+@pytest.mark.parametrize("precision", [M.F64, M.F32])
+@pytest.mark.parametrize("steps", [1, 2, 9, 131])
+@pytest.mark.parametrize("dims,periodic,walls,rows", [((136, 45), 0b01, "mixed", 2), ((256, 256), 0b00, "box", 2),
+                                                      ((8, 12), 0b10, "box", 4), ((64, 64), 0b11, "none", 8)])
+def test_segment_persistent(precision, steps, dims, periodic, walls, rows):
+    """ty = 3: the step pairs of a run in one persistent cooperative launch,
+    each block waiting between sweeps for the blocks that own rows within two
+    of its own instead of a kernel boundary; runs end in a one-step launch.
+    The same bits as the tiled kernel, across calls, and no wait ran out
+    (maclab_sync)."""
+    case = inputs.random_case(D2, dims, periodic, seed=49, u_amp=0.05, walls=walls,
+                              force=(1e-4, -1e-4))
+    s = M.Solver.from_case(case, precision)
+    s.set_kernel(M.KERNEL_SEGMENT)
+    s.set_tile(3, rows)
+    assert s.kernel_info()["steps_per_launch"] == 2
+    s.step(steps)
+    s.step(steps + 3)
+    s.sync()
+    t = M.Solver.from_case(case, precision)
+    t.set_kernel(M.KERNEL_TILED)
+    t.step(2 * steps + 3)
+    assert np.array_equal(s.get_lattice_state(), t.get_lattice_state())
+    assert s.diagnostics()["residual"] == t.diagnostics()["residual"]
+    s.close()
+    t.close()
+
+
+def test_segment_persistent_wait_runs_out():
+    """A zero wait budget makes the persistent launch's first wait between
+    blocks give up at once: the blocks end their sweeps, the next sync reports
+    MACLAB_ERR_TIMEOUT (and only that one), and the context stays usable -- a
+    fresh set_state with the default budget gives the tiled kernel's bits."""
+    case = inputs.random_case(D2, (256, 256), 0b00, seed=50, u_amp=0.05, walls="box")
+    s = M.Solver.from_case(case, M.F32)
+    s.set_kernel(M.KERNEL_SEGMENT)
+    s.set_tile(3, 2)
+    s.set_wait_limit(0)
+    s.step(10)
+    with pytest.raises(M.MacLABError) as e:
+        s.sync()
+    assert e.value.status == M.ERR_TIMEOUT
+    s.sync()  # the status word was cleared
+    s.set_wait_limit(-1)
+    s.set_state(np.asarray(case.rho, np.float64), np.asarray(case.u, np.float64))  # e = 1
+    s.step(10)
+    s.sync()
+    t = M.Solver.from_case(case, M.F32)
+    t.set_kernel(M.KERNEL_TILED)
+    t.step(10)
+    assert np.array_equal(s.get_lattice_state(), t.get_lattice_state())
+    s.close()
+    t.close()
+
+
 def test_segment_default_for_large_2d_and_graphs():
     """1024^2 picks the segment kernel; 40 steps (a 32-step graph and 8
     launches) equal the tiled kernel's bits; a change of rows per item
