@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--inner", type=int, default=100, help="MacLAB steps per benchmark step")
     p.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "f16"])
     p.add_argument("--no-extras", action="store_true", help="skip fp64 / e2e / cpu legs")
-    p.add_argument("--kernel", default="auto", choices=["auto", "reference", "tiled", "folded", "segment", "rows2"])
+    p.add_argument("--kernel", default="auto", choices=["auto", "reference", "tiled", "folded", "segment", "rows2", "block"])
     p.add_argument("--ty", type=int, default=0, help="tiled kernel: rows per tile (0 = default)")
     p.add_argument("--tz", type=int, default=0, help="tiled kernel: planes per block (0 = default)")
     p.add_argument("--replicas", action="store_true",
@@ -305,7 +305,8 @@ def run_ours(args, rank, world, local_rank):
     solver = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
     solver.set_kernel({"auto": M.KERNEL_AUTO, "reference": M.KERNEL_REFERENCE,
                        "tiled": M.KERNEL_TILED, "folded": M.KERNEL_FOLDED,
-                       "segment": M.KERNEL_SEGMENT, "rows2": M.KERNEL_ROWS2}[args.kernel])
+                       "segment": M.KERNEL_SEGMENT, "rows2": M.KERNEL_ROWS2,
+                       "block": M.KERNEL_BLOCK}[args.kernel])
     if args.ty or args.tz:
         solver.set_tile(args.ty, args.tz)
     lups_per_step = case.n_fluid * args.inner

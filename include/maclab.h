@@ -166,7 +166,8 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * memory; nx % 4 == 0; the tile's tz is its rows per work item, default 2
  * up to 65,536 quads and 4 above, and ty the time steps per launch, 1 or 2,
  * default 2 below 200,000 quads where two steps are supported, see
- * maclab_batch_set_depth), the default for D2Q9 grids with nx % 4 == 0.  All compute Eqs.
+ * maclab_batch_set_depth), the default for D2Q9 grids with nx % 4 == 0 that the
+ * block kernel does not take (below).  All compute Eqs.
  * (4)-(5) with the same terms per node (the folded kernel sums them in
  * another order; the segment and tiled kernels give identical bits).
  * MACLAB_KERNEL_ROWS2 is the D3Q19 kernel with two rows per thread (FP32,
@@ -175,13 +176,24 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * 16-bit storage; the default for FP32 storage where it applies): the
  * equilibria moving between a thread's rows stay in registers and the rest of
  * the y exchange is read 16 bytes per direction; its terms are formed and
- * summed in yet another order, so it agrees with the others to rounding. */
+ * summed in yet another order, so it agrees with the others to rounding.
+ * MACLAB_KERNEL_BLOCK is the block-resident D2Q9 kernel (FP32 or FP64
+ * storage, nx % 4 == 0): a launch takes ty steps (1, 2, 4 or, with FP32, 8;
+ * default 8 up to 65,536 node pairs and 4 above; FP64 4 up to 16,384 pairs
+ * and 2 above) on tiles of 32 x 32
+ * node pairs (FP64: 32 x 16; pair j of a row holds x = j and x = j + nx / 2) held in registers
+ * and shared memory, each with a halo of ty pairs and rows, so the state
+ * passes through global memory once per ty steps; a run of n steps ends with
+ * a one-step launch (the previous state is step n - 1).  Its sums run in the
+ * tiled kernel's order: identical bits.  The default for FP32 and FP64 D2Q9
+ * grids of up to 131,072 node pairs (512^2). */
 #define MACLAB_KERNEL_AUTO 0
 #define MACLAB_KERNEL_REFERENCE 1
 #define MACLAB_KERNEL_TILED 2
 #define MACLAB_KERNEL_FOLDED 3
 #define MACLAB_KERNEL_SEGMENT 4
 #define MACLAB_KERNEL_ROWS2 5
+#define MACLAB_KERNEL_BLOCK 6
 
 /* Choose the step kernel.  MACLAB_ERR_UNSUPPORTED if the tiled kernel cannot
  * serve this domain (then the handle keeps its previous choice). */

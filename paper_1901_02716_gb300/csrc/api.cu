@@ -554,13 +554,16 @@ static StepLaunch step_launch(const maclab_ctx* h, int from) {
   s.seg_blocks = h->seg_blocks;
   s.cur = from;
   s.seg_depth = h->seg_depth;
-  s.seg_steps = h->kernel == MACLAB_KERNEL_SEGMENT ? h->seg_depth : 1;
+  s.seg_steps = h->kernel == MACLAB_KERNEL_SEGMENT ? h->seg_depth
+                : h->kernel == MACLAB_KERNEL_BLOCK ? block_steps(h->g, h->precision, h->ty)
+                                                   : 1;
   s.overlap = h->overlap;
   return s;
 }
 
 // Time steps one launch of the handle's kernel advances.
 static int launch_depth(const maclab_ctx* h) {
+  if (h->kernel == MACLAB_KERNEL_BLOCK) return block_steps(h->g, h->precision, h->ty);
   return h->kernel == MACLAB_KERNEL_SEGMENT ? h->seg_depth : 1;
 }
 
@@ -1022,7 +1025,7 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
     return MACLAB_OK;
   }
   if (kernel != MACLAB_KERNEL_REFERENCE && kernel != MACLAB_KERNEL_TILED && kernel != MACLAB_KERNEL_FOLDED &&
-      kernel != MACLAB_KERNEL_SEGMENT && kernel != MACLAB_KERNEL_ROWS2)
+      kernel != MACLAB_KERNEL_SEGMENT && kernel != MACLAB_KERNEL_ROWS2 && kernel != MACLAB_KERNEL_BLOCK)
     return fail(MACLAB_ERR_INVALID, "unknown kernel id");
   if (!step_kernel_supported(h->g, h->precision, kernel))
     return fail(MACLAB_ERR_UNSUPPORTED, "kernel does not support this domain");
@@ -1030,6 +1033,7 @@ maclab_status maclab_set_kernel(maclab_handle h, int32_t kernel) {
   // a tile shape the new kernel lacks falls back to its default
   if (kernel == MACLAB_KERNEL_FOLDED && !fold_supported(h->g, h->precision, h->ty)) h->ty = 0;
   if (kernel == MACLAB_KERNEL_ROWS2 && !rows2_supported(h->g, h->precision, h->ty)) h->ty = 0;
+  if (kernel == MACLAB_KERNEL_BLOCK && !block_supported(h->g, h->precision, h->ty)) h->ty = 0;
   if (kernel == MACLAB_KERNEL_TILED && !tiled_supported(h->g, h->precision, h->ty, h->tz)) h->ty = 0;
   return MACLAB_OK;
 }
@@ -1053,6 +1057,7 @@ maclab_status maclab_set_tile(maclab_handle h, int32_t ty, int32_t tz) {
   if (ty < 0 || tz < 0 || tz > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad tile shape");
   const bool ok = h->kernel == MACLAB_KERNEL_FOLDED    ? fold_supported(h->g, h->precision, ty)
                   : h->kernel == MACLAB_KERNEL_ROWS2   ? rows2_supported(h->g, h->precision, ty)
+                  : h->kernel == MACLAB_KERNEL_BLOCK   ? block_supported(h->g, h->precision, ty)  // ty: steps
                   : h->kernel == MACLAB_KERNEL_SEGMENT
                       ? (ty <= 1 || segment_depth(h->g, h->precision, ty) == 2)  // ty: steps per launch, tz: rows
                                                        : tiled_supported(h->g, h->precision, ty, tz);
@@ -1200,7 +1205,9 @@ cudaError_t batch_launch_steps(maclab_batch_ctx* b, int c, int steps, cudaStream
     return launch_batch_step(b->precision, b->d_insts, b->d_items, b->n_items, c, b->blocks,
                              b->depth == 2 ? kBatchSegW2 : kBatchSegW1, st, b->overlap);
   for (maclab_ctx* m : b->members) {
-    cudaError_t e = launch_step(step_launch(m, c), st, m->kernel);
+    StepLaunch sl = step_launch(m, c);
+    sl.seg_steps = 1;  // one step per member launch (the block kernel's one-step form)
+    cudaError_t e = launch_step(sl, st, m->kernel);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1275,9 +1282,11 @@ maclab_status maclab_batch_create(const maclab_config* cfgs, int32_t count, macl
   DeviceGuard dg(b->device);
   b->one_launch = b->lattice == MACLAB_D2Q9;
   for (maclab_ctx* m : b->members) b->one_launch = b->one_launch && m->g.ilv == 1;
-  if (!b->one_launch)  // one launch per member and step: the segment kernel's work list is not built
+  // one launch per member and step: the segment kernel's work list is not
+  // built, and the block kernel would take one step per launch
+  if (!b->one_launch)
     for (maclab_ctx* m : b->members)
-      if (m->kernel == MACLAB_KERNEL_SEGMENT)
+      if (m->kernel == MACLAB_KERNEL_SEGMENT || m->kernel == MACLAB_KERNEL_BLOCK)
         m->kernel = tiled_supported(m->g, m->precision, 0, 0) ? MACLAB_KERNEL_TILED : MACLAB_KERNEL_REFERENCE;
   if (b->one_launch) {
     std::vector<unsigned char> insts(batch_inst_bytes() * b->members.size());
@@ -1424,6 +1433,7 @@ bool shape_supported(const maclab_ctx* h, int kernel, int ty, int tz) {
     return step_kernel_supported(h->g, h->precision, MACLAB_KERNEL_SEGMENT) &&
            (ty <= 1 || segment_depth(h->g, h->precision, ty) == 2);
   if (kernel == MACLAB_KERNEL_ROWS2) return rows2_supported(h->g, h->precision, ty);
+  if (kernel == MACLAB_KERNEL_BLOCK) return block_supported(h->g, h->precision, ty);
   return kernel == MACLAB_KERNEL_FOLDED ? fold_supported(h->g, h->precision, ty)
                                         : tiled_supported(h->g, h->precision, ty, tz);
 }
@@ -1601,6 +1611,7 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
       for (int tz : tzs) cands.push_back(Cand{kernel, h->g.d == 3 ? tys3[a] : 0, tz});
   for (int ty : {1, 2, 3})  // 3: two steps per sweep, runs in one persistent launch
     for (int tz : {2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_SEGMENT, ty, tz});
+  for (int ty : {1, 2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_BLOCK, ty, 0});  // ty: steps per launch
   if (h->g.d == 3)
     for (int ty : {4, 8})
       for (int tz : tzs) cands.push_back(Cand{MACLAB_KERNEL_ROWS2, ty, tz});

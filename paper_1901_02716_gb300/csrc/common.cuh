@@ -213,19 +213,25 @@ struct StepLaunch {
   const void* seg_items = nullptr;
   int seg_n_items = 0, seg_blocks = 0, cur = 0;
   int seg_depth = 1;  // steps per launch the work list was cut for (1 or 2)
-  int seg_steps = 1;  // steps this launch advances (1, or 2 with seg_depth 2)
+  int seg_steps = 1;  // steps this launch advances (segment: 1, or 2 with seg_depth 2; block: 1 to 8)
   int overlap = 0;    // programmatic dependent launch (launch_kernel)
 };
 
 // Defined in step.cu.  Kernel ids follow MACLAB_KERNEL_* of maclab.h.
 struct KernelInfo {
-  int id;                // MACLAB_KERNEL_REFERENCE / _TILED / _FOLDED / _SEGMENT
+  int id;                // MACLAB_KERNEL_REFERENCE / _TILED / _FOLDED / _SEGMENT / _ROWS2 / _BLOCK
   int steps_per_launch;  // time steps one launch group advances
   int launches;          // kernel launches in one group
   int threads;           // threads per block
   const char* name;      // static name of the instance
 };
 bool step_kernel_supported(const Geometry& g, int precision, int kernel);
+// Defined in step_block.cu: the block-resident D2Q9 kernel (ty = steps per
+// launch: 1, 2, 4 or, with FP32 storage, 8; 0 = by size; FP32 / FP64 storage, nx % 4 == 0).
+int block_steps(const Geometry& g, int precision, int ty);
+bool block_supported(const Geometry& g, int precision, int ty);
+int block_threads(int precision);
+cudaError_t launch_block(const StepLaunch& s, cudaStream_t stream, int steps);
 int segment_depth(const Geometry& g, int precision, int ty);
 // Defined in batch.cu: `sweeps` two-step launches of the segment kernel in one
 // persistent cooperative launch of `blocks` blocks, each waiting between sweeps

@@ -140,18 +140,25 @@ bool step_kernel_supported(const Geometry& g, int precision, int kernel) {
   if (kernel == MACLAB_KERNEL_FOLDED) return fold_supported(g, precision, 0);
   if (kernel == MACLAB_KERNEL_SEGMENT) return g.lattice == kD2Q9 && g.ilv == 1;
   if (kernel == MACLAB_KERNEL_ROWS2) return rows2_supported(g, precision, 0);
+  if (kernel == MACLAB_KERNEL_BLOCK) return block_supported(g, precision, 0);
   return false;
 }
 
 // D3Q19 with FP32 storage: the two-rows-per-thread kernel where it applies
 // (rows of up to 128 nodes), else the folded one where it is built (ny a
-// multiple of its tile rows); for D2Q9 grids with nx % 4 == 0 the segment
-// kernel (with its size defaults it is faster than the tiled one from 64^2 to
-// 1024^2); else the tiled one, else the reference kernel.
+// multiple of its tile rows); for D2Q9 grids with nx % 4 == 0 the block kernel
+// with FP32 or FP64 storage up to 131,072 node pairs (512^2; measured on a
+// GB300, FP32: 1.9x the segment kernel at 128^2 and 256^2, 1.16x at 512^2;
+// FP64: 1.9x to 2.4x), else the segment
+// kernel (faster than the tiled one from 64^2 to 1024^2 with its size
+// defaults, and than the block kernel above 512^2); else the tiled one, else
+// the reference kernel.
 int pick_step_kernel(const Geometry& g, int precision) {
   if (precision == MACLAB_F32 && step_kernel_supported(g, precision, MACLAB_KERNEL_ROWS2))
     return MACLAB_KERNEL_ROWS2;
   if (step_kernel_supported(g, precision, MACLAB_KERNEL_FOLDED)) return MACLAB_KERNEL_FOLDED;
+  if ((int64_t)(g.nx / 2) * g.ny <= 131072 && step_kernel_supported(g, precision, MACLAB_KERNEL_BLOCK))
+    return MACLAB_KERNEL_BLOCK;
   if (step_kernel_supported(g, precision, MACLAB_KERNEL_SEGMENT)) return MACLAB_KERNEL_SEGMENT;
   return step_kernel_supported(g, precision, MACLAB_KERNEL_TILED) ? MACLAB_KERNEL_TILED
                                                                  : MACLAB_KERNEL_REFERENCE;
@@ -167,6 +174,11 @@ static const char* kernel_name(const Geometry& g, int precision, int kernel) {
     static const char* fold[4] = {"step_fold<D3Q19,f64>", "step_fold<D3Q19,f32>", "step_fold<D3Q19,bf16>",
                                   "step_fold<D3Q19,f16>"};
     return fold[precision & 3];
+  }
+  if (kernel == MACLAB_KERNEL_BLOCK) {
+    static const char* blk[4] = {"step_block<D2Q9,f64>", "step_block<D2Q9,f32>", "step_block<D2Q9,bf16>",
+                                 "step_block<D2Q9,f16>"};
+    return blk[precision & 3];
   }
   if (kernel == MACLAB_KERNEL_SEGMENT) {
     static const char* seg[4] = {"segment<D2Q9,f64>", "segment<D2Q9,f32>", "segment<D2Q9,bf16>",
@@ -194,6 +206,9 @@ KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, in
                       kernel_name(g, precision, kernel)};
   if (kernel == MACLAB_KERNEL_ROWS2)
     return KernelInfo{MACLAB_KERNEL_ROWS2, 1, 1, rows2_threads(g, precision, ty), kernel_name(g, precision, kernel)};
+  if (kernel == MACLAB_KERNEL_BLOCK)
+    return KernelInfo{MACLAB_KERNEL_BLOCK, block_steps(g, precision, ty), 1, block_threads(precision),
+                      kernel_name(g, precision, kernel)};
 
   if (kernel == MACLAB_KERNEL_SEGMENT) {
     const int depth = segment_depth(g, precision, ty);
@@ -213,6 +228,8 @@ cudaError_t launch_step(const StepLaunch& s, cudaStream_t stream, int kernel) {
       return launch_fold(s, stream, s.ty, s.tz);
     case MACLAB_KERNEL_ROWS2:
       return launch_rows2(s, stream, s.ty, s.tz);
+    case MACLAB_KERNEL_BLOCK:
+      return launch_block(s, stream, s.seg_steps);
     case MACLAB_KERNEL_SEGMENT:
       if (!s.seg_inst || !s.seg_items) return cudaErrorInvalidValue;
       if (s.seg_steps == 2)

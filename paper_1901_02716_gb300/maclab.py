@@ -22,7 +22,8 @@ F64, F32, BF16_STORE, F16_STORE = 0, 1, 2, 3
 HOST, DEVICE = 0, 1
 DTYPE_F64, DTYPE_F32 = 0, 1
 OK, WARN_RLE = 0, 1
-KERNEL_AUTO, KERNEL_REFERENCE, KERNEL_TILED, KERNEL_FOLDED, KERNEL_SEGMENT, KERNEL_ROWS2 = 0, 1, 2, 3, 4, 5
+KERNEL_AUTO, KERNEL_REFERENCE, KERNEL_TILED, KERNEL_FOLDED, KERNEL_SEGMENT, KERNEL_ROWS2, KERNEL_BLOCK = (
+    0, 1, 2, 3, 4, 5, 6)
 ERR_INVALID, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_OOM, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 
 PRECISION_NAMES = {"f64": F64, "f32": F32, "bf16": BF16_STORE, "f16": F16_STORE}

@@ -113,7 +113,7 @@ def test_single_domain_tune(lat, dims, periodic, walls):
     ty, tz = s.tune()
     assert np.array_equal(s.get_lattice_state(), x)
     kernel = s.kernel_info()["kernel"]
-    assert kernel in (M.KERNEL_TILED, M.KERNEL_FOLDED, M.KERNEL_SEGMENT)
+    assert kernel in (M.KERNEL_TILED, M.KERNEL_FOLDED, M.KERNEL_SEGMENT, M.KERNEL_ROWS2, M.KERNEL_BLOCK)
     s.step(3)
     r_g, u_g = s.get_state()
     r_o, u_o = orc.step(lat, case.rho, case.u, periodic, wall=case.wall_mask, nsteps=5)
@@ -199,8 +199,8 @@ def test_two_steps_per_launch_refused(kind):
 def test_batch_2d_fallback_with_a_non_interleaved_member():
     """A D2Q9 batch with a member whose nx is not a multiple of 4 steps one
     launch per member; the other members then use the tiled kernel (their
-    default segment kernel needs the single launch's work list) and still equal
-    standalone runs bit for bit."""
+    default block or segment kernels take several steps per launch or need the
+    single launch's work list) and still equal standalone runs bit for bit."""
     cases = [inputs.random_case(D2, (64, 40), 0b00, seed=86, walls="box"),
              inputs.random_case(D2, (30, 20), 0b11, seed=87),
              inputs.random_case(D2, (512, 300), 0b01, seed=88, walls="mixed")]
