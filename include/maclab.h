@@ -180,9 +180,10 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * MACLAB_KERNEL_BLOCK is the block-resident D2Q9 kernel (FP32 or FP64
  * storage, nx % 4 == 0): a launch takes ty steps (1, 2, 4 or, with FP32, 8;
  * default 8 up to 65,536 node pairs and 4 above; FP64 4 up to 16,384 pairs
- * and 2 above) on tiles of 32 x 32
- * node pairs (FP64: 32 x 16; pair j of a row holds x = j and x = j + nx / 2) held in registers
- * and shared memory, each with a halo of ty pairs and rows, so the state
+ * and 2 above) on tiles of 32 x 32 node pairs (pair j of a row holds x = j
+ * and x = j + nx / 2; FP32: 2 x 2 pairs per thread, FP64: 32 x 16 pairs, one
+ * per thread) held in registers, exchanging equilibria through warp shuffles
+ * and shared memory, each tile with a halo of ty pairs and rows, so the state
  * passes through global memory once per ty steps; a run of n steps ends with
  * a one-step launch (the previous state is step n - 1).  Its sums run in the
  * tiled kernel's order: identical bits.  The default for FP32 and FP64 D2Q9
