@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--side", type=int, default=128, help="cavity side (nodes, walls included)")
     p.add_argument("--lattice", default="d3q19", choices=["d3q19", "d2q9"],
                    help="d2q9: the 2D lid-driven cavity of the same side instead (diagnostic runs)")
+    p.add_argument("--case", default="cavity", choices=["cavity", "tgv"],
+                   help="tgv: the periodic 3D Taylor-Green field (u0 = 0.02) of the same side instead "
+                        "(diagnostic runs, D3Q19)")
     p.add_argument("--re", type=float, default=100.0)
     p.add_argument("--inner", type=int, default=100, help="MacLAB steps per benchmark step")
     p.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "f16"])
@@ -299,6 +302,9 @@ def run_ours(args, rank, world, local_rank):
     if args.lattice == "d2q9":
         from paper_1901_02716_gb300 import inputs
         case = inputs.cavity2d(args.side, lid=inputs.lid_speed(args.re, args.side))
+    elif args.case == "tgv":
+        from paper_1901_02716_gb300 import inputs
+        case = inputs.tgv3d(args.side, 0.02)
     else:
         case = cavity_case(args.side, args.re)
     stream = torch.cuda.current_stream()
@@ -358,9 +364,11 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": (f"3D lid-driven cavity D3Q19 {args.side}^3" if d == 3 else
-                                f"2D lid-driven cavity D2Q9 {args.side}^2") +
-                               f" (walls included), Re={args.re:g}, {args.precision} storage",
+        "config": {"workload": (f"periodic 3D Taylor-Green field D3Q19 {args.side}^3, u0=0.02, "
+                                f"{args.precision} storage" if d == 3 and args.case == "tgv" else
+                                (f"3D lid-driven cavity D3Q19 {args.side}^3" if d == 3 else
+                                 f"2D lid-driven cavity D2Q9 {args.side}^2") +
+                                f" (walls included), Re={args.re:g}, {args.precision} storage"),
                    "inner_steps": args.inner, "fluid_nodes": case.n_fluid,
                    "l2": "flushed (256 MiB write) before each timed step",
                    "parallelism": f"replicas x{world}"},
@@ -585,7 +593,8 @@ def suite_leg(M, stream):
             ("cavity3d_128_bf16", cavity_case(128, 100.0), 100, M.BF16_STORE),
             ("tgv3d_96", inputs.tgv3d(96, 0.02), 128, M.F32),
             ("cavity2d_8192_hbm", inputs.cavity2d(8192, lid=inputs.lid_speed(1000.0, 8192)), 20, M.F32),
-            ("cavity3d_512_hbm", inputs.cavity3d(512, lid=inputs.lid_speed(100.0, 512)), 10, M.F32)):
+            ("cavity3d_512_hbm", inputs.cavity3d(512, lid=inputs.lid_speed(100.0, 512)), 10, M.F32),
+            ("cavity3d_512_bf16_hbm", inputs.cavity3d(512, lid=inputs.lid_speed(100.0, 512)), 10, M.BF16_STORE)):
         s = M.Solver.from_case(case, prec, stream=ctypes_stream(stream))
         tile = s.tune()
         ms = _timed_steps(torch, stream, s.step, steps)

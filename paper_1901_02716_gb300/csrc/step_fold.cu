@@ -8,14 +8,14 @@ namespace maclab {
 namespace {
 
 // Instantiated (BXC, TY) in order of preference for each width (the first whose
-// TY divides ny is the default): FP32 all of them, 16-bit storage the three
-// middle widths' shapes.
+// TY divides ny is the default): FP32 all of them, 16-bit storage (32, 8),
+// (32, 4), (64, 4) and (128, 4).
 constexpr FoldShape kFoldShapes[] = {{16, 8}, {32, 8}, {32, 4}, {64, 4}, {64, 8}, {128, 4}};
 
 bool fold_shape_built(const FoldShape& s, int precision) {
   if (precision == MACLAB_F32) return true;
   if (precision == MACLAB_BF16_STORE || precision == MACLAB_F16_STORE)
-    return (s.bxc == 32 && (s.ty == 8 || s.ty == 4)) || (s.bxc == 64 && s.ty == 4);
+    return (s.bxc == 32 && (s.ty == 8 || s.ty == 4)) || ((s.bxc == 64 || s.bxc == 128) && s.ty == 4);
   return false;
 }
 

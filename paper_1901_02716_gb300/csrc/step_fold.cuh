@@ -26,7 +26,7 @@ struct FoldShape {
 };
 
 // Launch dispatch for 16-bit storage (step_fold_s16.cu): shapes (32, 8),
-// (32, 4) and (64, 4); with resident set, only the blocks one SM holds.
+// (32, 4), (64, 4) and (128, 4); with resident set, only the blocks one SM holds.
 cudaError_t fold_dispatch_s16(int precision, const FoldShape& s, const TiledArgs& ta, const void* in,
                               void* out, cudaStream_t st, dim3 grid, int* resident);
 

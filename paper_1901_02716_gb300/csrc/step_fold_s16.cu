@@ -15,6 +15,7 @@ cudaError_t dispatch_t(const FoldShape& s, const TiledArgs& ta, const void* in, 
     case 3208: return launch_fold_shape<S, 32, 8>(ta, in, out, st, grid, resident);
     case 3204: return launch_fold_shape<S, 32, 4>(ta, in, out, st, grid, resident);
     case 6404: return launch_fold_shape<S, 64, 4>(ta, in, out, st, grid, resident);
+    case 12804: return launch_fold_shape<S, 128, 4>(ta, in, out, st, grid, resident);
   }
   return cudaErrorInvalidValue;
 }

@@ -212,6 +212,25 @@ def test_folded_kernel_16bit_storage(precision, dims, periodic, walls, ty):
     assert np.abs(r_f - r_t).max() <= 4 * ulp * 0.05
 
 
+@pytest.mark.parametrize("precision", [M.BF16_STORE, M.F16_STORE])
+@pytest.mark.parametrize("dims,periodic,walls", [((400, 8, 6), 0b000, "box"), ((512, 4, 5), 0b111, "none"),
+                                                 ((272, 12, 5), 0b010, "mixed")])
+def test_folded_kernel_16bit_wide_rows(precision, dims, periodic, walls):
+    """Rows of 65 to 128 quads (up to 512 nodes) in 16-bit storage run the
+    folded kernel by default (no tiled instance serves them), within the
+    stated storage error against the oracle."""
+    case = inputs.random_case(D3, dims, periodic, seed=56, u_amp=0.08, rho_amp=0.02, walls=walls,
+                              force=(1e-4, 0.0, -1e-4))
+    s = M.Solver.from_case(case, precision)
+    assert s.kernel_info()["kernel"] == M.KERNEL_FOLDED
+    s.step(7)
+    r_g, u_g = s.get_state()
+    s.close()
+    r_o, u_o = orc.step(D3, case.rho, case.u, case.periodic, wall=case.wall_mask, force=case.force,
+                        nsteps=7)
+    assert_parity(r_g, u_g, r_o, u_o, precision)
+
+
 @pytest.mark.parametrize("precision,dims", [(M.F64, (32, 8, 5)), (M.F32, (32, 6, 5)),
                                             (M.F32, (16, 12, 5)), (M.BF16_STORE, (16, 8, 5))])
 def test_folded_rejects_unsupported(precision, dims):
