@@ -514,6 +514,20 @@ maclab_status maclab_sync(maclab_handle h);
  * counterpart.  Errors: MACLAB_ERR_INVALID (NULL handle, polls > 2^32 - 1). */
 maclab_status maclab_set_wait_limit(maclab_handle h, int64_t polls);
 
+/* The persistent segment launch's work items and wait lists for a D2Q9 domain
+ * of nx x ny nodes (nx % 4 == 0, nx >= 8; periodic_y != 0 if y wraps), rows
+ * rows per item and `blocks` blocks of four warps (warp w takes items w,
+ * w + 4 blocks, ...).  items receives 4 ints per item (0, x segment, first
+ * row, end row); waits receives blocks + 1 offsets into waits itself, then
+ * each block's list of the other blocks it waits for between sweeps.  lens[0]
+ * and lens[1] receive the number of ints each needs; with a capacity that is
+ * too small nothing is copied and MACLAB_ERR_INVALID is returned (call with
+ * 0 capacities to size the arrays).  Host only, no device work.  A
+ * verification aid with no paper counterpart. */
+maclab_status maclab_debug_segment_waits(int32_t nx, int32_t ny, int32_t periodic_y, int32_t rows,
+                                         int32_t blocks, int32_t *items, int64_t items_cap, int32_t *waits,
+                                         int64_t waits_cap, int64_t lens[2]);
+
 /* Name of a status code (static string). */
 const char *maclab_status_string(maclab_status s);
 

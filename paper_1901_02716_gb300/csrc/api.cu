@@ -1094,6 +1094,31 @@ maclab_status maclab_sync(maclab_handle h) {
   return MACLAB_OK;
 }
 
+maclab_status maclab_debug_segment_waits(int32_t nx, int32_t ny, int32_t periodic_y, int32_t rows,
+                                         int32_t blocks, int32_t* items, int64_t items_cap, int32_t* waits,
+                                         int64_t waits_cap, int64_t lens[2]) {
+  if (!lens) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (nx < 8 || nx % 4 != 0 || ny < 1 || rows < 1 || blocks < 1)
+    return fail(MACLAB_ERR_INVALID, "bad segment shape");
+  Geometry g{};
+  g.lattice = kD2Q9;
+  g.d = 2;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = 1;
+  g.n = (int64_t)nx * ny;
+  std::vector<int> it, w;
+  batch_items(0, g, rows, 2, it);
+  batch_persist_deps(it, ny, periodic_y != 0, blocks, w);
+  lens[0] = (int64_t)it.size();
+  lens[1] = (int64_t)w.size();
+  if (items_cap < lens[0] || waits_cap < lens[1] || (lens[0] && !items) || (lens[1] && !waits))
+    return fail(MACLAB_ERR_INVALID, "output arrays too small (lens holds the sizes)");
+  std::copy(it.begin(), it.end(), items);
+  std::copy(w.begin(), w.end(), waits);
+  return MACLAB_OK;
+}
+
 maclab_status maclab_set_wait_limit(maclab_handle h, int64_t polls) {
   if (!h) return fail(MACLAB_ERR_INVALID, "NULL handle");
   if (polls > (int64_t)0xffffffffu) return fail(MACLAB_ERR_INVALID, "wait limit above 2^32 - 1");

@@ -77,6 +77,8 @@ SIGNATURES = {
     "maclab_step": (_S, [_H, ctypes.c_int64]),
     "maclab_sync": (_S, [_H]),
     "maclab_set_wait_limit": (_S, [_H, ctypes.c_int64]),
+    "maclab_debug_segment_waits": (_S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "maclab_set_kernel": (_S, [_H, ctypes.c_int32]),
     "maclab_set_tile": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
     "maclab_set_launch_overlap": (_S, [_H, ctypes.c_int32]),
@@ -266,6 +268,20 @@ def maclab_sync(h):
 
 def maclab_set_wait_limit(h, polls):
     return _check(lib().maclab_set_wait_limit(h, int(polls)), "maclab_set_wait_limit")
+
+
+def maclab_debug_segment_waits(nx, ny, periodic_y, rows, blocks):
+    """(items [n, 4], waits) of the persistent segment launch (host only)."""
+    lens = (ctypes.c_int64 * 2)()
+    L = lib()
+    s = L.maclab_debug_segment_waits(nx, ny, int(periodic_y), rows, blocks, None, 0, None, 0, lens)
+    if s != ERR_INVALID or lens[0] == 0:
+        _check(s, "maclab_debug_segment_waits")
+    items = np.zeros(lens[0], dtype=np.int32)
+    waits = np.zeros(max(lens[1], 1), dtype=np.int32)
+    _check(L.maclab_debug_segment_waits(nx, ny, int(periodic_y), rows, blocks, items.ctypes.data, lens[0],
+                                        waits.ctypes.data, lens[1], lens), "maclab_debug_segment_waits")
+    return items.reshape(-1, 4), waits[:lens[1]]
 
 
 def maclab_set_kernel(h, kernel):
