@@ -582,67 +582,82 @@ static int device_sms() {
 // else one), built on first use and after a change of either; graphs captured
 // with the old list are dropped.  Synchronises the handle's stream when it
 // uploads.
+// The persistent form's wait lists (segment kernel, ty 3): as many blocks as
+// fit at once, each with the list of blocks it waits for between sweeps.
+// Built on first use for the current work list.
+static maclab_status segment_persist_prepare(maclab_ctx* h) {
+  if (h->seg_persist_blocks > 0 || h->seg_depth != 2) return MACLAB_OK;
+  int capacity = 0;
+  if (batch_persist_capacity(h->precision, &capacity) != cudaSuccess || capacity < 1) {
+    cudaGetLastError();
+    return MACLAB_OK;  // the form is unavailable; stepping uses graphs of launches
+  }
+  const int want = (h->seg_n_items + 3) / 4;
+  const int pb = want < capacity ? (want > 0 ? want : 1) : capacity;
+  std::vector<int> deps;
+  batch_persist_deps(h->seg_items_host, h->g.ny, (h->g.periodic & 2u) != 0, pb, deps);
+  if (cudaMalloc(&h->d_seg_deps, deps.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_seg_done, (size_t)pb * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->d_seg_deps);
+    h->d_seg_deps = nullptr;
+    return fail(MACLAB_ERR_OOM, "persistent segment lists allocation failed");
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->d_seg_deps, deps.data(), deps.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           h->stream),
+           "persistent segment lists upload");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "persistent segment lists sync");
+  h->seg_persist_blocks = pb;
+  return MACLAB_OK;
+}
+
+// The segment kernel's descriptor and work list for the current tile setting
+// (rows per item and steps per launch), rebuilt when they change, and for the
+// persistent form (ty 3) its wait lists.
 static maclab_status segment_prepare(maclab_ctx* h) {
   if (h->kernel != MACLAB_KERNEL_SEGMENT) return MACLAB_OK;
-  const int rows = segment_rows(h->g, h->tz);
+  const int rows = segment_rows(h->g, h->precision, h->ty, h->tz);
   const int depth = segment_depth(h->g, h->precision, h->ty);
-  if (h->d_seg_inst && h->d_seg_items && h->seg_rows == rows && h->seg_depth == depth) return MACLAB_OK;
-  if (!h->d_seg_inst) {
-    if (cudaMalloc(&h->d_seg_inst, batch_inst_bytes()) != cudaSuccess) {
-      cudaGetLastError();
-      h->d_seg_inst = nullptr;
-      return fail(MACLAB_ERR_OOM, "segment descriptor allocation failed");
+  if (!(h->d_seg_inst && h->d_seg_items && h->seg_rows == rows && h->seg_depth == depth)) {
+    if (!h->d_seg_inst) {
+      if (cudaMalloc(&h->d_seg_inst, batch_inst_bytes()) != cudaSuccess) {
+        cudaGetLastError();
+        h->d_seg_inst = nullptr;
+        return fail(MACLAB_ERR_OOM, "segment descriptor allocation failed");
+      }
     }
-  }
-  std::vector<unsigned char> inst(batch_inst_bytes());
-  batch_fill_inst(inst.data(), h->g, h->buf[0], h->buf[1], h->force_lat);
-  std::vector<int> items;
-  batch_items(0, h->g, rows, depth, items);
-  void* d = nullptr;
-  if (cudaMalloc(&d, items.size() * sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(MACLAB_ERR_OOM, "segment work list allocation failed");
-  }
-  CUDA_TRY(cudaMemcpyAsync(h->d_seg_inst, inst.data(), inst.size(), cudaMemcpyHostToDevice, h->stream),
-           "segment descriptor upload");
-  CUDA_TRY(cudaMemcpyAsync(d, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream),
-           "segment work list upload");
-  CUDA_TRY(cudaStreamSynchronize(h->stream), "segment upload sync");
-  cudaFree(h->d_seg_items);
-  h->d_seg_items = d;
-  h->seg_n_items = (int)(items.size() / 4);
-  h->seg_rows = rows;
-  h->seg_depth = depth;
-  // one step per launch: 256-thread blocks, two per SM; two: 128-thread blocks, three per SM
-  const int warps = depth == 2 ? 4 : 8, per_sm = depth == 2 ? 3 : 2;
-  const int want = (h->seg_n_items + warps - 1) / warps;
-  h->seg_blocks = want < per_sm * device_sms() ? (want > 0 ? want : 1) : per_sm * device_sms();
-  drop_graphs(h);
-  // the persistent form (two steps per sweep): as many blocks as fit at once,
-  // each with the list of blocks it waits for between sweeps
-  cudaFree(h->d_seg_deps);
-  cudaFree(h->d_seg_done);
-  h->d_seg_deps = nullptr;
-  h->d_seg_done = nullptr;
-  h->seg_persist_blocks = 0;
-  int capacity = 0;
-  if (depth == 2 && batch_persist_capacity(h->precision, &capacity) == cudaSuccess && capacity > 0) {
-    const int pb = want < capacity ? (want > 0 ? want : 1) : capacity;
-    std::vector<int> deps;
-    batch_persist_deps(items, h->g.ny, (h->g.periodic & 2u) != 0, pb, deps);
-    if (cudaMalloc(&h->d_seg_deps, deps.size() * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&h->d_seg_done, (size_t)pb * sizeof(unsigned)) != cudaSuccess) {
+    std::vector<unsigned char> inst(batch_inst_bytes());
+    batch_fill_inst(inst.data(), h->g, h->buf[0], h->buf[1], h->force_lat);
+    std::vector<int> items;
+    batch_items(0, h->g, rows, depth, items);
+    void* d = nullptr;
+    if (cudaMalloc(&d, items.size() * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
-      return fail(MACLAB_ERR_OOM, "persistent segment lists allocation failed");
+      return fail(MACLAB_ERR_OOM, "segment work list allocation failed");
     }
-    CUDA_TRY(cudaMemcpyAsync(h->d_seg_deps, deps.data(), deps.size() * sizeof(int), cudaMemcpyHostToDevice,
-                             h->stream),
-             "persistent segment lists upload");
-    CUDA_TRY(cudaStreamSynchronize(h->stream), "persistent segment lists sync");
-    h->seg_persist_blocks = pb;
+    CUDA_TRY(cudaMemcpyAsync(h->d_seg_inst, inst.data(), inst.size(), cudaMemcpyHostToDevice, h->stream),
+             "segment descriptor upload");
+    CUDA_TRY(cudaMemcpyAsync(d, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream),
+             "segment work list upload");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "segment upload sync");
+    cudaFree(h->d_seg_items);
+    h->d_seg_items = d;
+    h->seg_n_items = (int)(items.size() / 4);
+    h->seg_items_host.swap(items);
+    h->seg_rows = rows;
+    h->seg_depth = depth;
+    // one step per launch: 256-thread blocks, two per SM; two: 128-thread blocks, three per SM
+    const int warps = depth == 2 ? 4 : 8, per_sm = depth == 2 ? 3 : 2;
+    const int want = (h->seg_n_items + warps - 1) / warps;
+    h->seg_blocks = want < per_sm * device_sms() ? (want > 0 ? want : 1) : per_sm * device_sms();
+    drop_graphs(h);
+    cudaFree(h->d_seg_deps);
+    cudaFree(h->d_seg_done);
+    h->d_seg_deps = nullptr;
+    h->d_seg_done = nullptr;
+    h->seg_persist_blocks = 0;
   }
-  cudaGetLastError();
-  return MACLAB_OK;
+  return h->ty == 3 ? segment_persist_prepare(h) : MACLAB_OK;
 }
 
 // Capture graph_steps / depth launches (graph_steps steps) starting from
@@ -1578,7 +1593,11 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
       return MACLAB_OK;
     }
   }
-  if (!tiled_supported(h->g, h->precision, 0, 0)) {
+  bool any = false;
+  for (int kernel : {MACLAB_KERNEL_TILED, MACLAB_KERNEL_FOLDED, MACLAB_KERNEL_SEGMENT, MACLAB_KERNEL_ROWS2,
+                     MACLAB_KERNEL_BLOCK})
+    any = any || step_kernel_supported(h->g, h->precision, kernel);
+  if (!any) {
     if (out) { out[0] = 0; out[1] = 0; }
     return MACLAB_OK;  // only the reference kernel serves this domain
   }
@@ -1635,7 +1654,7 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
     for (int a = 0; a < n_ty; ++a)
       for (int tz : tzs) cands.push_back(Cand{kernel, h->g.d == 3 ? tys3[a] : 0, tz});
   for (int ty : {1, 2, 3})  // 3: two steps per sweep, runs in one persistent launch
-    for (int tz : {2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_SEGMENT, ty, tz});
+    for (int tz : {2, 4, 8, 16, 32}) cands.push_back(Cand{MACLAB_KERNEL_SEGMENT, ty, tz});
   for (int ty : {1, 2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_BLOCK, ty, 0});  // ty: steps per launch
   if (h->g.d == 3)
     for (int ty : {4, 8})

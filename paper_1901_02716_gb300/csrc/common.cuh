@@ -243,7 +243,7 @@ cudaError_t launch_batch_step2_persist(int precision, const void* insts, const v
                                        unsigned wait_limit, cudaStream_t st);
 cudaError_t batch_persist_capacity(int precision, int* capacity);
 void batch_persist_deps(const std::vector<int>& items4, int ny, bool py, int blocks, std::vector<int>& out);
-int segment_rows(const Geometry& g, int tz);
+int segment_rows(const Geometry& g, int precision, int ty, int tz);
 int pick_step_kernel(const Geometry& g, int precision);
 KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, int ty, int tz);
 // Queue one launch group of `kernel` (advances steps_per_launch steps).
@@ -380,6 +380,7 @@ struct maclab_ctx {
   int* d_seg_deps = nullptr;       // persistent segment launches: each block's wait list
   unsigned* d_seg_done = nullptr;  // and the blocks' finished-sweep counters
   int seg_n_items = 0, seg_blocks = 0, seg_rows = 0, seg_depth = 1, seg_persist_blocks = 0;
+  std::vector<int> seg_items_host;  // the work list (4 ints per item) the wait lists are built from
   unsigned wait_limit = maclab::kWaitLimit;  // polls before a wait between blocks gives up
   void* d_adj_scratch = nullptr;   // reference adjoint: (L_r, L_m) at every node
   double* d_adj_red = nullptr;     // adjoint: reductions (1 + 4 * n_wall_ids doubles)

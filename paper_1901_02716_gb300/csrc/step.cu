@@ -121,16 +121,23 @@ static cudaError_t launch_naive_lat(const StepLaunch& s, cudaStream_t stream) {
 // Time steps per launch of the segment kernel for the tile setting ty (2 asks
 // for two steps per launch: FP32 or FP64 storage and nx >= 8; otherwise 1).
 // Segment kernel defaults (measured on a GB300, FP32 cavities of 64^2 to
-// 1024^2): two steps per launch below 200,000 quads (small grids are bound by
-// the launches), and 2 rows per work item up to 65,536 quads, 4 above.
+// 8192^2): two steps per launch below 200,000 quads (small grids are bound by
+// the launches) and above 524,288 quads (large grids are bound by memory
+// traffic, which two steps halve: 1.57x at 2048^2, 1.8x at 8192^2), one step
+// in between (1024^2); rows per work item 2 up to 65,536 quads, 4 above, and
+// 32 for two steps above 524,288 quads (the two halo rows each side of an
+// item then cost an eighth of its rows).
+static bool segment_large(const Geometry& g) { return (int64_t)(g.nx / 4) * g.ny > 524288; }
+
 int segment_depth(const Geometry& g, int precision, int ty) {
   const bool two_ok = (precision == MACLAB_F32 || precision == MACLAB_F64) && g.nx >= 8;
-  if (ty == 0) return two_ok && (int64_t)(g.nx / 4) * g.ny < 200000 ? 2 : 1;
+  if (ty == 0) return two_ok && ((int64_t)(g.nx / 4) * g.ny < 200000 || segment_large(g)) ? 2 : 1;
   return (ty == 2 || ty == 3) && two_ok ? 2 : 1;  // 3: two steps, runs in one persistent launch
 }
 
-int segment_rows(const Geometry& g, int tz) {
+int segment_rows(const Geometry& g, int precision, int ty, int tz) {
   if (tz > 0) return tz;
+  if (segment_large(g) && segment_depth(g, precision, ty) == 2) return 32;
   return (int64_t)(g.nx / 4) * g.ny <= 65536 ? 2 : 4;
 }
 

@@ -379,6 +379,29 @@ def test_segment_default_for_large_2d_and_graphs():
     t.close()
 
 
+def test_segment_large_2d_two_steps_per_launch():
+    """Above 524,288 quads (here 2048^2) the default is two steps per launch
+    with 32 rows per work item: 5 steps against the oracle over the whole
+    field, and 9 steps bit for bit against one step per launch."""
+    case = inputs.random_case(D2, (2048, 2048), 0b00, seed=57, u_amp=0.08, rho_amp=0.02, walls="box")
+    s = M.Solver.from_case(case, M.F32)
+    info = s.kernel_info()
+    assert info["kernel"] == M.KERNEL_SEGMENT and info["steps_per_launch"] == 2
+    s.step(5)
+    r_g, u_g = s.get_state()
+    r_o, u_o = orc.step(D2, case.rho, case.u, case.periodic, wall=case.wall_mask, nsteps=5)
+    assert_parity(r_g, u_g, r_o, u_o, M.F32)
+    s.step(4)
+    x = s.get_lattice_state().copy()
+    s.close()
+    t = M.Solver.from_case(case, M.F32)
+    t.set_tile(1, 4)
+    assert t.kernel_info()["steps_per_launch"] == 1
+    t.step(9)
+    assert np.array_equal(t.get_lattice_state(), x)
+    t.close()
+
+
 def test_segment_rejects_3d_and_odd_widths():
     for case in (inputs.random_case(D3, (8, 8, 8), 0b111, seed=46),
                  inputs.random_case(D2, (17, 13), 0b11, seed=47)):
