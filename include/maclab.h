@@ -165,8 +165,8 @@ maclab_status maclab_step(maclab_handle h, int64_t n);
  * steps per launch the rows are staged four ahead in the warp's own shared
  * memory; nx % 4 == 0; the tile's tz is its rows per work item, default 2
  * up to 65,536 quads, 4 above and 32 with two steps above 524,288 quads, and
- * ty the time steps per launch, 1 or 2, default 2 below 200,000 quads and
- * above 524,288 quads where two steps are supported, see
+ * ty the time steps per launch, 1 or 2, default 2 below 200,000 quads and,
+ * with FP32 storage, above 524,288 quads, where two steps are supported, see
  * maclab_batch_set_depth), the default for D2Q9 grids with nx % 4 == 0 that the
  * block kernel does not take (below).  All compute Eqs.
  * (4)-(5) with the same terms per node (the folded kernel sums them in

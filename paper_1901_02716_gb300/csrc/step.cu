@@ -122,16 +122,19 @@ static cudaError_t launch_naive_lat(const StepLaunch& s, cudaStream_t stream) {
 // for two steps per launch: FP32 or FP64 storage and nx >= 8; otherwise 1).
 // Segment kernel defaults (measured on a GB300, FP32 cavities of 64^2 to
 // 8192^2): two steps per launch below 200,000 quads (small grids are bound by
-// the launches) and above 524,288 quads (large grids are bound by memory
-// traffic, which two steps halve: 1.57x at 2048^2, 1.8x at 8192^2), one step
-// in between (1024^2); rows per work item 2 up to 65,536 quads, 4 above, and
-// 32 for two steps above 524,288 quads (the two halo rows each side of an
-// item then cost an eighth of its rows).
+// the launches) and, with FP32 storage, above 524,288 quads (large grids are
+// bound by memory traffic, which two steps halve: 1.57x at 2048^2, 1.8x at
+// 8192^2; FP64 is bound by its arithmetic, which the halo rows only add to),
+// one step in between (1024^2); rows per work item 2 up to 65,536 quads, 4
+// above, and 32 for two steps above 524,288 quads (the two halo rows each
+// side of an item then cost an eighth of its rows).
 static bool segment_large(const Geometry& g) { return (int64_t)(g.nx / 4) * g.ny > 524288; }
 
 int segment_depth(const Geometry& g, int precision, int ty) {
   const bool two_ok = (precision == MACLAB_F32 || precision == MACLAB_F64) && g.nx >= 8;
-  if (ty == 0) return two_ok && ((int64_t)(g.nx / 4) * g.ny < 200000 || segment_large(g)) ? 2 : 1;
+  if (ty == 0)
+    return two_ok && ((int64_t)(g.nx / 4) * g.ny < 200000 || (segment_large(g) && precision == MACLAB_F32)) ? 2
+                                                                                                             : 1;
   return (ty == 2 || ty == 3) && two_ok ? 2 : 1;  // 3: two steps, runs in one persistent launch
 }
 
