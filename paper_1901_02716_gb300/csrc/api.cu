@@ -1655,7 +1655,12 @@ maclab_status maclab_tune(maclab_handle h, int32_t out[2]) {
       for (int tz : tzs) cands.push_back(Cand{kernel, h->g.d == 3 ? tys3[a] : 0, tz});
   for (int ty : {1, 2, 3})  // 3: two steps per sweep, runs in one persistent launch
     for (int tz : {2, 4, 8, 16, 32}) cands.push_back(Cand{MACLAB_KERNEL_SEGMENT, ty, tz});
-  for (int ty : {1, 2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_BLOCK, ty, 0});  // ty: steps per launch
+  // the block kernel up to 131,072 node pairs (512^2), where it was measured
+  // to win; above it the segment kernel is faster in sustained runs (1024^2:
+  // 5.5 against 5.6-5.7 us/step), though a short timing can rank them the
+  // other way
+  if ((int64_t)(h->g.nx / 2) * h->g.ny <= 131072)
+    for (int ty : {1, 2, 4, 8}) cands.push_back(Cand{MACLAB_KERNEL_BLOCK, ty, 0});  // ty: steps per launch
   if (h->g.d == 3)
     for (int ty : {4, 8})
       for (int tz : tzs) cands.push_back(Cand{MACLAB_KERNEL_ROWS2, ty, tz});
