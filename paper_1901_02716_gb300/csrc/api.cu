@@ -809,7 +809,7 @@ maclab_status maclab_adjoint_nu_term(maclab_handle h, const void* state_n, const
   if (state_np1 && h->kernel != MACLAB_KERNEL_REFERENCE && rows2_nu_supported(h->g, h->precision) &&
       aligned(state_n) && aligned(state_np1) && aligned(lam_np1)) {
     CUDA_TRY(launch_rows2_nu(h->g, state_n, state_np1, static_cast<const float*>(lam_np1), h->force_lat, acc,
-                             h->stream),
+                             h->overlap, h->stream),
              "adjoint nu term (two-rows kernel)");
     return MACLAB_OK;
   }

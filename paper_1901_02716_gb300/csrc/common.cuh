@@ -270,7 +270,7 @@ cudaError_t launch_rows2(const StepLaunch& s, cudaStream_t stream, int ty, int t
 // kernel: FP32 storage where the step kernel is built; acc += the sum.
 bool rows2_nu_supported(const Geometry& g, int precision);
 cudaError_t launch_rows2_nu(const Geometry& g, const void* state_n, const void* state_np1, const float* lam,
-                            const double force[3], double* acc, cudaStream_t stream);
+                            const double force[3], double* acc, int overlap, cudaStream_t stream);
 
 // Defined in api.cu: message returned by maclab_last_error on this thread.
 void record_error(const char* msg);

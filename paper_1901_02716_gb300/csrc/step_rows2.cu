@@ -157,7 +157,7 @@ bool rows2_nu_supported(const Geometry& g, int precision) {
 }
 
 cudaError_t launch_rows2_nu(const Geometry& g, const void* state_n, const void* state_np1, const float* lam,
-                            const double force[3], double* acc, cudaStream_t stream) {
+                            const double force[3], double* acc, int overlap, cudaStream_t stream) {
   Rows2Shape s;
   if (!rows2_nu_supported(g, MACLAB_F32) || !rows2_shape(g, MACLAB_F32, 0, &s)) return cudaErrorInvalidValue;
   TiledArgs ta{};
@@ -181,7 +181,7 @@ cudaError_t launch_rows2_nu(const Geometry& g, const void* state_n, const void* 
   ta.wall_mode = g.wall_mode;
   ta.mask = g.mask;
   for (int i = 0; i < 3; ++i) ta.force[i] = force[i];
-  ta.overlap = 0;
+  ta.overlap = overlap;  // waits for the previous kernel before reading (pdl_wait)
   ta.bounds = bounds_log();
   ta.lam = lam;
   ta.nu_acc = acc;
