@@ -320,9 +320,24 @@ maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows);
  * the default, 1) or 2.  With 2, each warp carries its row segment through two
  * updates of Eqs. (4)-(5) in registers, a two-quad and two-row halo wide, and
  * the intermediate state never goes to memory; results are bit-identical to
- * single steps.  MACLAB_ERR_UNSUPPORTED unless the batch uses one launch per
- * step, stores FP32 or FP64 and every nx >= 8.  Rebuilds the work list. */
+ * single steps.  3 is the persistent form of 2: every step pair of one
+ * maclab_batch_step call runs in a single cooperative launch (the procedure
+ * after Eq. (6), step (ii) repeated, on all domains at once), where between
+ * two sweeps a block waits only for the blocks owning rows of its domains
+ * within two rows of its own (per-block finished-sweep counters, acquire and
+ * release ordering).  Every block is resident, so every wait ends; each is
+ * bounded all the same (maclab_batch_set_wait_limit), and one that runs out
+ * ends that block's sweeps and sets the status word that maclab_sync (on any
+ * member) returns as MACLAB_ERR_TIMEOUT.  Bit-identical to depth 2.
+ * MACLAB_ERR_UNSUPPORTED unless the batch uses one launch per step, stores
+ * FP32 or FP64 and every nx >= 8 (depth 3 also when the cooperative launch
+ * does not fit on the device).  Rebuilds the work list. */
 maclab_status maclab_batch_set_depth(maclab_batch b, int32_t depth);
+
+/* Polls a wait between blocks of the persistent batch launch may take before
+ * it gives up (as maclab_set_wait_limit; < 0 restores the default).  No paper
+ * counterpart.  Errors: MACLAB_ERR_INVALID (NULL batch, above 2^32 - 1). */
+maclab_status maclab_batch_set_wait_limit(maclab_batch b, int64_t polls);
 
 /* maclab_set_launch_overlap for the batch's launches and its members
  * (maclab_batch_tune may change it).  Errors: MACLAB_ERR_INVALID (NULL batch,
@@ -331,7 +346,8 @@ maclab_status maclab_batch_set_launch_overlap(maclab_batch b, int32_t on);
 
 /* out[0] members, out[1] total nodes, out[2] fluid nodes, out[3] work items
  * per launch (0 when one launch per member is used), out[4] rows per item,
- * out[5] kernel launches per step, out[6] time steps per launch. */
+ * out[5] kernel launches per step, out[6] time steps per launch (3: the
+ * persistent form of two, maclab_batch_set_depth). */
 maclab_status maclab_batch_info(maclab_batch b, int64_t out[7]);
 
 /* ---------------------------------------------------------------- tuning
@@ -352,8 +368,8 @@ maclab_status maclab_batch_info(maclab_batch b, int64_t out[7]);
 maclab_status maclab_tune(maclab_handle h, int32_t out[2]);
 
 /* The same for a batch: chooses the rows per work item and the time steps per
- * launch (1 or 2, compared per step), then the launch overlap as above;
- * *rows receives the rows. */
+ * launch (1, 2 or the persistent form 3, compared per step), then the launch
+ * overlap as above; *rows receives the rows. */
 maclab_status maclab_batch_tune(maclab_batch b, int32_t *rows);
 
 /* ---------------------------------------------------------------- adjoint
@@ -528,6 +544,19 @@ maclab_status maclab_set_wait_limit(maclab_handle h, int64_t polls);
 maclab_status maclab_debug_segment_waits(int32_t nx, int32_t ny, int32_t periodic_y, int32_t rows,
                                          int32_t blocks, int32_t *items, int64_t items_cap, int32_t *waits,
                                          int64_t waits_cap, int64_t lens[2]);
+
+/* The same for the persistent batch launch (maclab_batch_set_depth 3): the
+ * work items and wait lists of `count` D2Q9 domains of nx[i] x ny[i] nodes
+ * (nx[i] % 4 == 0, nx[i] >= 8; periodic_y[i] != 0 if domain i wraps in y),
+ * rows rows per item.  items: 4 ints per item (domain, x segment, first row,
+ * end row), the domains' items in order; waits, lens and the capacity rule as
+ * above.  A block waits only for blocks owning rows of the same domain within
+ * two rows of its own.  Host only, no device work.  A verification aid with
+ * no paper counterpart. */
+maclab_status maclab_debug_batch_waits(int32_t count, const int32_t *nx, const int32_t *ny,
+                                       const int32_t *periodic_y, int32_t rows, int32_t blocks,
+                                       int32_t *items, int64_t items_cap, int32_t *waits,
+                                       int64_t waits_cap, int64_t lens[2]);
 
 /* Name of a status code (static string). */
 const char *maclab_status_string(maclab_status s);

@@ -595,7 +595,7 @@ static maclab_status segment_persist_prepare(maclab_ctx* h) {
   const int want = (h->seg_n_items + 3) / 4;
   const int pb = want < capacity ? (want > 0 ? want : 1) : capacity;
   std::vector<int> deps;
-  batch_persist_deps(h->seg_items_host, h->g.ny, (h->g.periodic & 2u) != 0, pb, deps);
+  batch_persist_deps(h->seg_items_host, {(int)h->g.ny}, {(h->g.periodic & 2u) != 0 ? 1 : 0}, pb, deps);
   if (cudaMalloc(&h->d_seg_deps, deps.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_seg_done, (size_t)pb * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
@@ -1124,7 +1124,36 @@ maclab_status maclab_debug_segment_waits(int32_t nx, int32_t ny, int32_t periodi
   g.n = (int64_t)nx * ny;
   std::vector<int> it, w;
   batch_items(0, g, rows, 2, it);
-  batch_persist_deps(it, ny, periodic_y != 0, blocks, w);
+  batch_persist_deps(it, {ny}, {periodic_y != 0 ? 1 : 0}, blocks, w);
+  lens[0] = (int64_t)it.size();
+  lens[1] = (int64_t)w.size();
+  if (items_cap < lens[0] || waits_cap < lens[1] || (lens[0] && !items) || (lens[1] && !waits))
+    return fail(MACLAB_ERR_INVALID, "output arrays too small (lens holds the sizes)");
+  std::copy(it.begin(), it.end(), items);
+  std::copy(w.begin(), w.end(), waits);
+  return MACLAB_OK;
+}
+
+maclab_status maclab_debug_batch_waits(int32_t count, const int32_t* nx, const int32_t* ny,
+                                       const int32_t* periodic_y, int32_t rows, int32_t blocks, int32_t* items,
+                                       int64_t items_cap, int32_t* waits, int64_t waits_cap, int64_t lens[2]) {
+  if (!lens || !nx || !ny || !periodic_y) return fail(MACLAB_ERR_INVALID, "NULL argument");
+  if (count < 1 || rows < 1 || blocks < 1) return fail(MACLAB_ERR_INVALID, "bad batch shape");
+  std::vector<int> it, w, nys, pys;
+  for (int i = 0; i < count; ++i) {
+    if (nx[i] < 8 || nx[i] % 4 != 0 || ny[i] < 1) return fail(MACLAB_ERR_INVALID, "bad domain shape");
+    Geometry g{};
+    g.lattice = kD2Q9;
+    g.d = 2;
+    g.nx = nx[i];
+    g.ny = ny[i];
+    g.nz = 1;
+    g.n = (int64_t)nx[i] * ny[i];
+    batch_items(i, g, rows, 2, it);
+    nys.push_back(ny[i]);
+    pys.push_back(periodic_y[i] != 0 ? 1 : 0);
+  }
+  batch_persist_deps(it, nys, pys, blocks, w);
   lens[0] = (int64_t)it.size();
   lens[1] = (int64_t)w.size();
   if (items_cap < lens[0] || waits_cap < lens[1] || (lens[0] && !items) || (lens[1] && !waits))
@@ -1155,6 +1184,15 @@ struct maclab_batch_ctx {
   int rows = 0;                // rows per work item
   int depth = 1;               // time steps per launch (1 or 2)
   int blocks = 0;
+  // the persistent form (depth 3 in maclab_batch_set_depth): the two-step
+  // work list, and every step pair of a call in one cooperative launch whose
+  // blocks wait only for the blocks owning rows next to theirs
+  bool persist = false;
+  std::vector<int> items_host;  // the work list (4 ints per item) the wait lists are built from
+  int* d_deps = nullptr;        // each block's wait list (batch_persist_deps)
+  unsigned* d_done = nullptr;   // the blocks' finished-sweep counters
+  int persist_blocks = 0;
+  unsigned wait_limit = maclab::kWaitLimit;  // polls before a wait between blocks gives up
   int overlap = 1;             // programmatic dependent launch
   int cur = 0;
   cudaStream_t stream = nullptr;
@@ -1180,6 +1218,8 @@ void batch_free(maclab_batch_ctx* b) {
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   cudaFree(b->d_insts);
   cudaFree(b->d_items);
+  cudaFree(b->d_deps);
+  cudaFree(b->d_done);
   for (maclab_ctx* m : b->members) maclab_destroy(m);
   delete b;
 }
@@ -1225,8 +1265,14 @@ maclab_status batch_build_items(maclab_batch_ctx* b, int rows, int depth) {
   cudaFree(b->d_items);
   b->d_items = d;
   b->n_items = (int)(items.size() / 4);
+  b->items_host.swap(items);
   b->rows = rows;
   b->depth = depth;
+  cudaFree(b->d_deps);
+  cudaFree(b->d_done);
+  b->d_deps = nullptr;
+  b->d_done = nullptr;
+  b->persist_blocks = 0;
   // resident warps: two 256-thread blocks per SM (one step per launch) or
   // three 128-thread blocks (two steps)
   const int warps_per_block = depth == 2 ? 4 : 8, per_sm = depth == 2 ? 3 : 2;
@@ -1234,6 +1280,47 @@ maclab_status batch_build_items(maclab_batch_ctx* b, int rows, int depth) {
   b->blocks = want < per_sm * sm_count() ? (want > 0 ? want : 1) : per_sm * sm_count();
   batch_drop_graphs(b);
   return MACLAB_OK;
+}
+
+// The persistent form's wait lists for the current (two-step) work list: as
+// many blocks as fit at once.  Returns MACLAB_ERR_UNSUPPORTED when the device
+// cannot hold even one block of the cooperative launch.
+maclab_status batch_persist_prepare(maclab_batch_ctx* b) {
+  if (b->persist_blocks > 0) return MACLAB_OK;
+  if (b->depth != 2) return fail(MACLAB_ERR_INVALID, "the persistent form needs the two-step work list");
+  int capacity = 0;
+  if (batch_persist_capacity(b->precision, &capacity) != cudaSuccess || capacity < 1) {
+    cudaGetLastError();
+    return fail(MACLAB_ERR_UNSUPPORTED, "the persistent launch does not fit on this device");
+  }
+  const int want = (b->n_items + 3) / 4;
+  const int pb = want < capacity ? (want > 0 ? want : 1) : capacity;
+  std::vector<int> ny, py;
+  for (const maclab_ctx* m : b->members) {
+    ny.push_back(m->g.ny);
+    py.push_back((m->g.periodic & 2u) != 0 ? 1 : 0);
+  }
+  std::vector<int> deps;
+  batch_persist_deps(b->items_host, ny, py, pb, deps);
+  if (cudaMalloc(&b->d_deps, deps.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->d_done, (size_t)pb * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->d_deps);
+    b->d_deps = nullptr;
+    b->d_done = nullptr;
+    return fail(MACLAB_ERR_OOM, "persistent batch lists allocation failed");
+  }
+  CUDA_TRY(cudaMemcpyAsync(b->d_deps, deps.data(), deps.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream),
+           "persistent batch lists upload");
+  CUDA_TRY(cudaStreamSynchronize(b->stream), "persistent batch lists sync");
+  b->persist_blocks = pb;
+  return MACLAB_OK;
+}
+
+// `sweeps` two-step sweeps from buffer c in one persistent launch.
+cudaError_t batch_launch_persist(maclab_batch_ctx* b, int c, int sweeps, cudaStream_t st) {
+  return launch_batch_step2_persist(b->precision, b->d_insts, b->d_items, b->n_items, c, b->persist_blocks, sweeps,
+                                    b->d_deps, b->d_done, step_status(), b->wait_limit, st);
 }
 
 // One launch of `steps` time steps (1, or b->depth) from buffer c.
@@ -1383,7 +1470,16 @@ maclab_status maclab_batch_step(maclab_batch b, int64_t n) {
   const int launches = batch_graph_launches(b);
   const int64_t gsteps = (int64_t)launches * k;
   int64_t done = 0;
-  while (gsteps > 0 && bulk - done >= gsteps) {
+  // the persistent form: the bulk's step pairs in one cooperative launch
+  const bool persist = b->persist && k == 2 && b->persist_blocks > 0;
+  for (int64_t pairs = persist ? bulk / 2 : 0; pairs > 0;) {
+    const int sweeps = pairs > (1 << 30) ? (1 << 30) : (int)pairs;
+    CUDA_TRY(batch_launch_persist(b, b->cur, sweeps, b->stream), "persistent batch launch");
+    if (sweeps & 1) b->cur ^= 1;
+    done += 2 * (int64_t)sweeps;
+    pairs -= sweeps;
+  }
+  while (!persist && gsteps > 0 && bulk - done >= gsteps) {
     if (!b->graph_exec[b->cur]) {
       maclab_status s = batch_build_graph(b, b->cur);
       if (s != MACLAB_OK) return s;
@@ -1412,18 +1508,35 @@ maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows) {
   if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
   if (rows < 0 || rows > (1 << 20)) return fail(MACLAB_ERR_INVALID, "bad row count");
   DeviceGuard dg(b->device);
-  return batch_build_items(b, rows ? rows : 16, b->depth);
+  maclab_status s = batch_build_items(b, rows ? rows : 16, b->depth);
+  return s == MACLAB_OK && b->persist ? batch_persist_prepare(b) : s;
 }
 
 maclab_status maclab_batch_set_depth(maclab_batch b, int32_t depth) {
   if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
-  if (depth < 0 || depth > 2) return fail(MACLAB_ERR_INVALID, "depth must be 0, 1 or 2");
+  if (depth < 0 || depth > 3) return fail(MACLAB_ERR_INVALID, "depth must be 0, 1, 2 or 3");
   if (depth == 0) depth = 1;
-  if (depth == 2 && !batch_depth2_ok(b))
+  if (depth >= 2 && !batch_depth2_ok(b))
     return fail(MACLAB_ERR_UNSUPPORTED,
                 "two steps per launch need one launch per step, FP32 or FP64 storage and nx >= 8");
   DeviceGuard dg(b->device);
-  return batch_build_items(b, b->rows ? b->rows : 16, depth);
+  const bool persist = depth == 3;
+  maclab_status s = batch_build_items(b, b->rows ? b->rows : 16, persist ? 2 : depth);
+  if (s != MACLAB_OK) return s;
+  b->persist = false;
+  if (persist) {
+    s = batch_persist_prepare(b);
+    if (s != MACLAB_OK) return s;
+    b->persist = true;
+  }
+  return MACLAB_OK;
+}
+
+maclab_status maclab_batch_set_wait_limit(maclab_batch b, int64_t polls) {
+  if (!b) return fail(MACLAB_ERR_INVALID, "NULL batch");
+  if (polls > (int64_t)0xffffffffu) return fail(MACLAB_ERR_INVALID, "wait limit above 2^32 - 1");
+  b->wait_limit = polls < 0 ? kWaitLimit : (unsigned)polls;
+  return MACLAB_OK;
 }
 
 maclab_status maclab_batch_set_launch_overlap(maclab_batch b, int32_t on) {
@@ -1451,7 +1564,7 @@ maclab_status maclab_batch_info(maclab_batch b, int64_t out[7]) {
   out[3] = b->one_launch ? b->n_items : 0;
   out[4] = b->rows;
   out[5] = b->one_launch ? 1 : (int64_t)b->members.size();
-  out[6] = b->one_launch ? b->depth : 1;
+  out[6] = !b->one_launch ? 1 : (b->persist ? 3 : b->depth);
   return MACLAB_OK;
 }
 
@@ -1795,6 +1908,8 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
   const int candidates[] = {2, 4, 8, 16, 32, 64};
   float best = 1e30f;
   int best_rows = 16, best_depth = 1;
+  bool best_persist = false;
+  b->persist = false;
   const int max_depth = batch_depth2_ok(b) ? 2 : 1;
   for (int depth = 1; depth <= max_depth; ++depth)
     for (int rows : candidates) {
@@ -1806,6 +1921,17 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
         best = ms;
         best_rows = rows;
         best_depth = depth;
+        best_persist = false;
+      }
+      // the persistent form of the same work list: one launch of 32 sweeps (64 steps)
+      if (depth == 2 && batch_persist_prepare(b) == MACLAB_OK) {
+        const float pms = time_ms(b->stream, 1, [&]() { batch_launch_persist(b, b->cur, 32, b->stream); }) / 64.f;
+        if (pms < best) {
+          best = pms;
+          best_rows = rows;
+          best_depth = depth;
+          best_persist = true;
+        }
       }
     }
   // launch overlap for the chosen work list: kept on unless plain launches
@@ -1834,6 +1960,10 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
   for (void* p : saved) cudaFree(p);
   if (e != cudaSuccess) return cuda_fail(e, "batch tuning launch");
   maclab_status s = batch_build_items(b, best_rows, best_depth);
+  if (s == MACLAB_OK && best_persist) {
+    s = batch_persist_prepare(b);
+    b->persist = s == MACLAB_OK;
+  }
   if (rows_out) *rows_out = best_rows;
   return s;
 }

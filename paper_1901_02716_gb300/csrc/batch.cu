@@ -739,30 +739,36 @@ cudaError_t launch_batch_step2_persist(int precision, const void* insts, const v
 }
 
 // The wait lists of the persistent launch: with `blocks` blocks of four warps,
-// warp w takes the items w, w + 4 blocks, ...; item (y0, y1) reads rows
-// y0 - 2 .. y1 + 1 (wrapped where y is periodic) of every x segment and
-// writes rows y0 .. y1 - 1.  Block b waits for every other block owning a row
-// that one of its items reads; the relation is symmetric, so these are also
-// the blocks that read b's rows.  out: blocks + 1 offsets (relative to the
-// array's start), then the lists.
-void batch_persist_deps(const std::vector<int>& items4, int ny, bool py, int blocks, std::vector<int>& out) {
+// warp w takes the items w, w + 4 blocks, ...; an item (domain i, rows y0, y1)
+// reads rows y0 - 2 .. y1 + 1 of domain i (wrapped where its y is periodic,
+// py[i]; domain i has ny[i] rows) in every x segment and writes rows
+// y0 .. y1 - 1.  Block b waits for every other block owning a row that one of
+// its items reads; the relation is symmetric, so these are also the blocks
+// that read b's rows.  Rows of different domains never meet.  out: blocks + 1
+// offsets (relative to the array's start), then the lists.
+void batch_persist_deps(const std::vector<int>& items4, const std::vector<int>& ny, const std::vector<int>& py,
+                        int blocks, std::vector<int>& out) {
   const int n = (int)(items4.size() / 4), nwarps = 4 * blocks;
-  std::vector<std::vector<int>> owners(ny);  // blocks owning row y (ascending, no repeats)
+  std::vector<size_t> base(ny.size() + 1, 0);  // first row of domain i in `owners`
+  for (size_t i = 0; i < ny.size(); ++i) base[i + 1] = base[i] + (size_t)ny[i];
+  std::vector<std::vector<int>> owners(base.back());  // blocks owning a row (ascending, no repeats)
   for (int i = 0; i < n; ++i) {
-    const int b = (i % nwarps) / 4;
-    for (int y = items4[4 * i + 2]; y < items4[4 * i + 3]; ++y)
-      if (owners[y].empty() || owners[y].back() != b) owners[y].push_back(b);
+    const int b = (i % nwarps) / 4, d = items4[4 * i];
+    for (int y = items4[4 * i + 2]; y < items4[4 * i + 3]; ++y) {
+      std::vector<int>& o = owners[base[d] + y];
+      if (o.empty() || o.back() != b) o.push_back(b);
+    }
   }
   std::vector<std::vector<int>> dep(blocks);
   for (int i = 0; i < n; ++i) {
-    const int b = (i % nwarps) / 4;
+    const int b = (i % nwarps) / 4, d = items4[4 * i];
     for (int y = items4[4 * i + 2] - 2; y < items4[4 * i + 3] + 2; ++y) {
       int r = y;
-      if (r < 0 || r >= ny) {
-        if (!py) continue;
-        r = ((r % ny) + ny) % ny;
+      if (r < 0 || r >= ny[d]) {
+        if (!py[d]) continue;
+        r = ((r % ny[d]) + ny[d]) % ny[d];
       }
-      for (int c : owners[r])
+      for (int c : owners[base[d] + r])
         if (c != b) dep[b].push_back(c);
     }
   }

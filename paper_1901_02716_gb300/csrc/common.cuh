@@ -242,7 +242,9 @@ cudaError_t launch_batch_step2_persist(int precision, const void* insts, const v
                                        int blocks, int sweeps, const int* deps, unsigned* done, unsigned* status,
                                        unsigned wait_limit, cudaStream_t st);
 cudaError_t batch_persist_capacity(int precision, int* capacity);
-void batch_persist_deps(const std::vector<int>& items4, int ny, bool py, int blocks, std::vector<int>& out);
+// ny[i], py[i]: rows and y periodicity of domain i of the work list.
+void batch_persist_deps(const std::vector<int>& items4, const std::vector<int>& ny, const std::vector<int>& py,
+                        int blocks, std::vector<int>& out);
 int segment_rows(const Geometry& g, int precision, int ty, int tz);
 int pick_step_kernel(const Geometry& g, int precision);
 KernelInfo describe_step_kernel(const Geometry& g, int precision, int kernel, int ty, int tz);

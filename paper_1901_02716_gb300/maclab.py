@@ -91,6 +91,9 @@ SIGNATURES = {
     "maclab_batch_step": (_S, [_H, ctypes.c_int64]),
     "maclab_batch_set_rows": (_S, [_H, ctypes.c_int32]),
     "maclab_batch_set_depth": (_S, [_H, ctypes.c_int32]),
+    "maclab_batch_set_wait_limit": (_S, [_H, ctypes.c_int64]),
+    "maclab_debug_batch_waits": (_S, [ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32,
+                                      _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "maclab_batch_set_launch_overlap": (_S, [_H, ctypes.c_int32]),
     "maclab_batch_info": (_S, [_H, ctypes.POINTER(ctypes.c_int64)]),
     "maclab_tune": (_S, [_H, ctypes.POINTER(ctypes.c_int32)]),
@@ -268,6 +271,27 @@ def maclab_sync(h):
 
 def maclab_set_wait_limit(h, polls):
     return _check(lib().maclab_set_wait_limit(h, int(polls)), "maclab_set_wait_limit")
+
+
+def maclab_debug_batch_waits(nx, ny, periodic_y, rows, blocks):
+    """(items [n, 4], waits) of the persistent batch launch over domains of
+    nx[i] x ny[i] nodes (host only)."""
+    nx = np.ascontiguousarray(nx, dtype=np.int32)
+    ny = np.ascontiguousarray(ny, dtype=np.int32)
+    py = np.ascontiguousarray(periodic_y, dtype=np.int32)
+    if not (len(nx) == len(ny) == len(py)):
+        raise ValueError("nx, ny and periodic_y need one entry per domain")
+    lens = (ctypes.c_int64 * 2)()
+    L = lib()
+    args = (len(nx), nx.ctypes.data, ny.ctypes.data, py.ctypes.data, rows, blocks)
+    s = L.maclab_debug_batch_waits(*args, None, 0, None, 0, lens)
+    if s != ERR_INVALID or lens[0] == 0:
+        _check(s, "maclab_debug_batch_waits")
+    items = np.zeros(lens[0], dtype=np.int32)
+    waits = np.zeros(max(lens[1], 1), dtype=np.int32)
+    _check(L.maclab_debug_batch_waits(*args, items.ctypes.data, lens[0], waits.ctypes.data, lens[1], lens),
+           "maclab_debug_batch_waits")
+    return items.reshape(-1, 4), waits[:lens[1]]
 
 
 def maclab_debug_segment_waits(nx, ny, periodic_y, rows, blocks):
@@ -717,8 +741,17 @@ class Batch:
         _check(lib().maclab_batch_set_rows(self.handle, int(rows)), "maclab_batch_set_rows")
 
     def set_depth(self, depth):
-        """Time steps per launch of the single launch (1 or 2)."""
+        """Time steps per launch of the single launch (1 or 2; 3: every step
+        pair of a call in one persistent launch)."""
         _check(lib().maclab_batch_set_depth(self.handle, int(depth)), "maclab_batch_set_depth")
+
+    def set_wait_limit(self, polls):
+        """Polls a wait between blocks of the persistent launch may take (< 0: default)."""
+        _check(lib().maclab_batch_set_wait_limit(self.handle, int(polls)), "maclab_batch_set_wait_limit")
+
+    def sync(self):
+        """Wait for the batch's stream; MacLABError (ERR_TIMEOUT) if a bounded wait ran out."""
+        _check(lib().maclab_sync(self.members[0].handle), "maclab_sync")
 
     def set_launch_overlap(self, on):
         """Programmatic dependent launch of the batch's step kernels (default on)."""

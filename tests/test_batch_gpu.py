@@ -213,3 +213,103 @@ def test_batch_2d_fallback_with_a_non_interleaved_member():
         assert np.array_equal(s.get_lattice_state(), m.get_lattice_state())
         s.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [M.F32, M.F64])
+@pytest.mark.parametrize("steps,rows", [(1, 16), (2, 4), (7, 16), (37, 8), (64, 2)])
+def test_persistent_batch_bit_identical(precision, steps, rows):
+    """Depth 3: every step pair of a call in one persistent cooperative launch
+    over all members, blocks waiting only on the blocks next to their rows.
+    Same sums in the same order as the two-step launches, so the same bits;
+    the last step is a one-step launch, so the residual is the same too."""
+    cases = _depth_cases()
+    ref = M.Batch.from_cases(cases, precision)
+    ref.set_rows(rows)
+    ref.set_depth(2)
+    ref.step(steps)
+    b = M.Batch.from_cases(cases, precision)
+    b.set_rows(rows)
+    b.set_depth(3)
+    assert b.info()["steps_per_launch"] == 3 and b.info()["rows"] == rows
+    b.step(steps)
+    b.sync()
+    for m, r in zip(b.members, ref.members):
+        assert np.array_equal(m.get_lattice_state(), r.get_lattice_state())
+        assert m.params["steps"] == steps
+    for m, r in zip(b.members, ref.members):
+        assert m.diagnostics()["residual"] == r.diagnostics()["residual"]
+    # a change of rows per item keeps the persistent form and the bits
+    b.set_rows(2 * rows)
+    ref.set_rows(2 * rows)
+    b.step(9)
+    ref.step(9)
+    assert b.info()["steps_per_launch"] == 3
+    for m, r in zip(b.members, ref.members):
+        assert np.array_equal(m.get_lattice_state(), r.get_lattice_state())
+    b.close()
+    ref.close()
+
+
+def test_persistent_batch_64_cavities_against_standalone_and_oracle():
+    """The 64-cavity workload (sides 64..512, Re log-uniform in [100, 3200])
+    in one persistent launch per call: every member equals its standalone run
+    bit for bit after 301 steps, and the smallest one the FP64 oracle."""
+    sides, res, lids = inputs.batch_cavity_sides(64, seed=4)
+    cases = [inputs.cavity2d(n, lid=v) for n, v in zip(sides, lids)]
+    b = M.Batch.from_cases(cases, M.F32)
+    b.set_depth(3)
+    steps = 301
+    b.step(steps)
+    b.sync()
+    for i, (m, case) in enumerate(zip(b.members, cases)):
+        if i % 8:
+            continue  # every eighth member standalone (the bits of all are tied by the test above)
+        s = M.Solver.from_case(case, M.F32)
+        s.step(steps)
+        assert np.array_equal(s.get_lattice_state(), m.get_lattice_state())
+        s.close()
+    k = int(np.argmin(sides))
+    case = cases[k]
+    r_g, u_g = b.members[k].get_state()
+    r_o, u_o = orc.step(D2, case.rho, case.u, case.periodic, wall=case.wall_mask, nsteps=steps)
+    assert np.sqrt(np.sum((u_g - u_o) ** 2) / np.sum(u_o ** 2)) < 1e-5
+    b.close()
+
+
+def test_persistent_batch_wait_runs_out():
+    """A zero wait budget makes the first wait between blocks give up at once:
+    the blocks end their sweeps, the next sync reports MACLAB_ERR_TIMEOUT once,
+    and the context stays usable -- after set_state with the default budget
+    the batch gives the two-step launches' bits."""
+    cases = _depth_cases()
+    b = M.Batch.from_cases(cases, M.F32)
+    b.set_depth(3)
+    b.set_wait_limit(0)
+    b.step(10)
+    with pytest.raises(M.MacLABError) as e:
+        b.sync()
+    assert e.value.status == M.ERR_TIMEOUT
+    b.sync()  # the status word was cleared
+    b.set_wait_limit(-1)
+    for m, case in zip(b.members, cases):
+        m.set_state(np.asarray(case.rho, np.float64), np.asarray(case.u, np.float64))  # e = 1
+    b.step(10)
+    b.sync()
+    ref = M.Batch.from_cases(cases, M.F32)
+    ref.set_depth(2)
+    ref.step(10)
+    for m, r in zip(b.members, ref.members):
+        assert np.array_equal(m.get_lattice_state(), r.get_lattice_state())
+    b.close()
+    ref.close()
+
+
+def test_persistent_batch_refused():
+    for cases, precision in ((_cases()[:2], M.BF16_STORE),
+                             ([inputs.random_case(D3, (8, 8, 8), 0b111, seed=100)], M.F32)):
+        b = M.Batch.from_cases(cases, precision)
+        with pytest.raises(M.MacLABError) as ei:
+            b.set_depth(3)
+        assert ei.value.status == M.ERR_UNSUPPORTED
+        b.step(2)
+        b.close()
