@@ -32,9 +32,13 @@
 //    a fused multiply-add; the rest direction adds 12 A; the diagonals add 1 T.
 //    The sums are R = 36 drho' and M = 36 m', u' = M / (36 + R) + F.
 //  * Box x-walls: the lanes holding x = 0 or x = nx - 1 store the wall node's
-//    unchanged values (read from the input buffer at the start of the step)
-//    in place of the computed ones, with selects, so every lane stores whole
-//    quads.
+//    unchanged values in place of the computed ones, with selects, so every
+//    lane stores whole quads.  The values come from the staged plane: when a
+//    plane is taken from its stage slot, these lanes copy their wall node's
+//    four values of both rows into a small per-thread shared-memory slot
+//    (two, by plane parity), which the store of that plane reads a plane
+//    later.  (A global load at the store exposed its latency, and registers
+//    held across a plane's update do not fit.)
 //
 // Requires: D3Q19, FP32 arithmetic (FP32, BF16 or FP16 storage), nx % 4 == 0,
 // nx / 4 <= BXC, ny % TY == 0, TYT >= 2.
@@ -227,8 +231,12 @@ struct Rows2Layout {
   static constexpr size_t stage_bytes = (size_t)kStages * slot_bytes;
   static constexpr size_t mbar_off = stage_bytes;        // one mbarrier per slot
   static constexpr size_t y_off = stage_bytes + 16;
+  // box x-wall values of the two planes in flight, [plane parity][TYT][side]
+  // [2 rows x 4 fields] floats, each slot written and read by its own thread
+  static constexpr size_t wall_off = y_off + y_bytes;
+  static constexpr size_t wall_bytes = (size_t)2 * TYT * 2 * 8 * sizeof(float);
   // + 128: the base is rounded up to a 128-byte boundary at run time
-  static constexpr size_t smem = 128 + y_off + y_bytes;
+  static constexpr size_t smem = 128 + wall_off + wall_bytes;
   static constexpr int THREADS = BXC * TYT;
   // at least eight warps per SM where shared memory allows
   static constexpr int SMEM_BLOCKS = (int)((220 * 1024) / smem) < 1 ? 1 : (int)((220 * 1024) / smem);
@@ -317,6 +325,13 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   const bool x_hi_wall = ta.wall_mode == kWallBox && !ta.px && tx == bxr - 1;
   const bool box_x = ta.wall_mode == kWallBox && !ta.px;
   const bool per_node_store = ta.wall_mode == kWallMask || (x_lo_wall && x_hi_wall);
+  // box x-walls: the lanes holding x = 0 or nx - 1 keep the wall node's values
+  // of a staged plane (walls never change) in their own shared-memory slot
+  // until the plane is stored, a plane later, instead of registers or a
+  // global load at the store
+  const bool keep_walls = !NU && box_x && (x_lo_wall || x_hi_wall) && !per_node_store;
+  float* const WV = reinterpret_cast<float*>(smem_raw + Lay::wall_off);
+  auto wall_slot = [&](int parity) { return ((parity * TYT + tr) * 2 + (x_hi_wall ? 1 : 0)) * 8; };
 
   S* op[4];
 #pragma unroll
@@ -405,6 +420,15 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
           st[j][f][0] = st[j][f][1] = O::splat(C(0));
         }
       }
+    if (keep_walls) {
+      const int w = wall_slot(i & 1);
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          if (bounds_ok(ta.bounds, w + 4 * j + f, (int64_t)(Lay::wall_bytes / sizeof(float))))
+            WV[w + 4 * j + f] = x_lo_wall ? st[j][f][0].x : st[j][f][1].y;
+    }
   };
 
   // ---------------------------------------------------------------- one plane
@@ -577,27 +601,6 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   };
 
   // ---------------------------------------------------------------- store
-  // box x-walls: the wall node's four values of the plane being stored, read
-  // from the input at the start of the step (walls never change)
-  float wv[2][4];
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int f = 0; f < 4; ++f) wv[j][f] = 0.f;
-  const bool xwall_lane = x_lo_wall || x_hi_wall;
-  // node (x = 0 or nx - 1, row0) of field 0: in bounds for every lane
-  const S* const wall_src = in + (int64_t)row0 * ta.nx + (x_hi_wall ? ta.nx - 1 : 0);
-  auto load_walls = [&](int q) {
-    if (!NU && box_x && q >= 0 && q < ta.nplanes) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int64_t e = (int64_t)(wall_src - in) + (int64_t)f * ta.n + (int64_t)q * ps + j * nx64;
-          wv[j][f] = xwall_lane && bounds_ok(ta.bounds, e, n4) ? Store<S>::from(in[e]) : 0.f;
-        }
-    }
-  };
   Rows2Sum nus;  // viscosity-term mode: this thread's sum
   // viscosity-term mode: the stored state after the step and lam of the plane
   // q the next store sums, loaded early so their latency overlaps the update
@@ -670,6 +673,14 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
         continue;
       }
       if (skip) continue;
+      // box x-walls: the values kept when plane q was staged (take index q - z0 + 1)
+      float wv[4] = {0.f, 0.f, 0.f, 0.f};
+      if (keep_walls) {
+        const int w = wall_slot((q - z0 + 1) & 1) + 4 * j;
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          if (bounds_ok(ta.bounds, w + f, (int64_t)(Lay::wall_bytes / sizeof(float)))) wv[f] = WV[w + f];
+      }
       P v[4][2];
 #pragma unroll
       for (int qq = 0; qq < 2; ++qq) {
@@ -680,8 +691,8 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
       }
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        v[f][0].x = x_lo_wall ? wv[j][f] : v[f][0].x;
-        v[f][1].y = x_hi_wall ? wv[j][f] : v[f][1].y;
+        v[f][0].x = x_lo_wall ? wv[f] : v[f][0].x;
+        v[f][1].y = x_hi_wall ? wv[f] : v[f][1].y;
         if (bounds_ok(ta.bounds, f * ta.n + in_off + off, n4 - 3)) Quad<S>::st(op[f] + off, v[f][0], v[f][1]);
       }
     }
@@ -719,7 +730,6 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   for (int p = z0; p < z1; ++p) {
     const int i = p - z0 + 1;
     fetch(i + kStages - 1);
-    load_walls(p - 1);
     nu_prefetch(p - 1);
     take(i);
     update(std::integral_constant<int, kMid>{}, R0, R1, R2);
@@ -739,7 +749,6 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   {
     const int i = np - 1;
     fetch(i + kStages - 1);
-    load_walls(z1 - 1);
     nu_prefetch(z1 - 1);
     take(i);
     if (plane_exists(z1)) update(std::integral_constant<int, kLast>{}, R0, R1, R1);
