@@ -281,7 +281,9 @@ __global__ void __launch_bounds__(BXC * TYT, Rows2Layout<S, BXC, TYT>::MIN_BLOCK
   // mbarriers, then the y exchange
   unsigned char* const smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   const int tx = threadIdx.x, tr = threadIdx.y;
-  const bool leader = tx == 0 && tr == 0;  // issues the tile copies
+  // issues the tile copies: a thread of a middle thread-row, which forms no
+  // halo row, where there is one
+  const bool leader = tx == 0 && tr == (TYT > 2 ? 1 : 0);
   const uint32_t mbar0 = smem_u32(smem_raw + Lay::mbar_off);
   if (leader) {
     mbar_init(mbar0, 1);
