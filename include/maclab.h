@@ -331,7 +331,8 @@ maclab_status maclab_batch_set_rows(maclab_batch b, int32_t rows);
  * member) returns as MACLAB_ERR_TIMEOUT.  Bit-identical to depth 2.
  * MACLAB_ERR_UNSUPPORTED unless the batch uses one launch per step, stores
  * FP32 or FP64 and every nx >= 8 (depth 3 also when the cooperative launch
- * does not fit on the device).  Rebuilds the work list. */
+ * does not fit on the device; the batch then keeps two steps per launch).
+ * Rebuilds the work list. */
 maclab_status maclab_batch_set_depth(maclab_batch b, int32_t depth);
 
 /* Polls a wait between blocks of the persistent batch launch may take before

@@ -1925,7 +1925,12 @@ maclab_status maclab_batch_tune(maclab_batch b, int32_t* rows_out) {
       }
       // the persistent form of the same work list: one launch of 32 sweeps (64 steps)
       if (depth == 2 && batch_persist_prepare(b) == MACLAB_OK) {
+        // the default wait budget: a smaller one set by the caller could cut
+        // the sweeps short and time less than the work
+        const unsigned limit = b->wait_limit;
+        b->wait_limit = kWaitLimit;
         const float pms = time_ms(b->stream, 1, [&]() { batch_launch_persist(b, b->cur, 32, b->stream); }) / 64.f;
+        b->wait_limit = limit;
         if (pms < best) {
           best = pms;
           best_rows = rows;
